@@ -1,0 +1,293 @@
+"""Pins for the FP64 oracle against facts that do not come from the oracle.
+
+Each test fixes the oracle to a closed form, an invariant of Eqs. 1-2
+(Section 3), a brute-force sampling bound, or an independent numpy
+computation, so that a dropped term, a wrong sign, an index slip or a
+transposed operand in the oracle fails somewhere here.
+"""
+
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2411_11244_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+# ----------------------------------------------------------- primitives
+
+
+def test_point_segment_closed_forms(oracle_mod):
+    o = oracle_mod
+    d, q = o.point_segment((0, 1, 0), (-1, 0, 0), (1, 0, 0))
+    assert d == pytest.approx(1.0, abs=1e-15) and np.allclose(q, 0)
+    d, q = o.point_segment((3, 4, 0), (-1, 0, 0), (0, 0, 0))  # endpoint region
+    assert d == pytest.approx(5.0, abs=1e-15) and np.allclose(q, 0)
+    d, q = o.point_segment((2, 2, 2), (1, 1, 1), (1, 1, 1))  # degenerate segment
+    assert d == pytest.approx(math.sqrt(3), abs=1e-15)
+
+
+def test_point_triangle_regions(oracle_mod):
+    o = oracle_mod
+    a, b, c = (0, 0, 0), (1, 0, 0), (0, 1, 0)
+    d, q = o.point_triangle((0.2, 0.3, 2.5), a, b, c)  # face interior: plane distance
+    assert d == pytest.approx(2.5, abs=1e-15) and np.allclose(q, (0.2, 0.3, 0))
+    d, q = o.point_triangle((0.2, 0.3, -1.5), a, b, c)  # below the face
+    assert d == pytest.approx(1.5, abs=1e-15)
+    d, q = o.point_triangle((-3, -4, 0), a, b, c)  # vertex region
+    assert d == pytest.approx(5.0, abs=1e-15) and np.allclose(q, a)
+    d, q = o.point_triangle((0.5, -2, 0), a, b, c)  # edge region (ab)
+    assert d == pytest.approx(2.0, abs=1e-15) and np.allclose(q, (0.5, 0, 0))
+    d, q = o.point_triangle((1, 1, 1), a, b, c)  # edge region (bc), out of plane
+    assert d == pytest.approx(math.sqrt(1.5), abs=1e-15) and np.allclose(q, (0.5, 0.5, 0))
+    d, q = o.point_triangle((1, 1, 0), (0, 0, 0), (1, 0, 0), (2, 0, 0))  # collinear triangle
+    assert d == pytest.approx(1.0, abs=1e-15)
+
+
+def test_point_triangle_general_plane_distance(oracle_mod):
+    """A point above the interior of a tilted triangle: |n^ . (p - a)|."""
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        a, b, c = rng.normal(size=(3, 3))
+        n = np.cross(b - a, c - a)
+        n /= np.linalg.norm(n)
+        w = rng.dirichlet((2, 2, 2))
+        inside = w[0] * a + w[1] * b + w[2] * c
+        h = rng.uniform(-2, 2)
+        d, q = oracle_mod.point_triangle(inside + h * n, a, b, c)
+        assert d == pytest.approx(abs(h), rel=1e-12, abs=1e-14)
+        assert np.allclose(q, inside, atol=1e-12)
+
+
+def test_segment_segment_closed_forms(oracle_mod):
+    o = oracle_mod
+    h = 0.37
+    d, cp, cq = o.segment_segment((-1, 0, 0), (1, 0, 0), (0, -1, h), (0, 1, h))  # perpendicular skew
+    assert d == pytest.approx(h, abs=1e-15)
+    assert np.allclose(cp, (0, 0, 0)) and np.allclose(cq, (0, 0, h))
+    th = 0.3
+    d, _, _ = o.segment_segment((-1, 0, 0), (1, 0, 0), (-math.cos(th), -math.sin(th), h),
+                                (math.cos(th), math.sin(th), h))  # oblique skew, interior
+    assert d == pytest.approx(h, abs=1e-14)
+    g = 0.25
+    d, _, _ = o.segment_segment((0, 0, 0), (2, 0, 0), (1, g, 0), (3, g, 0))  # parallel overlap
+    assert d == pytest.approx(g, abs=1e-15)
+    d, _, _ = o.segment_segment((-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0))  # crossing
+    assert d == pytest.approx(0.0, abs=1e-15)
+    d, _, _ = o.segment_segment((0, 0, 0), (1, 0, 0), (3, 0, 0), (4, 0, 0))  # collinear apart
+    assert d == pytest.approx(2.0, abs=1e-15)
+    d, _, _ = o.segment_segment((0, 0, 0), (0, 0, 0), (1, -1, 1), (1, 1, 1))  # point vs segment
+    assert d == pytest.approx(math.sqrt(2), abs=1e-15)
+
+
+def test_segment_segment_matches_line_distance(oracle_mod):
+    """Interior closest points: distance equals |(q0 - p0) . (d1 x d2)| / |d1 x d2|."""
+    rng = np.random.default_rng(11)
+    hits = 0
+    for _ in range(200):
+        p0, d1, q0, d2 = rng.normal(size=(4, 3))
+        p1, q1 = p0 + d1, q0 + d2
+        d, cp, cq = oracle_mod.segment_segment(p0, p1, q0, q1)
+        # closest points of the infinite lines
+        A = np.array([[d1 @ d1, -(d1 @ d2)], [d1 @ d2, -(d2 @ d2)]])
+        s, t = np.linalg.solve(A, [-(d1 @ (p0 - q0)), -(d2 @ (p0 - q0))])
+        if 0 < s < 1 and 0 < t < 1:
+            n = np.cross(d1, d2)
+            ref = abs((q0 - p0) @ n) / np.linalg.norm(n)
+            assert d == pytest.approx(ref, rel=1e-10, abs=1e-12)
+            hits += 1
+        else:
+            assert d >= abs((q0 - p0) @ np.cross(d1, d2)) / np.linalg.norm(np.cross(d1, d2)) - 1e-12
+    assert hits > 10
+
+
+def test_tri_tri_constructed_cases(oracle_mod):
+    o = oracle_mod
+    A = np.array([(0, 0, 0), (1, 0, 0), (0, 1, 0)], float)
+    g = 0.125
+    assert o.tri_tri(A, A + (0, 0, g))[0] == pytest.approx(g, abs=1e-15)  # stacked faces
+    # edge-edge: A's top edge along x at z = 0, B's bottom edge along y at z = h
+    Ae = np.array([(-1, 0, 0), (1, 0, 0), (0, 0, -1)], float)
+    Be = np.array([(0, -1, 0.3), (0, 1, 0.3), (0, 0, 1.3)], float)
+    d, pa, pb = o.tri_tri(Ae, Be)
+    assert d == pytest.approx(0.3, abs=1e-15) and np.allclose(pa, 0) and np.allclose(pb, (0, 0, 0.3))
+    # vertex-face: B's lowest vertex above A's interior
+    Bv = np.array([(0.2, 0.2, 0.4), (0.5, 0.5, 2.0), (-0.5, 0.6, 1.5)], float)
+    d, pa, pb = o.tri_tri(A, Bv)
+    assert d == pytest.approx(0.4, abs=1e-15) and np.allclose(pa, (0.2, 0.2, 0))
+    # piercing: a vertical triangle through A's interior
+    Bp = np.array([(0.25, 0.25, -1), (0.25, 0.25, 1), (0.3, 0.35, 0.5)], float)
+    assert o.tri_tri(A, Bp)[0] == 0.0
+    # sharing a vertex
+    Bs = np.array([(0, 0, 0), (-1, 0, 0), (0, 0, 1)], float)
+    assert o.tri_tri(A, Bs)[0] == 0.0
+    # coplanar overlap
+    Bc = np.array([(0.2, 0.2, 0), (2, 0.2, 0), (0.2, 2, 0)], float)
+    assert o.tri_tri(A, Bc)[0] <= 1e-15
+    # coplanar, apart: vertex (1,0,0) to vertex (2,0,0)
+    Bd = A + (2, 0, 0) - (1, 0, 0) + (1, 0, 0)
+    assert o.tri_tri(A, Bd)[0] == pytest.approx(1.0, abs=1e-15)
+    # symmetric in its arguments
+    assert o.tri_tri(Bv, A)[0] == pytest.approx(0.4, abs=1e-15)
+
+
+def _bary_samples(T, n):
+    pts = []
+    for i in range(n + 1):
+        for j in range(n + 1 - i):
+            pts.append(T[0] + (i / n) * (T[1] - T[0]) + (j / n) * (T[2] - T[0]))
+    return np.array(pts)
+
+
+def test_tri_tri_against_dense_sampling(oracle_mod):
+    """Sampled distances are never below the exact minimum and approach it
+    within the sampling resolution; sampled farthest distance equals the max."""
+    rng = np.random.default_rng(7)
+    n = 24
+    for k in range(120):
+        A = rng.uniform(-1, 1, (3, 3))
+        B = rng.uniform(-1, 1, (3, 3)) + rng.normal(scale=0.8, size=3) * (k % 3)
+        d, pa, pb = oracle_mod.tri_tri(A, B)
+        SA, SB = _bary_samples(A, n), _bary_samples(B, n)
+        D = np.linalg.norm(SA[:, None] - SB[None], axis=-1)
+        emax = max(np.linalg.norm(A[i] - A[(i + 1) % 3]) for i in range(3))
+        emax += max(np.linalg.norm(B[i] - B[(i + 1) % 3]) for i in range(3))
+        assert D.min() >= d - 1e-12
+        assert D.min() <= d + emax / n + 1e-12
+        assert abs(np.linalg.norm(pa - pb) - d) <= 1e-12
+        # witness points lie on their triangles
+        assert oracle_mod.point_triangle(pa, *A)[0] <= 1e-12
+        assert oracle_mod.point_triangle(pb, *B)[0] <= 1e-12
+        dm, _, _ = oracle_mod.tri_tri_max(A, B)
+        assert dm == pytest.approx(D.max(), rel=1e-14)
+
+
+# ------------------------------------------------------------ meshes
+
+
+def _rigid(rng):
+    return synth.xform(synth.random_rotation(rng), rng.normal(size=3))
+
+
+def test_two_boxes_closed_form(oracle_mod):
+    g = 0.0625
+    A = synth.box((0, 0, 0), (1, 1, 1))
+    B = synth.box((1 + g, 0.25, 0.5), (2 + g, 0.75, 1.5))
+    dmax = math.sqrt((2 + g) ** 2 + 0.75 ** 2 + 1.5 ** 2)
+    rng = np.random.default_rng(3)
+    for k in range(4):
+        X = synth.identity_xform() if k == 0 else _rigid(rng)  # same motion for both
+        for f in (oracle_mod.brute, ):
+            r = f(A, X, B, X)
+            assert r.d == pytest.approx(g, abs=1e-12)
+            rm = f(A, X, B, X, "max")
+            assert rm.d == pytest.approx(dmax, rel=1e-13)
+        bA, bB = oracle_mod.Bvh(A), oracle_mod.Bvh(B)
+        assert oracle_mod.bvh_query(bA, X, bB, X).d == pytest.approx(g, abs=1e-12)
+        assert oracle_mod.bvh_query(bA, X, bB, X, "max").d == pytest.approx(dmax, rel=1e-13)
+
+
+def test_parallel_grids_closed_form(oracle_mod):
+    g = 0.01
+    A = synth.grid(8, 1.0, 0.0)
+    B = synth.grid(8, 1.0, g, x0=0.3, y0=0.25)
+    r = oracle_mod.brute(A, synth.identity_xform(), B, synth.identity_xform())
+    assert r.d == pytest.approx(g, abs=1e-9)
+    # massive ties: the witness is the smallest (ta, tb) at distance g
+    rm = oracle_mod.brute(A, synth.identity_xform(), B, synth.identity_xform(), "max")
+    assert rm.d == pytest.approx(math.sqrt(1.3 ** 2 + 1.25 ** 2 + g * g), rel=1e-7)
+
+
+def test_geospheres_within_tessellation_bounds(oracle_mod):
+    r1, r2, s = 1.0, 0.5, 2.0
+    A = synth.geosphere(4, r1)
+    B = synth.geosphere(3, r2)
+    xb = synth.xform(np.eye(3), (s, 0, 0))
+    r = oracle_mod.brute(A, synth.identity_xform(), B, xb)
+
+    def inrad(m, rad):
+        v = m[0].astype(np.float64)
+        T = v[m[1]]
+        n = np.cross(T[:, 1] - T[:, 0], T[:, 2] - T[:, 0])
+        n /= np.linalg.norm(n, axis=1, keepdims=True)
+        return float(np.min(np.abs(np.sum(n * T[:, 0], axis=1)))) / rad
+
+    rho1, rho2 = inrad(A, r1), inrad(B, r2)
+    vmax1 = float(np.max(np.linalg.norm(A[0].astype(np.float64), axis=1)))
+    vmax2 = float(np.max(np.linalg.norm(B[0].astype(np.float64), axis=1)))
+    assert s - vmax1 - vmax2 - 1e-12 <= r.d <= s - r1 * rho1 - r2 * rho2 + 1e-12
+    rm = oracle_mod.brute(A, synth.identity_xform(), B, xb, "max")
+    assert rm.d <= s + vmax1 + vmax2 + 1e-12
+    assert rm.d >= s + 0.95 * (r1 + r2)
+
+
+def _vertex_max(A, xa, B, xb, oracle_mod):
+    wa = oracle_mod.world_vertices(A, xa)[np.unique(A[1])]
+    wb = oracle_mod.world_vertices(B, xb)[np.unique(B[1])]
+    return float(np.max(np.linalg.norm(wa[:, None] - wb[None], axis=-1)))
+
+
+def test_invariants_symmetry_rigid_zero_and_vertex_max(oracle_mod):
+    rng = np.random.default_rng(21)
+    A = synth.torus(1.0, 0.3, 12, 10)
+    B = synth.geosphere(3, 0.6, 0.01, 4)
+    for k in range(6):
+        xa, xb = _rigid(rng), _rigid(rng)
+        xb = synth.compose(synth.xform(np.eye(3), (1.5 + 0.3 * k, 0, 0)), xb)
+        r = oracle_mod.brute(A, xa, B, xb)
+        rs = oracle_mod.brute(B, xb, A, xa)
+        assert rs.d == pytest.approx(r.d, rel=1e-12, abs=1e-14)  # symmetry
+        M = _rigid(rng)
+        rr = oracle_mod.brute(A, synth.compose(M, xa), B, synth.compose(M, xb))
+        assert rr.d == pytest.approx(r.d, rel=1e-9, abs=1e-12)  # rigid invariance
+        rm = oracle_mod.brute(A, xa, B, xb, "max")
+        assert rm.d == pytest.approx(_vertex_max(A, xa, B, xb, oracle_mod), rel=1e-14)
+        assert oracle_mod.brute(B, xb, A, xa, "max").d == pytest.approx(rm.d, rel=1e-14)
+    # intersecting meshes: a sphere through the torus tube
+    xb = synth.xform(np.eye(3), (1.0, 0, 0))
+    assert oracle_mod.brute(A, synth.identity_xform(), B, xb).d == 0.0
+
+
+def _soup(rng, n, spread):
+    v = rng.uniform(-spread, spread, (3 * n, 3)).astype(np.float32)
+    t = np.arange(3 * n, dtype=np.int32).reshape(n, 3)
+    return v, t
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_bvh_oracle_equals_brute_force(oracle_mod, seed):
+    rng = np.random.default_rng(100 + seed)
+    kinds = [
+        lambda: synth.torus(1.0, 0.25, 10 + seed, 8),
+        lambda: synth.geosphere(3 + seed % 3, 0.8, 0.02, seed),
+        lambda: _soup(rng, 150 + 30 * seed, 1.0),
+        lambda: synth.gear(64, 2, teeth=8, seed=seed),
+    ]
+    A = kinds[seed % 4]()
+    B = kinds[(seed + 1) % 4]()
+    bA, bB = oracle_mod.Bvh(A), oracle_mod.Bvh(B)
+    for k in range(3):
+        xa = _rigid(rng)
+        xb = synth.compose(synth.xform(np.eye(3), rng.normal(size=3) * (0.5 + k)), xa)
+        xb = synth.compose(xb, synth.xform(synth.random_rotation(rng), (0, 0, 0)))
+        for kind in ("min", "max"):
+            r1 = oracle_mod.brute(A, xa, B, xb, kind)
+            r2 = oracle_mod.bvh_query(bA, xa, bB, xb, kind)
+            assert r2.d == r1.d
+            assert (r2.ta, r2.tb) == (r1.ta, r1.tb)
+
+
+def test_config1_seed_fixture(oracle_mod):
+    """The stored two-tori seed is the first seed whose draw does not intersect."""
+    with open(os.path.join(GOLDEN, "tori_seed.json")) as f:
+        fx = json.load(f)
+    A, B, xa, xb = synth.config_tori(fx["seed"])
+    r = oracle_mod.brute(A, xa, B, xb)
+    assert r.d > 0.0
+    assert r.d == pytest.approx(fx["d_min"], rel=1e-12)
+    for s in range(fx["seed"]):
+        A, B, xa, xb = synth.config_tori(s)
+        assert oracle_mod.brute(A, xa, B, xb).d == 0.0
