@@ -1,0 +1,291 @@
+"""Benchmark: ms per min-distance query of two interlinked 7.5 M-triangle rings.
+
+Workload (the paper's Rings teaser, Fig. 1; synthetic stand-in): two tori
+R = 1, r = 0.05, 2,500 x 1,500 quads = 7.5 M triangles each, threaded through
+each other with a surface gap of about 1e-3; each step is one frame that spins
+ring B about its own axis by a seeded angle and computes D_min through the
+engine (persistent traversal + float64 refinement).  BVH builds are
+preprocessing and not timed per query (as in the paper).
+
+Timing: every step is bracketed by CUDA events on the launching stream, after
+W warm-up steps; the L2 is flushed (a 512 MB write) before every step, outside
+the events.  `value` is the mean device time per query with the transforms
+already resident in HBM; `e2e` is the same through the synchronous C ABI call
+with host transforms and a host result (launch parameters in, result record
+out).  `--impl reference` times the FP64 CPU oracle on the same frames.
+
+Multi-GPU: queries are independent, so N ranks run replicas (each its own
+frames, no collective); value = queries of all ranks / max rank time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ms/query at 2x7.5M tris (rings, min distance)"
+WORKLOAD = "rings: 2 tori R=1 r=0.05, 2500x1500 quads = 7.5M tris each, gap 1e-3, B spun per frame"
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(A, xa, xbs, frames, threads=None):
+    """The FP64 oracle (BVH traversal), timed on this host's cores on a bounded
+    sample of frames; returns ms/query (wall time / queries, all cores)."""
+    import oracle
+    threads = threads or os.cpu_count() or 1
+    t0 = time.perf_counter()
+    ob = oracle.Bvh(A)
+    build_s = time.perf_counter() - t0
+    sample = [xbs[i % len(xbs)] for i in range(frames)]
+    t0 = time.perf_counter()
+    oracle.bvh_query_batch(ob, xa, ob, sample, "min", threads=threads)
+    wall = time.perf_counter() - t0
+    return {"value": 1000.0 * wall / frames, "unit": "ms/query", "cores": threads, "kind": "oracle",
+            "sample": f"{frames} rings frames, FP64 BVH oracle on {threads} threads (one query per thread); "
+                      f"oracle BVH build {build_s:.1f} s excluded"}
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    from paper_2411_11244_gb300 import synth
+    A, B, xa, xbs = synth.config_rings(frames=100)
+    import oracle
+    ob = oracle.Bvh(A)
+    threads = os.cpu_count() or 1
+    per = max(1, min(threads, 16))
+    for w in range(args.warmup):
+        oracle.bvh_query(ob, xa, ob, xbs[w % 100])
+    times = []
+    for s in range(args.steps):
+        batch = [xbs[(s * per + j) % 100] for j in range(per)]
+        t0 = time.perf_counter()
+        oracle.bvh_query_batch(ob, xa, ob, batch, "min", threads=per)
+        times.append(1000.0 * (time.perf_counter() - t0) / per)
+    v = statistics.mean(times)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms/query", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": v, "unit": "ms/query", "cores": per, "kind": "oracle",
+                             "sample": f"each step: {per} frames on {per} threads (FP64 BVH oracle)"},
+            "e2e": {"value": v, "unit": "ms/query", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gdist", choices=["gdist", "reference"])
+    ap.add_argument("--cpu-frames", type=int, default=32)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2411_11244_gb300 import build as B_
+    from paper_2411_11244_gb300 import gdist as G
+    from paper_2411_11244_gb300 import synth
+    if rank == 0:
+        B_.build()
+    if world > 1:
+        torch.distributed.barrier()
+    G.load()
+
+    A, B, xa, xbs = synth.config_rings(frames=100)
+    ctx = G.gd_ctx_create(local)
+    t0 = time.perf_counter()
+    ma = G.gd_mesh_create(ctx, *A)
+    G.gd_bvh_build(ma, ctx=ctx)
+    mb = G.gd_mesh_create(ctx, *B)
+    G.gd_bvh_build(mb, ctx=ctx)
+    build_ms = 1000.0 * (time.perf_counter() - t0) / 2
+    G.gd_min_distance(ctx, ma, mb, xa, xbs[0])  # sizes the work buffers
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)  # the engine's kernels, the flush and the events share it
+    torch.cuda.set_stream(stream)
+    sptr = stream.cuda_stream
+    frames = [(rank + world * i) % len(xbs) for i in range(args.warmup + args.steps)]
+    d_xa = torch.tensor(np.asarray(xa), dtype=torch.float64, device=dev)
+    d_xb = torch.tensor(np.stack([xbs[f] for f in frames]), dtype=torch.float64, device=dev)
+    d_out = torch.zeros((len(frames), 10), dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def one(i):
+        G.gd_query_device(ctx, ma, mb, G.GD_MIN, d_xa.data_ptr(), d_xb[i].data_ptr(), d_out[i].data_ptr(), sptr)
+
+    for i in range(args.warmup):
+        flush.fill_(float(i))
+        one(i)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        for s in range(args.steps):
+            flush.fill_(float(s))
+            ev[s][0].record(stream)
+            one(args.warmup + s)
+            ev[s][1].record(stream)
+            ev[s][1].synchronize()
+            stats.append(G.gd_get_stats(ctx))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    # every result must be valid
+    res = d_out.cpu().numpy()
+    import ctypes
+    for i in range(len(frames)):
+        r = G.gd_result.from_buffer_copy(res[i].tobytes())
+        assert r.status == 0, (i, r.status)
+
+    # e2e through the synchronous C ABI with host transforms and host result
+    e2e_ms = []
+    for s in range(args.steps):
+        flush.fill_(float(s))
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        G.gd_min_distance(ctx, ma, mb, xa, xbs[frames[args.warmup + s]])
+        e2e_ms.append(1000.0 * (time.perf_counter() - t1))
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    mean_ms = total_ms / args.steps
+    sorted_ms = sorted(ms)
+    p50 = sorted_ms[len(ms) // 2]
+    p99 = sorted_ms[min(len(ms) - 1, int(0.99 * len(ms)))]
+    alg = statistics.mean(s["alg_bytes"] for s in stats)
+    peak, peak_kind = _peaks()
+    achieved = alg / (statistics.mean(ms) * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": mean_ms, "unit": "ms/query", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "frames": 100, "l2": "flushed (512 MB write) before every step",
+                   "p50_ms": p50, "p99_ms": p99, "bvh_build_ms_per_mesh": build_ms,
+                   "paper_context_ms": 0.38, "paper_context_gpu": "RTX 4090 (FP32 only)"},
+        "e2e": {"value": statistics.mean(e2e_ms), "unit": "ms/query", "h2d_bytes_per_step": 192,
+                "d2h_bytes_per_step": 632, "p50_ms": sorted(e2e_ms)[len(e2e_ms) // 2]},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                     "kernel": "k_query<min>", "alg_bytes_per_launch": alg},
+        "traversal": {k: stats[-1][k] for k in ("levels", "front", "slots", "pairs_tested", "leaf_pairs",
+                                                  "tri_pairs", "candidates", "refined", "blocks")},
+        "clocks": clk.summary(),
+        "wall_s": wall,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(A, xa, xbs, args.cpu_frames)
+    print(json.dumps(line), flush=True)
+    G.gd_mesh_destroy(ma)
+    G.gd_mesh_destroy(mb)
+    G.gd_ctx_destroy(ctx)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,206 @@
+/*
+ * gdist.h -- C ABI of the GB300 mesh-mesh distance engine.
+ *
+ * The engine computes, for two triangle meshes placed by rigid transforms,
+ *   D_min = min ||p - q||  and  D_max = max ||p - q||  over p in mesh A, q in
+ *   mesh B (the paper's problem statement: Section 3, Eqs. 1-2),
+ * with a bounding-volume-pair (BVTT) front traversal over full binary
+ * "f12" BVHs (Section 7.3), pruned against a shared running bound computed
+ * from the AABB distance bounds of Section 4 (Eqs. 5-11), followed by an
+ * exact triangle-triangle narrow phase on the surviving pairs.  Traversal and
+ * culling run in float32 with outward-widened bounds; the final candidates are
+ * re-evaluated in float64.
+ *
+ * Conventions shared by every entry point:
+ *   - Vertices are float32 xyz triples; triangles are int32 index triples.
+ *   - Transforms are 12 doubles, a row-major 3x4 matrix [R | t] that maps
+ *     local coordinates v to world coordinates R v + t.  R must be orthonormal
+ *     to within 1e-9 (max-abs entry of R^T R - I); otherwise GD_ERR_INVALID_ARG.
+ *   - Results are in world units.  Witness triangles are the caller's original
+ *     triangle indices; witness points are float64 world coordinates.
+ *   - Every host pointer argument is read (or written) during the call only;
+ *     the library copies what it keeps.  Handles are owned by the library and
+ *     released by the matching *_destroy / gd_serve_stop call.  A mesh must
+ *     outlive every query and server that uses it, and the context must outlive
+ *     its meshes.
+ *   - Thread safety: a gd_ctx serves one host thread at a time (serialise
+ *     calls on a shared context); a gd_server may be used from any thread.
+ *   - No entry point falls back to a CPU computation: without a CUDA device
+ *     gd_ctx_create fails with GD_ERR_CUDA.
+ */
+#ifndef GDIST_H_
+#define GDIST_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define GD_API __attribute__((visibility("default")))
+#else
+#define GD_API
+#endif
+
+typedef enum {
+    GD_OK = 0,
+    GD_ERR_INVALID_ARG = 1, /* a NULL handle, bad sizes, out-of-range indices,
+                               non-finite data, or a non-orthonormal R */
+    GD_ERR_OOM = 2,         /* device or pinned host allocation failed */
+    GD_ERR_CUDA = 3,        /* a CUDA runtime error (text in gd_last_error) */
+    GD_ERR_NOT_BUILT = 4,   /* query on a mesh whose BVH was not built */
+    GD_ERR_OVERFLOW = 5,    /* a work queue exceeded its capacity even after
+                               the library grew it to the configured limit */
+    GD_ERR_TIMEOUT = 6,     /* a bounded device wait gave up (the kernel
+                               returned early; the context stays usable) */
+    GD_ERR_BUSY = 7,        /* server: request not admitted (no slot / memory) */
+    GD_ERR_NOT_READY = 8    /* server: ticket not finished yet */
+} gd_status;
+
+typedef enum { GD_MIN = 0, GD_MAX = 1 } gd_kind;
+
+typedef struct gd_ctx gd_ctx;
+typedef struct gd_mesh gd_mesh;
+typedef struct gd_server gd_server;
+
+/* One query answer.  For GD_MIN, pa and pb are a closest pair (pa on tri_a
+ * of mesh A, pb on tri_b of mesh B); for GD_MAX, a farthest vertex pair.
+ * status is a gd_status for this query; flags bit 0 = meshes intersect
+ * (d == 0). */
+typedef struct {
+    double d;
+    int64_t tri_a, tri_b;
+    double pa[3], pb[3];
+    uint32_t status, flags;
+} gd_result;
+
+/* One query of a batch or of the server. */
+typedef struct {
+    const gd_mesh *a, *b;
+    double xa[12], xb[12];
+    gd_kind kind;
+    uint64_t user_tag;
+} gd_query;
+
+/* BVH build options (NULL = defaults). */
+typedef struct {
+    int morton_bits; /* bits per axis of the Morton code, 1..21 (default 21) */
+} gd_build_opts;
+
+/* Traversal tunables of a context.  Zero fields keep the current value. */
+typedef struct {
+    int64_t work_target;   /* C of Section 6: a level expands n front entries by
+                              k levels per side with n * 4^k < C (default 2^20) */
+    int32_t k_max;         /* cap on k (default 5) */
+    int32_t blocks_per_sm; /* persistent CTAs per SM (default: occupancy limit) */
+    int64_t front_capacity;/* BVTT entries per front buffer (default 2^24) */
+    int64_t leaf_capacity; /* leaf-pair queue entries (default 2^24) */
+    int64_t cand_capacity; /* float64 candidate slots (default 2^22) */
+    int64_t max_capacity;  /* growth limit for the three above (default 2^28) */
+    int64_t timeout_ns;    /* bound on every device-side wait (default 2e9) */
+} gd_tunables;
+
+/* Counters of the last query (or batch) run on a context. */
+typedef struct {
+    uint32_t levels;             /* BVTT expansion levels executed */
+    uint32_t front[32];          /* front entries entering each level */
+    uint32_t slots[32];          /* log2 descendant pairs per entry per level */
+    uint64_t pairs_tested;       /* BVH node pairs whose bounds were computed */
+    uint32_t leaf_pairs;         /* leaf-leaf pairs reaching the narrow phase */
+    uint32_t tri_pairs;          /* float32 triangle pairs evaluated */
+    uint32_t candidates;         /* triangle pairs kept for float64 refinement */
+    uint32_t refined;            /* candidates evaluated in float64 */
+    uint64_t alg_bytes;          /* algorithmic bytes moved by the traversal
+                                    kernel (front entries, node boxes, triangles,
+                                    candidates), counted by the kernel */
+    uint32_t retries;            /* capacity growths during the call */
+    uint32_t blocks;             /* persistent CTAs launched */
+} gd_stats;
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`; allocates its stream and, on the
+ * first query, its work buffers.  GD_ERR_CUDA if the device is unusable. */
+GD_API gd_status gd_ctx_create(int device, gd_ctx **out);
+GD_API void gd_ctx_destroy(gd_ctx *ctx);
+/* Message of the last failing call on ctx ("" if none).  Owned by ctx. */
+GD_API const char *gd_last_error(gd_ctx *ctx);
+GD_API gd_status gd_ctx_set_tunables(gd_ctx *ctx, const gd_tunables *t);
+GD_API gd_status gd_ctx_get_tunables(gd_ctx *ctx, gd_tunables *t);
+GD_API gd_status gd_get_stats(gd_ctx *ctx, gd_stats *out);
+/* The CUDA stream (cudaStream_t) the context runs on. */
+GD_API void *gd_ctx_stream(gd_ctx *ctx);
+
+/* ---- meshes (Section 7.3: f12-BVH) --------------------------------------- */
+
+/* Copy a mesh to the device.  verts: nv x 3 float32 (host), tris: nt x 3 int32
+ * (host), 1 <= nt <= 2^30.  Indices must lie in [0, nv) and every vertex must
+ * be finite (checked on the device by gd_bvh_build). */
+GD_API gd_status gd_mesh_create(gd_ctx *ctx, const float *verts, int64_t nv, const int32_t *tris,
+                                int64_t nt, gd_mesh **out);
+/* Build the mesh's f12-BVH on the device (Section 7.3): Morton codes of the
+ * triangle centroids, a stable radix sort (ties by original index), 2^L
+ * leaves (L = floor(log2 nt)) of one or two consecutive sorted triangles, leaf
+ * boxes that are exact bounds of their vertices, and a level-by-level union of
+ * boxes up to the root.  Every box is tight (Section 4, tightness lemma).
+ * Synchronous.  GD_ERR_INVALID_ARG on bad indices or non-finite vertices. */
+GD_API gd_status gd_bvh_build(gd_mesh *mesh, const gd_build_opts *opts);
+GD_API void gd_mesh_destroy(gd_mesh *mesh);
+/* Tree depth L (leaves = 2^L) and triangle count of a built mesh. */
+GD_API gd_status gd_mesh_info(const gd_mesh *mesh, int32_t *levels, int64_t *triangles);
+/* Copy the BVH to the host for inspection: boxes (6 floats per node, node
+ * ids 1 .. 2^(L+1)-1 in heap order, entry 0 unused) and the original index of
+ * each triangle in leaf order.  Either pointer may be NULL. */
+GD_API gd_status gd_mesh_download(const gd_mesh *mesh, float *boxes, int32_t *tri_order);
+
+/* ---- queries (Algorithms 1-2; Sections 5-7) ------------------------------ */
+
+/* Minimum distance D_min (Eq. 1).  xa, xb: host transforms.  Synchronous:
+ * copies the transforms to the device, runs one persistent traversal launch,
+ * copies the result back. */
+GD_API gd_status gd_min_distance(gd_ctx *ctx, const gd_mesh *A, const gd_mesh *B, const double xa[12],
+                                 const double xb[12], gd_result *out);
+/* Maximum distance D_max (Eq. 2); same contract as gd_min_distance. */
+GD_API gd_status gd_max_distance(gd_ctx *ctx, const gd_mesh *A, const gd_mesh *B, const double xa[12],
+                                 const double xb[12], gd_result *out);
+/* Device-resident form: d_xa, d_xb are device pointers to 12 doubles each,
+ * d_out a device pointer to one gd_result; stream is a cudaStream_t (NULL =
+ * the context's stream).  Asynchronous (no host synchronisation); the
+ * context's work buffers must already be sized (any prior synchronous query
+ * does that).  Returns launch errors only; the per-query status is in
+ * d_out->status. */
+GD_API gd_status gd_query_device(gd_ctx *ctx, const gd_mesh *A, const gd_mesh *B, gd_kind kind,
+                                 const double *d_xa, const double *d_xb, gd_result *d_out, void *stream);
+/* n independent queries (any mix of meshes and kinds) in persistent
+ * launches (one per kind present), results in out[0..n).  Synchronous.
+ * A query whose work exceeds the buffers is retried alone with grown buffers. */
+GD_API gd_status gd_batch_query(gd_ctx *ctx, const gd_query *q, int64_t n, gd_result *out);
+
+/* ---- serving ----------------------------------------------------------- */
+
+typedef struct {
+    int32_t slots;            /* concurrent in-flight batches (default 4) */
+    int32_t max_batch;        /* queries per launch (default 1024) */
+    int64_t memory_budget;    /* bytes of work buffers across slots (default 8 GiB) */
+    int32_t linger_us;        /* wait this long for more requests before
+                                 launching a partial batch (default 0) */
+} gd_serve_opts;
+
+/* Start a serving loop on ctx (continuous batching: queued requests are
+ * admitted into free slots and launched while other slots are running). */
+GD_API gd_status gd_serve_start(gd_ctx *ctx, const gd_serve_opts *opts, gd_server **out);
+/* Enqueue one query; GD_ERR_BUSY if the queue is full or its footprint does
+ * not fit the memory budget.  *ticket identifies the request. */
+GD_API gd_status gd_serve_submit(gd_server *srv, const gd_query *q, uint64_t *ticket);
+/* GD_OK and *out filled if the ticket is done (the ticket is then released);
+ * GD_ERR_NOT_READY otherwise. */
+GD_API gd_status gd_serve_poll(gd_server *srv, uint64_t ticket, gd_result *out);
+/* Drain in-flight work, stop the loop and free the server. */
+GD_API gd_status gd_serve_stop(gd_server *srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GDIST_H_ */

@@ -1,0 +1,611 @@
+// C ABI of the engine (include/gdist.h): contexts, meshes, synchronous,
+// device-resident and batched queries.  Host code only validates, sizes
+// buffers and launches; every step of the computation runs in the kernels of
+// gd_build.cu and gd_query.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gd_internal.cuh"
+#include "gd_launch.h"
+#include "gd_serve.h"
+
+using namespace gd;
+
+struct Mailbox {
+    gd_result out;
+    StatsDev stats;
+    unsigned ctr[kCtrWords];
+};
+
+struct gd_mesh {
+    gd_ctx* ctx = nullptr;
+    long long nv = 0, nt = 0;
+    int L = 0;
+    float* d_verts = nullptr;
+    int32_t* d_tris = nullptr;
+    float* d_box = nullptr;
+    float4* d_tri = nullptr;
+    MeshDev* d_desc = nullptr;
+    MeshDev h_desc{};
+    bool built = false;
+};
+
+struct gd_ctx {
+    int device = 0;
+    int sms = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    gd_tunables tun{};
+    // work buffers
+    bool ready = false;
+    Item* front[2] = {nullptr, nullptr};
+    Item* leafq = nullptr;
+    Cand* cand = nullptr;
+    double* cand_d = nullptr;
+    long long cap_front = 0, cap_leaf = 0, cap_cand = 0;
+    Mailbox* mb_dev = nullptr;   // single-query results, stats and counters
+    Mailbox* mb_host = nullptr;  // pinned mirror
+    QState* qs = nullptr;
+    QIn* qin_dev = nullptr;
+    QIn* qin_host = nullptr;
+    gd_result* out_dev = nullptr;
+    gd_result* out_host = nullptr;
+    long long cap_q = 0;
+    gd_stats last{};
+    bool stats_pending = false;  // last run was device-resident: stats still on the device
+    int last_grid = 0;
+};
+
+namespace {
+
+gd_status fail(gd_ctx* ctx, gd_status s, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    return s;
+}
+
+gd_status cuda_fail(gd_ctx* ctx, cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return fail(ctx, GD_ERR_OOM, m);
+    return fail(ctx, GD_ERR_CUDA, m);
+}
+
+#define GD_CUDA(ctx, call)                                         \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call); \
+    } while (0)
+
+bool xform_ok(const double* x, std::string* why) {
+    for (int i = 0; i < 12; ++i)
+        if (!std::isfinite(x[i])) { *why = "transform has a non-finite entry"; return false; }
+    double worst = 0.0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = x[i] * x[j] + x[4 + i] * x[4 + j] + x[8 + i] * x[8 + j];
+            worst = std::max(worst, std::fabs(s - (i == j ? 1.0 : 0.0)));
+        }
+    if (worst > 1e-9) { *why = "transform rotation is not orthonormal within 1e-9"; return false; }
+    return true;
+}
+
+void free_ws(gd_ctx* c) {
+    cudaFree(c->front[0]); cudaFree(c->front[1]); cudaFree(c->leafq);
+    cudaFree(c->cand); cudaFree(c->cand_d);
+    c->front[0] = c->front[1] = c->leafq = nullptr;
+    c->cand = nullptr; c->cand_d = nullptr;
+    c->ready = false;
+}
+
+gd_status alloc_queues(gd_ctx* c) {
+    free_ws(c);
+    GD_CUDA(c, cudaMalloc(&c->front[0], sizeof(Item) * c->cap_front));
+    GD_CUDA(c, cudaMalloc(&c->front[1], sizeof(Item) * c->cap_front));
+    GD_CUDA(c, cudaMalloc(&c->leafq, sizeof(Item) * c->cap_leaf));
+    GD_CUDA(c, cudaMalloc(&c->cand, sizeof(Cand) * c->cap_cand));
+    GD_CUDA(c, cudaMalloc(&c->cand_d, sizeof(double) * c->cap_cand));
+    c->ready = true;
+    return GD_OK;
+}
+
+gd_status ensure_ws(gd_ctx* c, long long nq) {
+    if (!c->mb_dev) {
+        GD_CUDA(c, cudaMalloc(&c->mb_dev, sizeof(Mailbox)));
+        GD_CUDA(c, cudaMemset(c->mb_dev, 0, sizeof(Mailbox)));
+        GD_CUDA(c, cudaMallocHost(&c->mb_host, sizeof(Mailbox)));
+    }
+    if (!c->ready) {
+        c->cap_front = std::min<long long>(c->tun.front_capacity, 0xffffffffll);
+        c->cap_leaf = std::min<long long>(c->tun.leaf_capacity, 0xffffffffll);
+        c->cap_cand = std::min<long long>(c->tun.cand_capacity, 0xffffffffll);
+        gd_status s = alloc_queues(c);
+        if (s != GD_OK) return s;
+    }
+    if (nq > c->cap_q) {
+        long long cap = std::max<long long>(nq, 2 * c->cap_q);
+        cudaFree(c->qs); cudaFree(c->qin_dev); cudaFree(c->out_dev);
+        cudaFreeHost(c->qin_host); cudaFreeHost(c->out_host);
+        c->qs = nullptr; c->qin_dev = nullptr; c->out_dev = nullptr; c->qin_host = nullptr; c->out_host = nullptr;
+        c->cap_q = 0;
+        GD_CUDA(c, cudaMalloc(&c->qs, sizeof(QState) * cap));
+        GD_CUDA(c, cudaMalloc(&c->qin_dev, sizeof(QIn) * cap));
+        GD_CUDA(c, cudaMalloc(&c->out_dev, sizeof(gd_result) * cap));
+        GD_CUDA(c, cudaMallocHost(&c->qin_host, sizeof(QIn) * cap));
+        GD_CUDA(c, cudaMallocHost(&c->out_host, sizeof(gd_result) * cap));
+        c->cap_q = cap;
+    }
+    return GD_OK;
+}
+
+// grow every queue by 4x (bounded by max_capacity); false if already at the limit
+bool grow(gd_ctx* c) {
+    long long lim = std::min<long long>(c->tun.max_capacity, 0xffffffffll);
+    long long f = std::min(lim, c->cap_front * 4), l = std::min(lim, c->cap_leaf * 4),
+              k = std::min(lim, c->cap_cand * 4);
+    if (f == c->cap_front && l == c->cap_leaf && k == c->cap_cand) return false;
+    c->cap_front = f; c->cap_leaf = l; c->cap_cand = k;
+    return alloc_queues(c) == GD_OK;
+}
+
+int grid_blocks(gd_ctx* c, int kind) {
+    int occ = query_max_blocks_per_sm(kind);
+    int b = c->tun.blocks_per_sm > 0 ? std::min(c->tun.blocks_per_sm, occ) : occ;
+    if (b < 1) b = 1;
+    return b * c->sms;
+}
+
+void fill_common(gd_ctx* c, KArgs& a, unsigned* ctr, StatsDev* stats) {
+    a.qs = c->qs;
+    a.front0 = c->front[0];
+    a.front1 = c->front[1];
+    a.cap_front = (unsigned)c->cap_front;
+    a.leafq = c->leafq;
+    a.cap_leaf = (unsigned)c->cap_leaf;
+    a.cand = c->cand;
+    a.cand_d = c->cand_d;
+    a.cap_cand = (unsigned)c->cap_cand;
+    a.ctr = ctr;
+    a.stats = stats;
+    a.work_target = c->tun.work_target;
+    a.k_max = c->tun.k_max;
+    a.timeout_ns = c->tun.timeout_ns;
+}
+
+void to_stats(const StatsDev& s, unsigned blocks, unsigned retries, gd_stats* o) {
+    std::memset(o, 0, sizeof(*o));
+    o->levels = s.levels;
+    for (int i = 0; i < 32; ++i) { o->front[i] = s.front[i]; o->slots[i] = s.slots[i]; }
+    o->pairs_tested = s.pairs_tested;
+    o->leaf_pairs = s.leaf_pairs;
+    o->tri_pairs = s.tri_pairs;
+    o->candidates = s.candidates;
+    o->refined = s.refined;
+    o->alg_bytes = s.alg_bytes;
+    o->retries = retries;
+    o->blocks = blocks;
+}
+
+gd_status check_pair(gd_ctx* ctx, const gd_mesh* A, const gd_mesh* B) {
+    if (!A || !B) return fail(ctx, GD_ERR_INVALID_ARG, "NULL mesh");
+    if (A->ctx != ctx || B->ctx != ctx) return fail(ctx, GD_ERR_INVALID_ARG, "mesh belongs to another context");
+    if (!A->built || !B->built) return fail(ctx, GD_ERR_NOT_BUILT, "BVH not built (call gd_bvh_build)");
+    return GD_OK;
+}
+
+gd_status run_single(gd_ctx* ctx, const gd_mesh* A, const gd_mesh* B, int kind, const double* xa, const double* xb,
+                     gd_result* out) {
+    if (!ctx) return GD_ERR_INVALID_ARG;
+    if (!out || !xa || !xb) return fail(ctx, GD_ERR_INVALID_ARG, "NULL argument");
+    gd_status s = check_pair(ctx, A, B);
+    if (s != GD_OK) return s;
+    std::string why;
+    if (!xform_ok(xa, &why) || !xform_ok(xb, &why)) return fail(ctx, GD_ERR_INVALID_ARG, why);
+    s = ensure_ws(ctx, 1);
+    if (s != GD_OK) return s;
+    unsigned retries = 0;
+    for (;;) {
+        KArgs a{};
+        a.nq = 1;
+        a.qin = nullptr;
+        a.mA = A->d_desc;
+        a.mB = B->d_desc;
+        a.xa_src = nullptr;
+        a.xb_src = nullptr;
+        std::memcpy(a.xa_val, xa, sizeof(a.xa_val));
+        std::memcpy(a.xb_val, xb, sizeof(a.xb_val));
+        fill_common(ctx, a, ctx->mb_dev->ctr, &ctx->mb_dev->stats);
+        a.out = &ctx->mb_dev->out;
+        int grid = grid_blocks(ctx, kind);
+        GD_CUDA(ctx, launch_query(kind, a, grid, ctx->stream));
+        GD_CUDA(ctx, cudaMemcpyAsync(ctx->mb_host, ctx->mb_dev, sizeof(Mailbox), cudaMemcpyDeviceToHost, ctx->stream));
+        GD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        const Mailbox& m = *ctx->mb_host;
+        to_stats(m.stats, (unsigned)grid, retries, &ctx->last);
+        ctx->stats_pending = false;
+        if (m.ctr[kCtrLastAbort]) return fail(ctx, GD_ERR_TIMEOUT, "a device-side wait timed out");
+        if (m.out.status == GD_ERR_OVERFLOW) {
+            if (!grow(ctx)) return fail(ctx, GD_ERR_OVERFLOW, "work queues exceeded max_capacity");
+            ++retries;
+            continue;
+        }
+        *out = m.out;
+        if (m.out.status != GD_OK) return fail(ctx, (gd_status)m.out.status, "query failed");
+        return GD_OK;
+    }
+}
+
+}  // namespace
+
+// =========================================================== C ABI
+
+extern "C" {
+
+GD_API gd_status gd_ctx_create(int device, gd_ctx** out) {
+    if (!out) return GD_ERR_INVALID_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return GD_ERR_CUDA;
+    if (cudaSetDevice(device) != cudaSuccess) return GD_ERR_CUDA;
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
+    if (!coop) return GD_ERR_CUDA;
+    gd_ctx* c = new gd_ctx();
+    c->device = device;
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete c;
+        return GD_ERR_CUDA;
+    }
+    c->tun.work_target = 1ll << 19;
+    c->tun.k_max = 5;
+    c->tun.blocks_per_sm = 0;
+    c->tun.front_capacity = 1ll << 24;
+    c->tun.leaf_capacity = 1ll << 24;
+    c->tun.cand_capacity = 1ll << 22;
+    c->tun.max_capacity = 1ll << 28;
+    c->tun.timeout_ns = 2000000000ll;
+    *out = c;
+    return GD_OK;
+}
+
+GD_API void gd_ctx_destroy(gd_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_ws(c);
+    cudaFree(c->mb_dev);
+    cudaFreeHost(c->mb_host);
+    cudaFree(c->qs); cudaFree(c->qin_dev); cudaFree(c->out_dev);
+    cudaFreeHost(c->qin_host); cudaFreeHost(c->out_host);
+    cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+GD_API const char* gd_last_error(gd_ctx* c) { return c ? c->err.c_str() : "no context"; }
+
+GD_API void* gd_ctx_stream(gd_ctx* c) { return c ? (void*)c->stream : nullptr; }
+
+GD_API gd_status gd_ctx_set_tunables(gd_ctx* c, const gd_tunables* t) {
+    if (!c || !t) return GD_ERR_INVALID_ARG;
+    bool realloc = false;
+    if (t->work_target > 0) c->tun.work_target = t->work_target;
+    if (t->k_max > 0) c->tun.k_max = std::min(t->k_max, 12);
+    if (t->blocks_per_sm > 0) c->tun.blocks_per_sm = t->blocks_per_sm;
+    if (t->front_capacity > 0) { c->tun.front_capacity = t->front_capacity; realloc = true; }
+    if (t->leaf_capacity > 0) { c->tun.leaf_capacity = t->leaf_capacity; realloc = true; }
+    if (t->cand_capacity > 0) { c->tun.cand_capacity = t->cand_capacity; realloc = true; }
+    if (t->max_capacity > 0) c->tun.max_capacity = t->max_capacity;
+    if (t->timeout_ns > 0) c->tun.timeout_ns = t->timeout_ns;
+    if (realloc && c->ready) {
+        cudaStreamSynchronize(c->stream);
+        free_ws(c);
+    }
+    return GD_OK;
+}
+
+GD_API gd_status gd_ctx_get_tunables(gd_ctx* c, gd_tunables* t) {
+    if (!c || !t) return GD_ERR_INVALID_ARG;
+    *t = c->tun;
+    return GD_OK;
+}
+
+GD_API gd_status gd_get_stats(gd_ctx* c, gd_stats* o) {
+    if (!c || !o) return GD_ERR_INVALID_ARG;
+    if (c->stats_pending) {
+        // a device-resident query ran on a caller's stream: wait for the device
+        cudaSetDevice(c->device);
+        GD_CUDA(c, cudaDeviceSynchronize());
+        GD_CUDA(c, cudaMemcpy(&c->mb_host->stats, &c->mb_dev->stats, sizeof(StatsDev), cudaMemcpyDeviceToHost));
+        to_stats(c->mb_host->stats, (unsigned)c->last_grid, 0, &c->last);
+        c->stats_pending = false;
+    }
+    *o = c->last;
+    return GD_OK;
+}
+
+GD_API gd_status gd_mesh_create(gd_ctx* ctx, const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                                gd_mesh** out) {
+    if (!ctx || !out) return GD_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!verts || !tris || nv <= 0 || nt <= 0 || nt > (1ll << 30) || nv > (1ll << 31))
+        return fail(ctx, GD_ERR_INVALID_ARG, "bad mesh sizes (need 1 <= nt <= 2^30, nv >= 1)");
+    cudaSetDevice(ctx->device);
+    gd_mesh* m = new gd_mesh();
+    m->ctx = ctx;
+    m->nv = nv;
+    m->nt = nt;
+    cudaError_t e = cudaMalloc(&m->d_verts, sizeof(float) * 3 * nv);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_tris, sizeof(int32_t) * 3 * nt);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m->d_verts, verts, sizeof(float) * 3 * nv, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m->d_tris, tris, sizeof(int32_t) * 3 * nt, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        gd_mesh_destroy(m);
+        return cuda_fail(ctx, e, "gd_mesh_create");
+    }
+    *out = m;
+    return GD_OK;
+}
+
+GD_API gd_status gd_bvh_build(gd_mesh* m, const gd_build_opts* opts) {
+    if (!m) return GD_ERR_INVALID_ARG;
+    gd_ctx* ctx = m->ctx;
+    cudaSetDevice(ctx->device);
+    int bits = 21;
+    if (opts) {
+        if (opts->morton_bits < 1 || opts->morton_bits > 21) return fail(ctx, GD_ERR_INVALID_ARG, "morton_bits in 1..21");
+        bits = opts->morton_bits;
+    }
+    int L = 0;
+    while ((2ll << L) <= m->nt) ++L;
+    cudaFree(m->d_box); cudaFree(m->d_tri);
+    m->d_box = nullptr; m->d_tri = nullptr;
+    m->built = false;
+    BuildBuffers b{};
+    b.verts = m->d_verts; b.tris = m->d_tris; b.nv = m->nv; b.nt = m->nt; b.L = L; b.morton_bits = bits;
+    std::vector<void*> tmp;
+    auto cleanup = [&]() { for (void* p : tmp) cudaFree(p); };
+#define GD_ALLOC(ptr, bytes)                                                 \
+    do {                                                                     \
+        cudaError_t e_ = cudaMalloc((void**)&(ptr), (bytes));                \
+        if (e_ != cudaSuccess) { cleanup(); return cuda_fail(ctx, e_, "gd_bvh_build alloc"); } \
+        tmp.push_back((void*)(ptr));                                         \
+    } while (0)
+    GD_ALLOC(b.flags, 64 * sizeof(unsigned));
+    GD_ALLOC(b.keys[0], sizeof(unsigned long long) * m->nt);
+    GD_ALLOC(b.keys[1], sizeof(unsigned long long) * m->nt);
+    GD_ALLOC(b.vals[0], sizeof(unsigned) * m->nt);
+    GD_ALLOC(b.vals[1], sizeof(unsigned) * m->nt);
+    GD_ALLOC(b.hist, sizeof(unsigned) * build_hist_words(m->nt));
+#undef GD_ALLOC
+    cudaError_t e = cudaMalloc(&m->d_box, sizeof(float) * 6 * (2ull << L));
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_tri, sizeof(float4) * 3 * m->nt);
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(ctx, e, "gd_bvh_build alloc"); }
+    b.box = m->d_box;
+    b.tri = m->d_tri;
+    unsigned flags[8] = {0};
+    e = build_validate(b, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(flags, b.flags, sizeof(flags), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(ctx, e, "gd_bvh_build validate"); }
+    if (flags[0]) { cleanup(); return fail(ctx, GD_ERR_INVALID_ARG, "triangle index out of range"); }
+    if (flags[1]) { cleanup(); return fail(ctx, GD_ERR_INVALID_ARG, "non-finite vertex coordinate"); }
+    e = build_tree(b, ctx->stream);
+    float root[6];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(root, m->d_box + 6, sizeof(root), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cleanup();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "gd_bvh_build");
+    float P = 0.f;
+    for (int i = 0; i < 6; ++i) P = std::max(P, std::fabs(root[i]));
+    m->L = L;
+    m->h_desc.box = m->d_box;
+    m->h_desc.tri = m->d_tri;
+    m->h_desc.T = m->nt;
+    m->h_desc.L = L;
+    m->h_desc.P = P;
+    if (!m->d_desc) GD_CUDA(ctx, cudaMalloc(&m->d_desc, sizeof(MeshDev)));
+    GD_CUDA(ctx, cudaMemcpyAsync(m->d_desc, &m->h_desc, sizeof(MeshDev), cudaMemcpyHostToDevice, ctx->stream));
+    GD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    m->built = true;
+    return GD_OK;
+}
+
+GD_API void gd_mesh_destroy(gd_mesh* m) {
+    if (!m) return;
+    if (m->ctx) {
+        cudaSetDevice(m->ctx->device);
+        cudaStreamSynchronize(m->ctx->stream);
+    }
+    cudaFree(m->d_verts); cudaFree(m->d_tris); cudaFree(m->d_box); cudaFree(m->d_tri); cudaFree(m->d_desc);
+    delete m;
+}
+
+GD_API gd_status gd_mesh_info(const gd_mesh* m, int32_t* levels, int64_t* triangles) {
+    if (!m) return GD_ERR_INVALID_ARG;
+    if (levels) *levels = m->L;
+    if (triangles) *triangles = m->nt;
+    return m->built ? GD_OK : GD_ERR_NOT_BUILT;
+}
+
+GD_API gd_status gd_mesh_download(const gd_mesh* m, float* boxes, int32_t* order) {
+    if (!m) return GD_ERR_INVALID_ARG;
+    if (!m->built) return fail(m->ctx, GD_ERR_NOT_BUILT, "BVH not built");
+    gd_ctx* ctx = m->ctx;
+    cudaSetDevice(ctx->device);
+    if (boxes)
+        GD_CUDA(ctx, cudaMemcpy(boxes, m->d_box, sizeof(float) * 6 * (2ull << m->L), cudaMemcpyDeviceToHost));
+    if (order) {
+        std::vector<float4> t(3 * m->nt);
+        GD_CUDA(ctx, cudaMemcpy(t.data(), m->d_tri, sizeof(float4) * 3 * m->nt, cudaMemcpyDeviceToHost));
+        for (long long j = 0; j < m->nt; ++j) {
+            int id;
+            std::memcpy(&id, &t[3 * j + 2].y, sizeof(int));
+            order[j] = id;
+        }
+    }
+    return GD_OK;
+}
+
+GD_API gd_status gd_min_distance(gd_ctx* ctx, const gd_mesh* A, const gd_mesh* B, const double xa[12],
+                                 const double xb[12], gd_result* out) {
+    return run_single(ctx, A, B, 0, xa, xb, out);
+}
+
+GD_API gd_status gd_max_distance(gd_ctx* ctx, const gd_mesh* A, const gd_mesh* B, const double xa[12],
+                                 const double xb[12], gd_result* out) {
+    return run_single(ctx, A, B, 1, xa, xb, out);
+}
+
+GD_API gd_status gd_query_device(gd_ctx* ctx, const gd_mesh* A, const gd_mesh* B, gd_kind kind, const double* d_xa,
+                                 const double* d_xb, gd_result* d_out, void* stream) {
+    if (!ctx) return GD_ERR_INVALID_ARG;
+    if (!d_xa || !d_xb || !d_out || (kind != GD_MIN && kind != GD_MAX))
+        return fail(ctx, GD_ERR_INVALID_ARG, "NULL argument or bad kind");
+    gd_status s = check_pair(ctx, A, B);
+    if (s != GD_OK) return s;
+    if (!ctx->ready || !ctx->mb_dev || ctx->cap_q < 1)
+        return fail(ctx, GD_ERR_INVALID_ARG, "work buffers not sized: run one synchronous query first");
+    KArgs a{};
+    a.nq = 1;
+    a.mA = A->d_desc;
+    a.mB = B->d_desc;
+    a.xa_src = d_xa;
+    a.xb_src = d_xb;
+    fill_common(ctx, a, ctx->mb_dev->ctr, &ctx->mb_dev->stats);
+    a.out = d_out;
+    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+    int grid = grid_blocks(ctx, (int)kind);
+    GD_CUDA(ctx, launch_query((int)kind, a, grid, st));
+    ctx->stats_pending = true;
+    ctx->last_grid = grid;
+    return GD_OK;
+}
+
+GD_API gd_status gd_batch_query(gd_ctx* ctx, const gd_query* q, int64_t n, gd_result* out) {
+    if (!ctx) return GD_ERR_INVALID_ARG;
+    if (n < 0 || (n > 0 && (!q || !out))) return fail(ctx, GD_ERR_INVALID_ARG, "NULL argument");
+    if (n == 0) return GD_OK;
+    if (n > (1ll << 24)) return fail(ctx, GD_ERR_INVALID_ARG, "batch larger than 2^24 queries");
+    std::string why;
+    for (int64_t i = 0; i < n; ++i) {
+        gd_status s = check_pair(ctx, q[i].a, q[i].b);
+        if (s != GD_OK) return s;
+        if (q[i].kind != GD_MIN && q[i].kind != GD_MAX) return fail(ctx, GD_ERR_INVALID_ARG, "bad query kind");
+        if (!xform_ok(q[i].xa, &why) || !xform_ok(q[i].xb, &why)) return fail(ctx, GD_ERR_INVALID_ARG, why);
+    }
+    unsigned total_retries = 0;
+    gd_stats agg{};
+    for (int kind = 0; kind < 2; ++kind) {
+        std::vector<int64_t> idx;
+        for (int64_t i = 0; i < n; ++i)
+            if ((int)q[i].kind == kind) idx.push_back(i);
+        if (idx.empty()) continue;
+        long long m = (long long)idx.size();
+        gd_status s = ensure_ws(ctx, m);
+        if (s != GD_OK) return s;
+        for (long long j = 0; j < m; ++j) {
+            const gd_query& Q = q[idx[j]];
+            QIn& in = ctx->qin_host[j];
+            in.A = Q.a->d_desc;
+            in.B = Q.b->d_desc;
+            std::memcpy(in.xa, Q.xa, sizeof(in.xa));
+            std::memcpy(in.xb, Q.xb, sizeof(in.xb));
+        }
+        GD_CUDA(ctx, cudaMemcpyAsync(ctx->qin_dev, ctx->qin_host, sizeof(QIn) * m, cudaMemcpyHostToDevice, ctx->stream));
+        KArgs a{};
+        a.nq = (int)m;
+        a.qin = ctx->qin_dev;
+        fill_common(ctx, a, ctx->mb_dev->ctr, &ctx->mb_dev->stats);
+        a.out = ctx->out_dev;
+        int grid = grid_blocks(ctx, kind);
+        GD_CUDA(ctx, launch_query(kind, a, grid, ctx->stream));
+        GD_CUDA(ctx, cudaMemcpyAsync(ctx->out_host, ctx->out_dev, sizeof(gd_result) * m, cudaMemcpyDeviceToHost, ctx->stream));
+        GD_CUDA(ctx, cudaMemcpyAsync(ctx->mb_host, ctx->mb_dev, sizeof(Mailbox), cudaMemcpyDeviceToHost, ctx->stream));
+        GD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        gd_stats st;
+        to_stats(ctx->mb_host->stats, (unsigned)grid, 0, &st);
+        agg.levels = std::max(agg.levels, st.levels);
+        agg.pairs_tested += st.pairs_tested;
+        agg.leaf_pairs += st.leaf_pairs;
+        agg.tri_pairs += st.tri_pairs;
+        agg.candidates += st.candidates;
+        agg.refined += st.refined;
+        agg.alg_bytes += st.alg_bytes;
+        agg.blocks = st.blocks;
+        for (int i = 0; i < 32; ++i) { agg.front[i] += st.front[i]; agg.slots[i] = std::max(agg.slots[i], st.slots[i]); }
+        if (ctx->mb_host->ctr[kCtrLastAbort]) return fail(ctx, GD_ERR_TIMEOUT, "a device-side wait timed out");
+        std::vector<int64_t> redo;
+        for (long long j = 0; j < m; ++j) {
+            out[idx[j]] = ctx->out_host[j];
+            if (ctx->out_host[j].status == GD_ERR_OVERFLOW) redo.push_back(idx[j]);
+        }
+        for (int64_t i : redo) {
+            gd_status r = run_single(ctx, q[i].a, q[i].b, kind, q[i].xa, q[i].xb, &out[i]);
+            total_retries += 1 + ctx->last.retries;
+            if (r != GD_OK && r != GD_ERR_OVERFLOW) return r;
+        }
+    }
+    agg.retries = total_retries;
+    ctx->last = agg;
+    ctx->stats_pending = false;
+    return GD_OK;
+}
+
+}  // extern "C"
+
+// ---- hooks for the serving loop (gd_serve.cu)
+namespace gd {
+
+gd_status serve_launch_batch(gd_ctx* ctx, SlotBuffers& sb, const gd_query* qs, long long m, int kind) {
+    for (long long j = 0; j < m; ++j) {
+        QIn& in = sb.qin_host[j];
+        in.A = qs[j].a->d_desc;
+        in.B = qs[j].b->d_desc;
+        std::memcpy(in.xa, qs[j].xa, sizeof(in.xa));
+        std::memcpy(in.xb, qs[j].xb, sizeof(in.xb));
+    }
+    GD_CUDA(ctx, cudaMemcpyAsync(sb.qin_dev, sb.qin_host, sizeof(QIn) * m, cudaMemcpyHostToDevice, sb.stream));
+    KArgs a{};
+    a.nq = (int)m;
+    a.qin = sb.qin_dev;
+    a.qs = sb.qs;
+    a.front0 = sb.front[0];
+    a.front1 = sb.front[1];
+    a.cap_front = (unsigned)sb.cap_front;
+    a.leafq = sb.leafq;
+    a.cap_leaf = (unsigned)sb.cap_leaf;
+    a.cand = sb.cand;
+    a.cand_d = sb.cand_d;
+    a.cap_cand = (unsigned)sb.cap_cand;
+    a.ctr = sb.mb_dev_ctr;
+    a.stats = sb.stats_dev;
+    a.work_target = ctx->tun.work_target;
+    a.k_max = ctx->tun.k_max;
+    a.timeout_ns = ctx->tun.timeout_ns;
+    a.out = sb.out_dev;
+    GD_CUDA(ctx, launch_query(kind, a, sb.grid, sb.stream));
+    GD_CUDA(ctx, cudaMemcpyAsync(sb.out_host, sb.out_dev, sizeof(gd_result) * m, cudaMemcpyDeviceToHost, sb.stream));
+    GD_CUDA(ctx, cudaMemcpyAsync(sb.ctr_host, sb.mb_dev_ctr, sizeof(unsigned) * kCtrWords, cudaMemcpyDeviceToHost,
+                                 sb.stream));
+    return GD_OK;
+}
+
+gd_status serve_single(gd_ctx* ctx, const gd_query& q, gd_result* out) {
+    return run_single(ctx, q.a, q.b, (int)q.kind, q.xa, q.xb, out);
+}
+
+int serve_device(gd_ctx* ctx) { return ctx->device; }
+int serve_sms(gd_ctx* ctx) { return ctx->sms; }
+const gd_tunables& serve_tunables(gd_ctx* ctx) { return ctx->tun; }
+bool serve_query_ok(gd_ctx* ctx, const gd_query& q, std::string* why) {
+    if (check_pair(ctx, q.a, q.b) != GD_OK) { *why = ctx->err; return false; }
+    if (q.kind != GD_MIN && q.kind != GD_MAX) { *why = "bad query kind"; return false; }
+    return xform_ok(q.xa, why) && xform_ok(q.xb, why);
+}
+long long serve_mesh_tris(const gd_mesh* m) { return m ? m->nt : 0; }
+
+}  // namespace gd

@@ -1,0 +1,266 @@
+// f12-BVH construction on the device (Section 7.3): Morton codes of the
+// triangle centroids, a stable LSD radix sort (ties keep the original
+// order), 2^L leaves of one or two consecutive sorted triangles, exact leaf
+// boxes, and a level-by-level union up to the root.  Leaf boxes are exact
+// bounds of their vertices, so every box is tight (Section 4: tight leaves
+// make every node tight).
+#include <cfloat>
+#include <cstdint>
+
+#include "gd_internal.cuh"
+#include "gd_launch.h"
+
+namespace gd {
+
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;                      // keys per thread per tile
+constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys per CTA
+
+// float -> uint32 whose unsigned order is the float order
+__device__ __forceinline__ unsigned ordered(float f) {
+    unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float unordered(unsigned u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// flags: [0] bad index, [1] non-finite vertex, [2..4] ordered min, [5..7] ordered max
+__global__ void k_init_flags(unsigned* flags) {
+    if (threadIdx.x < 8) flags[threadIdx.x] = (threadIdx.x >= 2 && threadIdx.x < 5) ? 0xffffffffu : 0u;
+}
+
+__global__ void k_validate(const float* verts, long long nv, const int32_t* tris, long long nt, unsigned* flags) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    bool bad_idx = false, bad_val = false;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += stride) {
+        for (int k = 0; k < 3; ++k) {
+            int32_t v = tris[3 * t + k];
+            if (v < 0 || v >= nv) { bad_idx = true; continue; }
+            for (int c = 0; c < 3; ++c) {
+                float x = verts[3ll * v + c];
+                if (!isfinite(x)) { bad_val = true; continue; }
+                lo[c] = fminf(lo[c], x);
+                hi[c] = fmaxf(hi[c], x);
+            }
+        }
+    }
+    if (__any_sync(kFull, bad_idx) && (threadIdx.x & 31) == 0) atomicOr(flags + 0, 1u);
+    if (__any_sync(kFull, bad_val) && (threadIdx.x & 31) == 0) atomicOr(flags + 1, 1u);
+    for (int c = 0; c < 3; ++c) {
+        unsigned a = __reduce_min_sync(kFull, ordered(lo[c]));
+        unsigned b = __reduce_max_sync(kFull, ordered(hi[c]));
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(flags + 2 + c, a);
+            atomicMax(flags + 5 + c, b);
+        }
+    }
+}
+
+__device__ __forceinline__ unsigned long long spread3(unsigned v) {
+    unsigned long long x = v & 0x1fffffull;
+    x = (x | (x << 32)) & 0x1f00000000ffffull;
+    x = (x | (x << 16)) & 0x1f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+__global__ void k_morton(const float* verts, const int32_t* tris, long long nt, const unsigned* flags, int bits,
+                         unsigned long long* keys, unsigned* vals) {
+    float lo[3], ext[3];
+    for (int c = 0; c < 3; ++c) {
+        lo[c] = unordered(flags[2 + c]);
+        ext[c] = unordered(flags[5 + c]) - lo[c];
+    }
+    const float cells = (float)(1u << bits);
+    const unsigned top = (1u << bits) - 1u;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += stride) {
+        unsigned q[3];
+        for (int c = 0; c < 3; ++c) {
+            // explicit round-to-nearest steps (no contraction), so that the
+            // codes can be reproduced bit for bit on the host
+            float s = __fadd_rn(__fadd_rn(verts[3ll * tris[3 * t] + c], verts[3ll * tris[3 * t + 1] + c]),
+                                verts[3ll * tris[3 * t + 2] + c]);
+            float x = __fsub_rn(__fmul_rn(s, 1.0f / 3.0f), lo[c]);
+            float f = ext[c] > 0.f ? __fmul_rn(__fdiv_rn(x, ext[c]), cells) : 0.f;
+            unsigned qi = f <= 0.f ? 0u : (f >= (float)top ? top : (unsigned)f);
+            q[c] = qi;
+        }
+        keys[t] = spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2);
+        vals[t] = (unsigned)t;
+    }
+}
+
+// ---- stable LSD radix sort of (64-bit key, 32-bit value), 8 bits per pass
+
+__global__ void k_rs_hist(const unsigned long long* keys, long long n, int shift, unsigned* hist) {
+    __shared__ unsigned h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    long long base = (long long)blockIdx.x * kSortTile;
+    for (int i = 0; i < kSortItems; ++i) {
+        long long j = base + (long long)i * kSortThreads + threadIdx.x;
+        if (j < n) atomicAdd(&h[(unsigned)(keys[j] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(long long)threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
+}
+
+// exclusive scan of m words in place, one CTA of 1024 threads
+__global__ void k_rs_scan(unsigned* hist, long long m) {
+    __shared__ unsigned part[1024];
+    long long per = (m + 1023) / 1024;
+    long long b = threadIdx.x * per, e = b + per < m ? b + per : m;
+    unsigned s = 0;
+    for (long long i = b; i < e; ++i) s += hist[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        unsigned v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    unsigned run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
+    for (long long i = b; i < e; ++i) {
+        unsigned v = hist[i];
+        hist[i] = run;
+        run += v;
+    }
+}
+
+__global__ void k_rs_scatter(const unsigned long long* kin, const unsigned* vin, unsigned long long* kout,
+                             unsigned* vout, long long n, int shift, const unsigned* hist) {
+    __shared__ unsigned wcnt[kSortThreads / 32][256];
+    __shared__ unsigned run[256];
+    __shared__ unsigned off[256];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    run[threadIdx.x] = 0;
+    off[threadIdx.x] = hist[(long long)threadIdx.x * gridDim.x + blockIdx.x];
+    long long base = (long long)blockIdx.x * kSortTile;
+    for (int i = 0; i < kSortItems; ++i) {
+        for (int w = 0; w < kSortThreads / 32; ++w) wcnt[w][threadIdx.x] = 0;
+        __syncthreads();
+        long long j = base + (long long)i * kSortThreads + threadIdx.x;
+        bool ok = j < n;
+        unsigned long long key = ok ? kin[j] : 0ull;
+        unsigned val = ok ? vin[j] : 0u;
+        unsigned d = ok ? (unsigned)(key >> shift) & 255u : 256u + (unsigned)lane;  // unique dummy digit
+        unsigned peers = __match_any_sync(kFull, d);
+        unsigned rank = __popc(peers & lanemask_lt());
+        if (ok && rank == 0) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        // per digit: exclusive prefix over warps, then advance the running count
+        {
+            unsigned acc = 0;
+            for (int w = 0; w < kSortThreads / 32; ++w) {
+                unsigned c = wcnt[w][threadIdx.x];
+                wcnt[w][threadIdx.x] = acc;
+                acc += c;
+            }
+            unsigned r0 = run[threadIdx.x];
+            run[threadIdx.x] = r0 + acc;
+            // stash the pre-advance running count in the slot of warp 0's prefix
+            // (warp 0 prefix is always 0, so store r0 there and add below)
+            wcnt[0][threadIdx.x] = r0;
+            for (int w = 1; w < kSortThreads / 32; ++w) wcnt[w][threadIdx.x] += r0;
+        }
+        __syncthreads();
+        if (ok) {
+            unsigned pos = off[d] + wcnt[warp][d] + rank;
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+        __syncthreads();
+    }
+}
+
+// leaves: leaf l owns sorted triangles [floor(l T / 2^L), floor((l+1) T / 2^L))
+__global__ void k_leaves(const float* verts, const int32_t* tris, long long nt, int L, const unsigned* order,
+                         float4* tri, float* box) {
+    const long long nleaf = 1ll << L;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x; l < nleaf; l += stride) {
+        long long s = (long long)(((unsigned long long)l * (unsigned long long)nt) >> L);
+        long long e = (long long)(((unsigned long long)(l + 1) * (unsigned long long)nt) >> L);
+        float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+        for (long long j = s; j < e; ++j) {
+            unsigned id = order[j];
+            float v[9];
+            for (int k = 0; k < 3; ++k)
+                for (int c = 0; c < 3; ++c) {
+                    float x = verts[3ll * tris[3ll * id + k] + c];
+                    v[3 * k + c] = x;
+                    lo[c] = fminf(lo[c], x);
+                    hi[c] = fmaxf(hi[c], x);
+                }
+            tri[3 * j] = make_float4(v[0], v[1], v[2], v[3]);
+            tri[3 * j + 1] = make_float4(v[4], v[5], v[6], v[7]);
+            tri[3 * j + 2] = make_float4(v[8], __int_as_float((int)id), 0.f, 0.f);
+        }
+        float* b = box + 6 * ((1ll << L) + l);
+        b[0] = lo[0]; b[1] = lo[1]; b[2] = lo[2];
+        b[3] = hi[0]; b[4] = hi[1]; b[5] = hi[2];
+    }
+}
+
+// one level: node i in [2^d, 2^(d+1)) gets the union of nodes 2i, 2i+1
+__global__ void k_reduce_level(float* box, int d) {
+    const long long n = 1ll << d;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+        long long i = n + k;
+        const float* l = box + 12 * i;
+        const float* r = l + 6;
+        float* o = box + 6 * i;
+        o[0] = fminf(l[0], r[0]); o[1] = fminf(l[1], r[1]); o[2] = fminf(l[2], r[2]);
+        o[3] = fmaxf(l[3], r[3]); o[4] = fmaxf(l[4], r[4]); o[5] = fmaxf(l[5], r[5]);
+    }
+}
+
+int grid_for(long long n, int threads) {
+    long long g = (n + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > 152 * 16) g = 152 * 16;
+    return (int)g;
+}
+
+}  // namespace
+
+size_t build_hist_words(long long nt) {
+    long long nb = (nt + kSortTile - 1) / kSortTile;
+    if (nb < 1) nb = 1;
+    return (size_t)nb * 256;
+}
+
+cudaError_t build_validate(const BuildBuffers& b, cudaStream_t st) {
+    k_init_flags<<<1, 32, 0, st>>>(b.flags);
+    k_validate<<<grid_for(b.nt, 256), 256, 0, st>>>(b.verts, b.nv, b.tris, b.nt, b.flags);
+    return cudaGetLastError();
+}
+
+cudaError_t build_tree(const BuildBuffers& b, cudaStream_t st) {
+    k_morton<<<grid_for(b.nt, 256), 256, 0, st>>>(b.verts, b.tris, b.nt, b.flags, b.morton_bits, b.keys[0],
+                                                  b.vals[0]);
+    const long long nb = (b.nt + kSortTile - 1) / kSortTile;
+    const int passes = (3 * b.morton_bits + 7) / 8;
+    int cur = 0;
+    for (int p = 0; p < passes; ++p) {
+        k_rs_hist<<<(unsigned)nb, kSortThreads, 0, st>>>(b.keys[cur], b.nt, 8 * p, b.hist);
+        k_rs_scan<<<1, 1024, 0, st>>>(b.hist, nb * 256);
+        k_rs_scatter<<<(unsigned)nb, kSortThreads, 0, st>>>(b.keys[cur], b.vals[cur], b.keys[cur ^ 1],
+                                                             b.vals[cur ^ 1], b.nt, 8 * p, b.hist);
+        cur ^= 1;
+    }
+    k_leaves<<<grid_for(1ll << b.L, 256), 256, 0, st>>>(b.verts, b.tris, b.nt, b.L, b.vals[cur], b.tri, b.box);
+    for (int d = b.L - 1; d >= 0; --d) k_reduce_level<<<grid_for(1ll << d, 256), 256, 0, st>>>(b.box, d);
+    return cudaGetLastError();
+}
+
+}  // namespace gd

@@ -1,0 +1,381 @@
+// Device geometry of the distance engine: closest points between triangle
+// features (float32 for the narrow phase, float64 for the refinement) and
+// the AABB distance bounds of Section 4 evaluated against a rigidly mapped
+// box.
+#pragma once
+
+#include <cfloat>
+#include <cmath>
+#include <cuda_runtime.h>
+
+namespace gd {
+
+template <class T>
+struct V3 {
+    T x, y, z;
+};
+
+template <class T>
+__device__ __forceinline__ V3<T> mk3(T x, T y, T z) {
+    return V3<T>{x, y, z};
+}
+template <class T>
+__device__ __forceinline__ V3<T> operator+(V3<T> a, V3<T> b) {
+    return mk3(a.x + b.x, a.y + b.y, a.z + b.z);
+}
+template <class T>
+__device__ __forceinline__ V3<T> operator-(V3<T> a, V3<T> b) {
+    return mk3(a.x - b.x, a.y - b.y, a.z - b.z);
+}
+template <class T>
+__device__ __forceinline__ V3<T> operator*(V3<T> a, T s) {
+    return mk3(a.x * s, a.y * s, a.z * s);
+}
+template <class T>
+__device__ __forceinline__ T dot(V3<T> a, V3<T> b) {
+    return a.x * b.x + a.y * b.y + a.z * b.z;
+}
+template <class T>
+__device__ __forceinline__ V3<T> cross(V3<T> a, V3<T> b) {
+    return mk3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+template <class T>
+__device__ __forceinline__ T clamp01(T s) {
+    return s < T(0) ? T(0) : (s > T(1) ? T(1) : s);
+}
+
+// Closest point to p on the segment a + s d, s in [0, 1].
+template <class T>
+__device__ __forceinline__ V3<T> closest_on_segment(V3<T> p, V3<T> a, V3<T> d) {
+    T dd = dot(d, d);
+    T s = T(0);
+    if (dd > T(0)) s = clamp01(dot(p - a, d) / dd);
+    return a + d * s;
+}
+
+template <class T>
+struct Tiny;
+template <>
+struct Tiny<float> {
+    static constexpr float rel_det = 1e-7f;
+};
+template <>
+struct Tiny<double> {
+    static constexpr double rel_det = 1e-15;
+};
+
+// Closest point to p on triangle (a, b, c).  The projection onto the plane is
+// expressed in the edge basis e0 = b - a, e1 = c - a by solving the 2x2 Gram
+// system; if its barycentric weights lie in the triangle the projection is
+// the answer, otherwise the answer lies on the boundary and is the nearest of
+// the three edge projections.  *inside reports the first case.
+template <class T>
+__device__ __forceinline__ V3<T> closest_on_triangle(V3<T> p, V3<T> a, V3<T> b, V3<T> c, bool* inside) {
+    V3<T> e0 = b - a, e1 = c - a, w = p - a;
+    T g00 = dot(e0, e0), g01 = dot(e0, e1), g11 = dot(e1, e1);
+    T det = g00 * g11 - g01 * g01;
+    if (det > Tiny<T>::rel_det * g00 * g11 && det > T(0)) {
+        T r0 = dot(w, e0), r1 = dot(w, e1);
+        T u = (g11 * r0 - g01 * r1) / det;
+        T v = (g00 * r1 - g01 * r0) / det;
+        if (u >= T(0) && v >= T(0) && u + v <= T(1)) {
+            *inside = true;
+            return a + e0 * u + e1 * v;
+        }
+    }
+    *inside = false;
+    V3<T> q0 = closest_on_segment(p, a, e0);
+    V3<T> q1 = closest_on_segment(p, b, c - b);
+    V3<T> q2 = closest_on_segment(p, a, e1);
+    V3<T> d0 = p - q0, d1 = p - q1, d2 = p - q2;
+    T n0 = dot(d0, d0), n1 = dot(d1, d1), n2 = dot(d2, d2);
+    V3<T> q = q0;
+    T n = n0;
+    if (n1 < n) { n = n1; q = q1; }
+    if (n2 < n) { q = q2; }
+    return q;
+}
+
+// Closest points between segments p0 + s d1 and q0 + t d2, s, t in [0, 1].
+// The squared distance is a convex quadratic in (s, t): take the stationary
+// s (0 for parallel segments), clamp it, put t at its optimum for that s,
+// and if t leaves [0, 1], clamp t and re-optimise s for the clamped t.
+template <class T>
+__device__ __forceinline__ void closest_segment_segment(V3<T> p0, V3<T> d1, V3<T> q0, V3<T> d2, V3<T>* P,
+                                                        V3<T>* Q) {
+    V3<T> r = p0 - q0;
+    T a = dot(d1, d1), e = dot(d2, d2), f = dot(d2, r);
+    T s, t;
+    if (!(a > T(0)) && !(e > T(0))) {
+        s = t = T(0);
+    } else if (!(a > T(0))) {
+        s = T(0);
+        t = clamp01(f / e);
+    } else {
+        T c = dot(d1, r);
+        if (!(e > T(0))) {
+            t = T(0);
+            s = clamp01(-c / a);
+        } else {
+            T b = dot(d1, d2);
+            T den = a * e - b * b;
+            s = den > T(0) ? clamp01((b * f - c * e) / den) : T(0);
+            T tn = b * s + f;
+            if (tn < T(0)) {
+                t = T(0);
+                s = clamp01(-c / a);
+            } else if (tn > e) {
+                t = T(1);
+                s = clamp01((b - c) / a);
+            } else {
+                t = tn / e;
+            }
+        }
+    }
+    *P = p0 + d1 * s;
+    *Q = q0 + d2 * t;
+}
+
+// Minimum distance between closed triangles A and B: the closest pair over the
+// 6 vertex-face and 9 edge-edge feature pairs, plus, for every edge crossing
+// the other triangle's plane, the crossing point against the other triangle
+// (an interior crossing means the triangles intersect).  Returns the best
+// pair (P on A, Q on B), its squared distance, and whether an interior
+// crossing was found.
+template <class T>
+__device__ __forceinline__ void tri_tri_min(const V3<T>* A, const V3<T>* B, V3<T>* Pbest, V3<T>* Qbest, T* d2best,
+                                            bool* hit) {
+    T best = T(INFINITY);
+    V3<T> P = A[0], Q = B[0];
+    bool touched = false;
+    auto consider = [&](V3<T> p, V3<T> q) {
+        V3<T> d = p - q;
+        T n = dot(d, d);
+        if (n < best) { best = n; P = p; Q = q; }
+    };
+    bool in;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        consider(A[i], closest_on_triangle(A[i], B[0], B[1], B[2], &in));
+        consider(closest_on_triangle(B[i], A[0], A[1], A[2], &in), B[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            V3<T> p, q;
+            closest_segment_segment(A[i], A[(i + 1) % 3] - A[i], B[j], B[(j + 1) % 3] - B[j], &p, &q);
+            consider(p, q);
+        }
+    }
+    // edges crossing the other triangle's plane
+    V3<T> nA = cross(A[1] - A[0], A[2] - A[0]);
+    V3<T> nB = cross(B[1] - B[0], B[2] - B[0]);
+    T sa[3], sb[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        sa[i] = dot(nB, A[i] - B[0]);
+        sb[i] = dot(nA, B[i] - A[0]);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        int j = (i + 1) % 3;
+        if ((sa[i] <= T(0) && sa[j] >= T(0)) || (sa[i] >= T(0) && sa[j] <= T(0))) {
+            T den = sa[i] - sa[j];
+            if (den != T(0)) {
+                V3<T> X = A[i] + (A[j] - A[i]) * clamp01(sa[i] / den);
+                V3<T> Y = closest_on_triangle(X, B[0], B[1], B[2], &in);
+                consider(X, Y);
+                if (in) { touched = true; P = X; Q = X; best = T(0); }
+            }
+        }
+        if ((sb[i] <= T(0) && sb[j] >= T(0)) || (sb[i] >= T(0) && sb[j] <= T(0))) {
+            T den = sb[i] - sb[j];
+            if (den != T(0)) {
+                V3<T> X = B[i] + (B[j] - B[i]) * clamp01(sb[i] / den);
+                V3<T> Y = closest_on_triangle(X, A[0], A[1], A[2], &in);
+                consider(Y, X);
+                if (in) { touched = true; P = X; Q = X; best = T(0); }
+            }
+        }
+    }
+    *Pbest = P;
+    *Qbest = Q;
+    *d2best = best;
+    *hit = touched;
+}
+
+// Farthest vertex pair (the maximum over two triangles is attained at vertices).
+template <class T>
+__device__ __forceinline__ void tri_tri_max(const V3<T>* A, const V3<T>* B, V3<T>* P, V3<T>* Q, T* d2) {
+    T best = T(-1);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            V3<T> d = A[i] - B[j];
+            T n = dot(d, d);
+            if (n > best) { best = n; *P = A[i]; *Q = B[j]; }
+        }
+    *d2 = best;
+}
+
+// ---------------------------------------------------------------- transforms
+
+struct Rigid32 {
+    float R[9], t[3];
+};
+
+// float32 map x -> R x + t, one FMA chain per coordinate
+__device__ __forceinline__ V3<float> map32(const Rigid32& X, float x, float y, float z) {
+    return mk3(fmaf(X.R[0], x, fmaf(X.R[1], y, fmaf(X.R[2], z, X.t[0]))),
+               fmaf(X.R[3], x, fmaf(X.R[4], y, fmaf(X.R[5], z, X.t[1]))),
+               fmaf(X.R[6], x, fmaf(X.R[7], y, fmaf(X.R[8], z, X.t[2]))));
+}
+
+__device__ __forceinline__ V3<double> map64(const double* X, double x, double y, double z) {
+    return mk3(fma(X[0], x, fma(X[1], y, fma(X[2], z, X[3]))), fma(X[4], x, fma(X[5], y, fma(X[6], z, X[7]))),
+               fma(X[8], x, fma(X[9], y, fma(X[10], z, X[11]))));
+}
+
+// ---------------------------------------------------------------- bounds
+
+// Box with lo[3], hi[3].
+struct Box {
+    float lo[3], hi[3];
+};
+
+// Axis-aligned box enclosing the mapped box b (centre +- |R| half-extent).
+__device__ __forceinline__ void enclose(const Rigid32& X, const Box& b, float* elo, float* ehi) {
+    float m0 = 0.5f * (b.lo[0] + b.hi[0]), m1 = 0.5f * (b.lo[1] + b.hi[1]), m2 = 0.5f * (b.lo[2] + b.hi[2]);
+    float h0 = 0.5f * (b.hi[0] - b.lo[0]), h1 = 0.5f * (b.hi[1] - b.lo[1]), h2 = 0.5f * (b.hi[2] - b.lo[2]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float c = fmaf(X.R[3 * i], m0, fmaf(X.R[3 * i + 1], m1, fmaf(X.R[3 * i + 2], m2, X.t[i])));
+        float e = fmaf(fabsf(X.R[3 * i]), h0, fmaf(fabsf(X.R[3 * i + 1]), h1, fabsf(X.R[3 * i + 2]) * h2));
+        elo[i] = c - e;
+        ehi[i] = c + e;
+    }
+}
+
+// Eqs. 5-6: squared conventional lower bound of the min distance.
+__device__ __forceinline__ float lower_min_sq(const Box& a, const float* elo, const float* ehi) {
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float g = fmaxf(0.f, fmaxf(a.lo[k] - ehi[k], elo[k] - a.hi[k]));
+        s = fmaf(g, g, s);
+    }
+    return s;
+}
+
+// Eqs. 7-8: squared conventional upper bound of the max distance.
+__device__ __forceinline__ float upper_max_sq(const Box& a, const float* elo, const float* ehi) {
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float f = fmaxf(fabsf(a.lo[k] - ehi[k]), fabsf(a.hi[k] - elo[k]));
+        s = fmaf(f, f, s);
+    }
+    return s;
+}
+
+// Corner m of the mapped box b (bit k of m selects hi on axis k).
+__device__ __forceinline__ V3<float> mapped_corner(const Rigid32& X, const Box& b, int m) {
+    return map32(X, (m & 1) ? b.hi[0] : b.lo[0], (m & 2) ? b.hi[1] : b.lo[1], (m & 4) ? b.hi[2] : b.lo[2]);
+}
+
+// Eq. 10: squared enhanced upper bound of the min distance,
+//   min over faces i of a, faces j of b of max over P in face i, Q in face j of |PQ|.
+// For a fixed corner Q of the mapped face j, the farthest point of the
+// axis-aligned face i (axis k at coordinate f) is at squared distance
+//   (Q_k - f)^2 + sum over the other axes l of max((Q_l - lo_l)^2, (Q_l - hi_l)^2),
+// and the maximum over face j is attained at one of its 4 corners.
+__device__ __forceinline__ float upper_min_sq_enhanced(const Rigid32& X, const Box& a, const Box& b) {
+    float run[6][6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j < 6; ++j) run[i][j] = 0.f;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        V3<float> c = mapped_corner(X, b, m);
+        float cc[3] = {c.x, c.y, c.z};
+        float dl[3], dh[3], M2[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            dl[k] = cc[k] - a.lo[k];
+            dh[k] = cc[k] - a.hi[k];
+            M2[k] = fmaxf(dl[k] * dl[k], dh[k] * dh[k]);
+        }
+        float Pk[3] = {M2[1] + M2[2], M2[0] + M2[2], M2[0] + M2[1]};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                float d = side ? dh[k] : dl[k];
+                float v = fmaf(d, d, Pk[k]);
+                int i = 2 * k + side;
+                // corner m lies on face (axis l, side bit l of m) of b
+#pragma unroll
+                for (int l = 0; l < 3; ++l) {
+                    int j = 2 * l + ((m >> l) & 1);
+                    run[i][j] = fmaxf(run[i][j], v);
+                }
+            }
+        }
+    }
+    float best = FLT_MAX;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j < 6; ++j) best = fminf(best, run[i][j]);
+    return best;
+}
+
+// Eq. 11 (as a valid lower bound): squared lower bound of the max distance,
+//   max over faces i of a, faces j of b of the min distance between face i
+//   and the axis-aligned box enclosing the 4 mapped corners of face j
+//   (that box contains face j, so its distance does not exceed the face's;
+//   with no rotation it is the face itself and the bound is Eq. 11 exactly).
+__device__ __forceinline__ float lower_max_sq_enhanced(const Rigid32& X, const Box& a, const Box& b) {
+    V3<float> c[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) c[m] = mapped_corner(X, b, m);
+    float best = 0.f;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+#pragma unroll
+        for (int sl = 0; sl < 2; ++sl) {
+            float flo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, fhi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                if (((m >> l) & 1) != sl) continue;
+                float cc[3] = {c[m].x, c[m].y, c[m].z};
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    flo[k] = fminf(flo[k], cc[k]);
+                    fhi[k] = fmaxf(fhi[k], cc[k]);
+                }
+            }
+            // per-axis gaps between a's full extent and the face box
+            float g[3], gf[3][2];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                g[k] = fmaxf(0.f, fmaxf(a.lo[k] - fhi[k], flo[k] - a.hi[k]));
+                gf[k][0] = fmaxf(0.f, fmaxf(a.lo[k] - fhi[k], flo[k] - a.lo[k]));
+                gf[k][1] = fmaxf(0.f, fmaxf(a.hi[k] - fhi[k], flo[k] - a.hi[k]));
+            }
+            float g2[3] = {g[0] * g[0], g[1] * g[1], g[2] * g[2]};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                float o = g2[(k + 1) % 3] + g2[(k + 2) % 3];
+#pragma unroll
+                for (int s = 0; s < 2; ++s) best = fmaxf(best, fmaf(gf[k][s], gf[k][s], o));
+            }
+        }
+    }
+    return best;
+}
+
+}  // namespace gd

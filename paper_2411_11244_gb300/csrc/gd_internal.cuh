@@ -1,0 +1,190 @@
+// Internal device-side declarations of the GB300 distance engine.
+//
+// Data layout in HBM (one mesh, T triangles, L = floor(log2 T), 2^L leaves):
+//   box  : float[6 * 2^(L+1)], node i (heap order, root 1, children 2i, 2i+1)
+//          at box[6i .. 6i+5] = (lo.x, lo.y, lo.z, hi.x, hi.y, hi.z); entry 0
+//          unused.  Implicit full binary tree with boxes only (Section 7.3).
+//   tri  : float4[3 * T] in leaf (Morton) order, triangle j at tri[3j..3j+2] =
+//          (v0x v0y v0z v1x) (v1y v1z v2x v2y) (v2z id 0 0), id = the caller's
+//          original index stored as int bits.
+//   leaf l owns sorted triangles [floor(l T / 2^L), floor((l+1) T / 2^L)):
+//          one or two each, no per-leaf storage (the f12 rule of Section 7.3).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/gdist.h"
+
+namespace gd {
+
+constexpr int kBlock = 256;          // threads per CTA of the persistent kernels
+constexpr int kMaxLevels = 64;       // BVTT expansion levels per launch
+constexpr unsigned kFull = 0xffffffffu;
+
+struct MeshDev {
+    const float* box;    // 6 floats per node
+    const float4* tri;   // 3 float4 per triangle, leaf order
+    long long T;         // triangles
+    int L;               // leaves = 2^L
+    float P;             // max |coordinate| over referenced vertices (exact)
+};
+
+// one BVTT front entry (Section 5): two node ids, the stored bound used to
+// re-cull the entry against the running bound, and the query it belongs to
+struct __align__(16) Item {
+    uint32_t a, b;
+    float bound;
+    uint32_t q;
+};
+
+// a triangle pair kept for float64 refinement (sorted triangle ids)
+struct __align__(16) Cand {
+    uint32_t ta, tb;
+    float bound;
+    uint32_t q;
+};
+
+struct QIn {
+    const MeshDev* A;
+    const MeshDev* B;
+    double xa[12], xb[12];
+};
+
+// per-query running state and derived constants
+struct __align__(16) QState {
+    unsigned U;                   // running bound, float bits (min: upper of
+                                  // D_min, atomicMin; max: lower of D_max, atomicMax)
+    unsigned status;              // kStat* bits
+    unsigned long long best_d;    // float64 bits of the refined extreme
+    unsigned long long best_key;  // (orig a << 32 | orig b) of the witness
+    float R[9], t[3];             // B-local -> A-local, float32
+    float E_box, E_tri;           // absolute widening of box / triangle bounds
+    const MeshDev* A;
+    const MeshDev* B;
+    double xa[12], xb[12];
+};
+
+constexpr unsigned kStatOverflow = 1u, kStatTimeout = 2u, kStatNoResult = 4u;
+
+// global counters, one uint32 array per context
+enum : int {
+    kCtrCnt = 0,      // [0..2] front entry counts, triple-buffered by level
+    kCtrRem = 3,      // [3..5] max remaining depth of the entries of that front
+    kCtrLeaf = 6,     // leaf-pair count
+    kCtrCand = 7,     // candidate count
+    kCtrOverflow = 9, // some push exceeded its capacity
+    kCtrReset = 16,   // counters [0, kCtrReset) are cleared at kernel start
+    kCtrAbort = 20,   // a wait gave up: every CTA leaves at its next barrier
+    kCtrLastAbort = 21, // the abort flag of the last finished launch
+    kCtrExit = 22,    // CTAs that left the kernel (the last one resets the barrier)
+    kCtrBarCount = 32,
+    kCtrBarGen = 33,
+    kCtrWords = 64,
+};
+
+struct StatsDev {
+    unsigned levels;
+    unsigned front[32];
+    unsigned slots[32];
+    unsigned long long pairs_tested;
+    unsigned leaf_pairs, tri_pairs, candidates, refined;
+    unsigned long long alg_bytes;
+};
+
+struct KArgs {
+    int nq;
+    const QIn* qin;             // batch: per-query meshes and transforms
+    const MeshDev* mA;          // single query (qin == nullptr)
+    const MeshDev* mB;
+    const double* xa_src;       // single query: device transforms, or nullptr
+    const double* xb_src;       //   to use xa_val / xb_val below
+    double xa_val[12], xb_val[12];
+    QState* qs;
+    Item* front0;
+    Item* front1;
+    unsigned cap_front;
+    Item* leafq;
+    unsigned cap_leaf;
+    Cand* cand;
+    double* cand_d;
+    unsigned cap_cand;
+    unsigned* ctr;
+    StatsDev* stats;
+    gd_result* out;
+    long long work_target;
+    int k_max;
+    long long timeout_ns;
+};
+
+// ------------------------------------------------------------------ memory
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident).  Every
+// wait is bounded: after timeout_ns the CTA raises the abort flag and returns
+// false, and every other CTA returns false at its next barrier.
+__device__ __forceinline__ bool grid_sync(const KArgs& A) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned* count = A.ctr + kCtrBarCount;
+        unsigned* gen = A.ctr + kCtrBarGen;
+        unsigned* abort_flag = A.ctr + kCtrAbort;
+        unsigned g = ld_acquire(gen);
+        __threadfence();
+        unsigned arrived = atomicAdd(count, 1u);
+        int ok = 1;
+        if (arrived == gridDim.x - 1) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            unsigned long long t0 = globaltimer();
+            while (ld_acquire(gen) == g) {
+                if (ld_relaxed(abort_flag)) { ok = 0; break; }
+                if ((long long)(globaltimer() - t0) > A.timeout_ns) {
+                    atomicExch(abort_flag, 1u);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        if (ld_acquire(abort_flag)) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+}  // namespace gd

@@ -1,0 +1,281 @@
+"""ctypes binding of the engine's C ABI (include/gdist.h).
+
+Argument marshalling only: every function forwards to the function of the same
+name in libgdist.so, and every step of the computation runs in the library's
+CUDA kernels.  There is no CPU fallback: if the library is missing or no CUDA
+device is present, the calls raise.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libgdist.so")
+
+GD_OK, GD_ERR_INVALID_ARG, GD_ERR_OOM, GD_ERR_CUDA, GD_ERR_NOT_BUILT = 0, 1, 2, 3, 4
+GD_ERR_OVERFLOW, GD_ERR_TIMEOUT, GD_ERR_BUSY, GD_ERR_NOT_READY = 5, 6, 7, 8
+GD_MIN, GD_MAX = 0, 1
+STATUS_NAMES = {
+    0: "GD_OK", 1: "GD_ERR_INVALID_ARG", 2: "GD_ERR_OOM", 3: "GD_ERR_CUDA", 4: "GD_ERR_NOT_BUILT",
+    5: "GD_ERR_OVERFLOW", 6: "GD_ERR_TIMEOUT", 7: "GD_ERR_BUSY", 8: "GD_ERR_NOT_READY",
+}
+
+# every symbol include/gdist.h declares
+EXPORTS = [
+    "gd_ctx_create", "gd_ctx_destroy", "gd_last_error", "gd_ctx_set_tunables", "gd_ctx_get_tunables",
+    "gd_get_stats", "gd_ctx_stream", "gd_mesh_create", "gd_bvh_build", "gd_mesh_destroy", "gd_mesh_info",
+    "gd_mesh_download", "gd_min_distance", "gd_max_distance", "gd_query_device", "gd_batch_query",
+    "gd_serve_start", "gd_serve_submit", "gd_serve_poll", "gd_serve_stop",
+]
+
+
+class gd_result(C.Structure):
+    _fields_ = [("d", C.c_double), ("tri_a", C.c_int64), ("tri_b", C.c_int64), ("pa", C.c_double * 3),
+                ("pb", C.c_double * 3), ("status", C.c_uint32), ("flags", C.c_uint32)]
+
+    def as_dict(self):
+        return {"d": self.d, "tri_a": self.tri_a, "tri_b": self.tri_b, "pa": list(self.pa), "pb": list(self.pb),
+                "status": self.status, "flags": self.flags}
+
+
+class gd_query(C.Structure):
+    _fields_ = [("a", C.c_void_p), ("b", C.c_void_p), ("xa", C.c_double * 12), ("xb", C.c_double * 12),
+                ("kind", C.c_int), ("user_tag", C.c_uint64)]
+
+
+class gd_build_opts(C.Structure):
+    _fields_ = [("morton_bits", C.c_int)]
+
+
+class gd_tunables(C.Structure):
+    _fields_ = [("work_target", C.c_int64), ("k_max", C.c_int32), ("blocks_per_sm", C.c_int32),
+                ("front_capacity", C.c_int64), ("leaf_capacity", C.c_int64), ("cand_capacity", C.c_int64),
+                ("max_capacity", C.c_int64), ("timeout_ns", C.c_int64)]
+
+
+class gd_stats(C.Structure):
+    _fields_ = [("levels", C.c_uint32), ("front", C.c_uint32 * 32), ("slots", C.c_uint32 * 32),
+                ("pairs_tested", C.c_uint64), ("leaf_pairs", C.c_uint32), ("tri_pairs", C.c_uint32),
+                ("candidates", C.c_uint32), ("refined", C.c_uint32), ("alg_bytes", C.c_uint64),
+                ("retries", C.c_uint32), ("blocks", C.c_uint32)]
+
+    def as_dict(self):
+        n = self.levels
+        return {"levels": n, "front": list(self.front[:min(n, 32)]), "slots": list(self.slots[:min(n, 32)]),
+                "pairs_tested": self.pairs_tested, "leaf_pairs": self.leaf_pairs, "tri_pairs": self.tri_pairs,
+                "candidates": self.candidates, "refined": self.refined, "alg_bytes": self.alg_bytes,
+                "retries": self.retries, "blocks": self.blocks}
+
+
+class gd_serve_opts(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("max_batch", C.c_int32), ("memory_budget", C.c_int64),
+                ("linger_us", C.c_int32)]
+
+
+_lib = None
+_vp = C.c_void_p
+_dp = C.POINTER(C.c_double)
+
+
+def load(path: str = LIB_PATH):
+    """Load libgdist.so (raises if it was not built: run __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA engine library missing: {path} (build it with __graft_entry__.build())")
+    L = C.CDLL(path)
+    sig = {
+        "gd_ctx_create": (C.c_int, [C.c_int, C.POINTER(_vp)]),
+        "gd_ctx_destroy": (None, [_vp]),
+        "gd_last_error": (C.c_char_p, [_vp]),
+        "gd_ctx_set_tunables": (C.c_int, [_vp, C.POINTER(gd_tunables)]),
+        "gd_ctx_get_tunables": (C.c_int, [_vp, C.POINTER(gd_tunables)]),
+        "gd_get_stats": (C.c_int, [_vp, C.POINTER(gd_stats)]),
+        "gd_ctx_stream": (_vp, [_vp]),
+        "gd_mesh_create": (C.c_int, [_vp, C.POINTER(C.c_float), C.c_int64, C.POINTER(C.c_int32), C.c_int64,
+                                     C.POINTER(_vp)]),
+        "gd_bvh_build": (C.c_int, [_vp, C.POINTER(gd_build_opts)]),
+        "gd_mesh_destroy": (None, [_vp]),
+        "gd_mesh_info": (C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
+        "gd_mesh_download": (C.c_int, [_vp, C.POINTER(C.c_float), C.POINTER(C.c_int32)]),
+        "gd_min_distance": (C.c_int, [_vp, _vp, _vp, _dp, _dp, C.POINTER(gd_result)]),
+        "gd_max_distance": (C.c_int, [_vp, _vp, _vp, _dp, _dp, C.POINTER(gd_result)]),
+        "gd_query_device": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp, _vp, _vp, _vp]),
+        "gd_batch_query": (C.c_int, [_vp, C.POINTER(gd_query), C.c_int64, C.POINTER(gd_result)]),
+        "gd_serve_start": (C.c_int, [_vp, C.POINTER(gd_serve_opts), C.POINTER(_vp)]),
+        "gd_serve_submit": (C.c_int, [_vp, C.POINTER(gd_query), C.POINTER(C.c_uint64)]),
+        "gd_serve_poll": (C.c_int, [_vp, C.c_uint64, C.POINTER(gd_result)]),
+        "gd_serve_stop": (C.c_int, [_vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+class GdError(RuntimeError):
+    def __init__(self, status, msg=""):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(rc, ctx=None):
+    if rc != GD_OK:
+        msg = load().gd_last_error(ctx).decode() if ctx else ""
+        raise GdError(rc, msg)
+
+
+def _x(a):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(12))
+    return a
+
+
+# ------------------------------------------------------------- same-name wrappers
+
+def gd_ctx_create(device: int = 0):
+    h = _vp()
+    _check(load().gd_ctx_create(device, C.byref(h)))
+    return h.value
+
+
+def gd_ctx_destroy(ctx):
+    load().gd_ctx_destroy(ctx)
+
+
+def gd_last_error(ctx) -> str:
+    return load().gd_last_error(ctx).decode()
+
+
+def gd_ctx_set_tunables(ctx, **kw):
+    t = gd_tunables()
+    for k, v in kw.items():
+        setattr(t, k, int(v))
+    _check(load().gd_ctx_set_tunables(ctx, C.byref(t)), ctx)
+
+
+def gd_ctx_get_tunables(ctx) -> dict:
+    t = gd_tunables()
+    _check(load().gd_ctx_get_tunables(ctx, C.byref(t)), ctx)
+    return {f: getattr(t, f) for f, _ in gd_tunables._fields_}
+
+
+def gd_get_stats(ctx) -> dict:
+    s = gd_stats()
+    _check(load().gd_get_stats(ctx, C.byref(s)), ctx)
+    return s.as_dict()
+
+
+def gd_ctx_stream(ctx) -> int:
+    return load().gd_ctx_stream(ctx) or 0
+
+
+def gd_mesh_create(ctx, verts, tris):
+    v = np.ascontiguousarray(np.asarray(verts, dtype=np.float32).reshape(-1, 3))
+    t = np.ascontiguousarray(np.asarray(tris, dtype=np.int32).reshape(-1, 3))
+    h = _vp()
+    rc = load().gd_mesh_create(ctx, v.ctypes.data_as(C.POINTER(C.c_float)), len(v),
+                               t.ctypes.data_as(C.POINTER(C.c_int32)), len(t), C.byref(h))
+    _check(rc, ctx)
+    return h.value
+
+
+def gd_bvh_build(mesh, morton_bits: int | None = None, ctx=None):
+    o = None
+    if morton_bits is not None:
+        o = C.byref(gd_build_opts(int(morton_bits)))
+    _check(load().gd_bvh_build(mesh, o), ctx)
+
+
+def gd_mesh_destroy(mesh):
+    load().gd_mesh_destroy(mesh)
+
+
+def gd_mesh_info(mesh):
+    L = C.c_int32()
+    T = C.c_int64()
+    _check(load().gd_mesh_info(mesh, C.byref(L), C.byref(T)))
+    return L.value, T.value
+
+
+def gd_mesh_download(mesh):
+    L, T = gd_mesh_info(mesh)
+    boxes = np.zeros((2 << L, 6), dtype=np.float32)
+    order = np.zeros(T, dtype=np.int32)
+    _check(load().gd_mesh_download(mesh, boxes.ctypes.data_as(C.POINTER(C.c_float)),
+                                   order.ctypes.data_as(C.POINTER(C.c_int32))))
+    return boxes, order
+
+
+def _query(fn, ctx, A, B, xa, xb):
+    xa, xb = _x(xa), _x(xb)
+    r = gd_result()
+    rc = fn(ctx, A, B, xa.ctypes.data_as(_dp), xb.ctypes.data_as(_dp), C.byref(r))
+    _check(rc, ctx)
+    return r
+
+
+def gd_min_distance(ctx, A, B, xa, xb) -> gd_result:
+    return _query(load().gd_min_distance, ctx, A, B, xa, xb)
+
+
+def gd_max_distance(ctx, A, B, xa, xb) -> gd_result:
+    return _query(load().gd_max_distance, ctx, A, B, xa, xb)
+
+
+def gd_query_device(ctx, A, B, kind: int, d_xa: int, d_xb: int, d_out: int, stream: int = 0):
+    """Device-resident query: d_xa, d_xb, d_out are device addresses (ints)."""
+    _check(load().gd_query_device(ctx, A, B, int(kind), d_xa, d_xb, d_out, stream or None), ctx)
+
+
+def make_queries(items):
+    """items: iterable of (meshA, meshB, xa, xb, kind[, tag]) -> ctypes array of gd_query."""
+    items = list(items)
+    arr = (gd_query * len(items))()
+    for i, it in enumerate(items):
+        a, b, xa, xb, kind = it[:5]
+        arr[i].a = a
+        arr[i].b = b
+        arr[i].xa[:] = list(_x(xa))
+        arr[i].xb[:] = list(_x(xb))
+        arr[i].kind = int(kind)
+        arr[i].user_tag = int(it[5]) if len(it) > 5 else i
+    return arr
+
+
+def gd_batch_query(ctx, queries):
+    if not isinstance(queries, C.Array):
+        queries = make_queries(queries)
+    n = len(queries)
+    out = (gd_result * n)()
+    _check(load().gd_batch_query(ctx, queries, n, out), ctx)
+    return out
+
+
+def gd_serve_start(ctx, slots=0, max_batch=0, memory_budget=0, linger_us=0):
+    o = gd_serve_opts(int(slots), int(max_batch), int(memory_budget), int(linger_us))
+    h = _vp()
+    _check(load().gd_serve_start(ctx, C.byref(o), C.byref(h)), ctx)
+    return h.value
+
+
+def gd_serve_submit(srv, query: gd_query):
+    t = C.c_uint64()
+    rc = load().gd_serve_submit(srv, C.byref(query), C.byref(t))
+    return rc, t.value
+
+
+def gd_serve_poll(srv, ticket):
+    r = gd_result()
+    rc = load().gd_serve_poll(srv, C.c_uint64(ticket), C.byref(r))
+    return rc, r
+
+
+def gd_serve_stop(srv):
+    _check(load().gd_serve_stop(srv))

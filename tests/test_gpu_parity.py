@@ -1,0 +1,394 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerance (Section 3 problem, float32 traversal + float64 refinement):
+  |d - d_ref| <= 1e-6 x diag, diag = world bounding-box diagonal of both meshes;
+  the oracle's float64 distance of the returned witness pair equals d_ref
+  within 1e-12 relative (+1e-15 x diag absolute for rounding at d ~ 0);
+  the returned d equals that witness distance to the same tolerance.
+Integer work (the BVH build's triangle order) is compared bit for bit.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+from paper_2411_11244_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2411_11244_gb300 import gdist
+    return gdist
+
+
+@pytest.fixture(scope="module")
+def ctx(G):
+    c = G.gd_ctx_create(0)
+    yield c
+    G.gd_ctx_destroy(c)
+
+
+def _mesh(G, ctx, m):
+    h = G.gd_mesh_create(ctx, *m)
+    G.gd_bvh_build(h, ctx=ctx)
+    return h
+
+
+def check(r, A, xa, B, xb, kind, ref, diag, oracle):
+    assert r.status == 0, r.status
+    assert abs(r.d - ref.d) <= 1e-6 * diag, (kind, r.d, ref.d)
+    dw, _, _ = oracle.witness_distance(A, xa, B, xb, r.tri_a, r.tri_b, kind)
+    tol = 1e-12 * abs(ref.d) + 1e-15 * diag
+    assert abs(dw - ref.d) <= tol, (kind, dw, ref.d, (r.tri_a, r.tri_b), (ref.ta, ref.tb))
+    assert abs(r.d - dw) <= tol, (kind, r.d, dw)
+    pa, pb = np.array(r.pa[:]), np.array(r.pb[:])
+    assert abs(np.linalg.norm(pa - pb) - r.d) <= 1e-12 * max(r.d, 1.0) + 1e-15 * diag
+    wa = oracle.world_vertices(A, xa)[np.asarray(A[1])[r.tri_a]]
+    wb = oracle.world_vertices(B, xb)[np.asarray(B[1])[r.tri_b]]
+    assert oracle.point_triangle(pa, *wa)[0] <= 1e-12 * diag
+    assert oracle.point_triangle(pb, *wb)[0] <= 1e-12 * diag
+    assert (r.flags & 1) == (1 if r.d == 0.0 else 0)
+
+
+def run_pair(G, ctx, oracle, A, B, xforms, kinds=("min", "max"), bvh_oracle=False):
+    ma, mb = _mesh(G, ctx, A), _mesh(G, ctx, B)
+    oa = ob = None
+    if bvh_oracle:
+        oa = oracle.Bvh(A)
+        ob = oa if B is A else oracle.Bvh(B)
+    try:
+        for xa, xb in xforms:
+            diag = oracle.diag(A, xa, B, xb)
+            for kind in kinds:
+                fn = G.gd_min_distance if kind == "min" else G.gd_max_distance
+                r = fn(ctx, ma, mb, xa, xb)
+                ref = oracle.bvh_query(oa, xa, ob, xb, kind) if bvh_oracle else oracle.brute(A, xa, B, xb, kind)
+                check(r, A, xa, B, xb, kind, ref, diag, oracle)
+    finally:
+        G.gd_mesh_destroy(ma)
+        G.gd_mesh_destroy(mb)
+
+
+def _rigid(rng, scale=1.0):
+    return synth.xform(synth.random_rotation(rng), rng.normal(size=3) * scale)
+
+
+def _soup(rng, n, spread=1.0):
+    v = rng.uniform(-spread, spread, (3 * n, 3)).astype(np.float32)
+    return v, np.arange(3 * n, dtype=np.int32).reshape(n, 3)
+
+
+# ------------------------------------------------------------------ BVH build
+
+def _morton_np(v, t, bits=21):
+    v = np.asarray(v, dtype=np.float32)
+    used = v[np.unique(t)]
+    lo = used.min(0)
+    hi = used.max(0)
+    ext = (hi - lo).astype(np.float32)
+    s = (v[t[:, 0]] + v[t[:, 1]]).astype(np.float32) + v[t[:, 2]]
+    x = (s * np.float32(1.0 / 3.0)).astype(np.float32) - lo
+    cells = np.float32(1 << bits)
+    top = (1 << bits) - 1
+    with np.errstate(divide="ignore", invalid="ignore"):
+        f = np.where(ext > 0, (x / np.where(ext > 0, ext, 1)).astype(np.float32) * cells, np.float32(0))
+    f = f.astype(np.float32)
+    q = np.where(f <= 0, 0, np.where(f >= top, top, np.floor(np.maximum(f, 0)))).astype(np.uint64)
+
+    def spread(a):
+        out = np.zeros_like(a)
+        for i in range(bits):
+            out |= ((a >> np.uint64(i)) & np.uint64(1)) << np.uint64(3 * i)
+        return out
+
+    return spread(q[:, 0]) | (spread(q[:, 1]) << np.uint64(1)) | (spread(q[:, 2]) << np.uint64(2))
+
+
+@pytest.mark.parametrize("case", ["torus", "sphere", "soup", "t1", "t2", "t3", "t5", "gear"])
+def test_bvh_build_structure(G, ctx, case):
+    rng = np.random.default_rng(4)
+    m = {
+        "torus": lambda: synth.torus(1.0, 0.3, 32, 32),
+        "sphere": lambda: synth.geosphere(7, 1.0, 1e-3, 2),
+        "soup": lambda: _soup(rng, 1000),
+        "t1": lambda: _soup(rng, 1),
+        "t2": lambda: _soup(rng, 2),
+        "t3": lambda: _soup(rng, 3),
+        "t5": lambda: _soup(rng, 5),
+        "gear": lambda: synth.gear(96, 3, teeth=12, seed=1),
+    }[case]()
+    v, t = m
+    h = _mesh(G, ctx, m)
+    try:
+        L, T = G.gd_mesh_info(h)
+        assert T == len(t) and (1 << L) <= T < (2 << L)
+        boxes, order = G.gd_mesh_download(h)
+        # stable Morton order, bit for bit
+        keys = _morton_np(v, t)
+        assert np.array_equal(order, np.argsort(keys, kind="stable").astype(np.int32))
+        # leaves: exact bounds of their one or two triangles
+        vt = np.asarray(v, dtype=np.float32)[np.asarray(t)[order]]  # (T, 3, 3) in leaf order
+        for leaf in range(1 << L):
+            s, e = (leaf * T) >> L, ((leaf + 1) * T) >> L
+            assert 1 <= e - s <= 2
+            pts = vt[s:e].reshape(-1, 3)
+            b = boxes[(1 << L) + leaf]
+            assert np.array_equal(b[:3], pts.min(0)) and np.array_equal(b[3:], pts.max(0))
+        # internal nodes: unions of their children (hence tight)
+        for i in range(1, 1 << L):
+            l, r = boxes[2 * i], boxes[2 * i + 1]
+            assert np.array_equal(boxes[i][:3], np.minimum(l[:3], r[:3]))
+            assert np.array_equal(boxes[i][3:], np.maximum(l[3:], r[3:]))
+    finally:
+        G.gd_mesh_destroy(h)
+
+
+def test_bvh_build_rejects_bad_input(G, ctx):
+    v = np.zeros((3, 3), np.float32)
+    t = np.array([[0, 1, 3]], np.int32)
+    h = G.gd_mesh_create(ctx, v, t)
+    with pytest.raises(G.GdError) as e:
+        G.gd_bvh_build(h, ctx=ctx)
+    assert e.value.status == G.GD_ERR_INVALID_ARG
+    G.gd_mesh_destroy(h)
+    v = np.array([[0, 0, 0], [1, 0, 0], [0, np.nan, 0]], np.float32)
+    h = G.gd_mesh_create(ctx, v, np.array([[0, 1, 2]], np.int32))
+    with pytest.raises(G.GdError):
+        G.gd_bvh_build(h, ctx=ctx)
+    G.gd_mesh_destroy(h)
+    with pytest.raises(G.GdError):
+        G.gd_min_distance(ctx, None, None, synth.identity_xform(), synth.identity_xform())
+
+
+# ------------------------------------------------------------------ queries
+
+def test_two_tori_min_max(G, ctx, oracle_mod):
+    import json
+    import os
+    seed = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "tori_seed.json")))["seed"]
+    A, B, xa, xb = synth.config_tori(seed)
+    run_pair(G, ctx, oracle_mod, A, B, [(xa, xb)])
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_random_pairs(G, ctx, oracle_mod, seed):
+    rng = np.random.default_rng(1000 + seed)
+    kinds = [
+        lambda: synth.torus(1.0, 0.25, 20 + seed, 13),
+        lambda: synth.geosphere(5 + seed, 0.7, 2e-3, seed),
+        lambda: _soup(rng, 300 + 77 * seed, 0.8),
+        lambda: synth.gear(128, 3, teeth=16, seed=seed),
+    ]
+    A = kinds[seed % 4]()
+    B = kinds[(seed + 2) % 4]()
+    xs = []
+    for k in range(6):
+        xa = _rigid(rng)
+        off = synth.xform(np.eye(3), rng.normal(size=3) * (0.4 + 0.5 * k))
+        xb = synth.compose(off, synth.compose(xa, synth.xform(synth.random_rotation(rng), (0, 0, 0))))
+        xs.append((xa, xb))
+    run_pair(G, ctx, oracle_mod, A, B, xs)
+
+
+def test_edge_cases(G, ctx, oracle_mod):
+    rng = np.random.default_rng(9)
+    I = synth.identity_xform()
+    one = _soup(rng, 1)
+    two = _soup(rng, 2)
+    torus = synth.torus(1.0, 0.3, 16, 12)
+    # single triangles, tiny meshes, ragged leaf counts
+    run_pair(G, ctx, oracle_mod, one, one, [(I, synth.xform(np.eye(3), (3, 0, 0))), (I, I)])
+    run_pair(G, ctx, oracle_mod, one, torus, [(I, synth.xform(np.eye(3), (0.5, 0.2, 2)))])
+    run_pair(G, ctx, oracle_mod, two, _soup(rng, 7), [(_rigid(rng), _rigid(rng)) for _ in range(3)])
+    # identical placement: intersecting, d = 0
+    run_pair(G, ctx, oracle_mod, torus, torus, [(I, I)], kinds=("min",))
+    # far apart (large coordinates)
+    run_pair(G, ctx, oracle_mod, torus, torus, [(I, synth.xform(synth.random_rotation(rng), (1e3, -2e3, 5e2)))])
+    # nested spheres: the inner one is strictly inside, surface distance > 0
+    run_pair(G, ctx, oracle_mod, synth.geosphere(6, 1.0), synth.geosphere(5, 0.5), [(I, I)])
+    # degenerate (zero-area) triangles
+    v = np.array([[0, 0, 0], [1, 0, 0], [2, 0, 0], [0, 1, 0], [0, 2, 0]], np.float32)
+    degen = (v, np.array([[0, 1, 2], [0, 3, 4], [1, 1, 1]], np.int32))
+    run_pair(G, ctx, oracle_mod, degen, torus, [(I, synth.xform(np.eye(3), (0.3, 0.1, 1.0)))])
+
+
+def test_closed_forms_on_gpu(G, ctx, oracle_mod):
+    g = 0.0625
+    A = synth.box((0, 0, 0), (1, 1, 1))
+    B = synth.box((1 + g, 0.25, 0.5), (2 + g, 0.75, 1.5))
+    I = synth.identity_xform()
+    ma, mb = _mesh(G, ctx, A), _mesh(G, ctx, B)
+    r = G.gd_min_distance(ctx, ma, mb, I, I)
+    assert r.d == pytest.approx(g, abs=1e-12)
+    r = G.gd_max_distance(ctx, ma, mb, I, I)
+    assert r.d == pytest.approx(math.sqrt((2 + g) ** 2 + 0.75 ** 2 + 1.5 ** 2), rel=1e-13)
+    G.gd_mesh_destroy(ma)
+    G.gd_mesh_destroy(mb)
+    gz = 0.01
+    A = synth.grid(24, 1.0, 0.0)
+    B = synth.grid(24, 1.0, gz, x0=0.3, y0=0.25)
+    run_pair(G, ctx, oracle_mod, A, B, [(I, I)])
+
+
+def test_icospheres_small(G, ctx, oracle_mod):
+    A, B, xa, xb = synth.config_icospheres(level=4, seed=3)
+    run_pair(G, ctx, oracle_mod, A, B, [(xa, xb)], bvh_oracle=True)
+
+
+def test_batch_matches_single(G, ctx, oracle_mod):
+    rng = np.random.default_rng(77)
+    A = synth.gear(256, 4, teeth=16, seed=2)
+    B = synth.geosphere(9, 0.5, 1e-3, 5)
+    ma, mb = _mesh(G, ctx, A), _mesh(G, ctx, B)
+    mt = _mesh(G, ctx, synth.torus(1.0, 0.2, 24, 10))
+    items = []
+    for i in range(40):
+        xa = _rigid(rng, 0.2)
+        xb = _rigid(rng, 1.2)
+        pair = [(ma, mb), (mb, mt), (mt, ma)][i % 3]
+        items.append((pair[0], pair[1], xa, xb, i % 2))
+    out = G.gd_batch_query(ctx, items)
+    for i, (a, b, xa, xb, kind) in enumerate(items):
+        fn = G.gd_min_distance if kind == 0 else G.gd_max_distance
+        r = fn(ctx, a, b, xa, xb)
+        assert out[i].status == 0
+        assert out[i].d == r.d
+        assert (out[i].tri_a, out[i].tri_b) == (r.tri_a, r.tri_b)
+    for h in (ma, mb, mt):
+        G.gd_mesh_destroy(h)
+
+
+def test_device_resident_query(G, ctx, oracle_mod):
+    torch = pytest.importorskip("torch")
+    A, B, xa, xb = synth.config_tori(1)
+    ma, mb = _mesh(G, ctx, A), _mesh(G, ctx, B)
+    ref = G.gd_min_distance(ctx, ma, mb, xa, xb)
+    dxa = torch.tensor(xa, dtype=torch.float64, device="cuda")
+    dxb = torch.tensor(xb, dtype=torch.float64, device="cuda")
+    out = torch.zeros(10, dtype=torch.float64, device="cuda")  # 80 bytes
+    stream = torch.cuda.current_stream().cuda_stream
+    G.gd_query_device(ctx, ma, mb, G.GD_MIN, dxa.data_ptr(), dxb.data_ptr(), out.data_ptr(), stream)
+    torch.cuda.synchronize()
+    raw = out.cpu().numpy().tobytes()
+    r = G.gd_result.from_buffer_copy(raw)
+    assert r.status == 0 and r.d == ref.d and (r.tri_a, r.tri_b) == (ref.tri_a, ref.tri_b)
+    G.gd_mesh_destroy(ma)
+    G.gd_mesh_destroy(mb)
+
+
+def test_overflow_grows_then_reports(G, oracle_mod):
+    """Capacity faults are injected on the host: tiny queues must grow and
+    still give the oracle's answer; a growth limit below the need reports
+    GD_ERR_OVERFLOW."""
+    c = G.gd_ctx_create(0)
+    try:
+        A = synth.torus(1.0, 0.3, 32, 32)
+        I = synth.identity_xform()
+        xb = synth.xform(np.eye(3), (0.4, 0.0, 0.0))  # heavy overlap: large fronts
+        ma, mb = _mesh(G, c, A), _mesh(G, c, A)
+        G.gd_ctx_set_tunables(c, front_capacity=64, leaf_capacity=64, cand_capacity=16, max_capacity=1 << 24)
+        r = G.gd_min_distance(c, ma, mb, I, xb)
+        ref = oracle_mod.brute(A, I, A, xb)
+        check(r, A, I, A, xb, "min", ref, oracle_mod.diag(A, I, A, xb), oracle_mod)
+        assert G.gd_get_stats(c)["retries"] > 0
+        G.gd_ctx_set_tunables(c, front_capacity=64, leaf_capacity=64, cand_capacity=16, max_capacity=128)
+        with pytest.raises(G.GdError) as e:
+            G.gd_min_distance(c, ma, mb, I, xb)
+        assert e.value.status == G.GD_ERR_OVERFLOW
+        G.gd_mesh_destroy(ma)
+        G.gd_mesh_destroy(mb)
+    finally:
+        G.gd_ctx_destroy(c)
+
+
+def test_wait_timeout_returns_status_and_context_survives(G, oracle_mod):
+    """A 1 ns bound on every grid-barrier wait makes the waits run out: the
+    kernel returns early, the call reports GD_ERR_TIMEOUT, and the same
+    context answers correctly once the bound is restored."""
+    c = G.gd_ctx_create(0)
+    try:
+        A, B, xa, xb = synth.config_tori(1)
+        ma, mb = _mesh(G, c, A), _mesh(G, c, B)
+        G.gd_ctx_set_tunables(c, timeout_ns=1)
+        saw_timeout = False
+        for _ in range(5):
+            try:
+                G.gd_min_distance(c, ma, mb, xa, xb)
+            except G.GdError as e:
+                assert e.status == G.GD_ERR_TIMEOUT
+                saw_timeout = True
+                break
+        assert saw_timeout
+        G.gd_ctx_set_tunables(c, timeout_ns=2_000_000_000)
+        r = G.gd_min_distance(c, ma, mb, xa, xb)
+        ref = oracle_mod.brute(A, xa, B, xb)
+        check(r, A, xa, B, xb, "min", ref, oracle_mod.diag(A, xa, B, xb), oracle_mod)
+        G.gd_mesh_destroy(ma)
+        G.gd_mesh_destroy(mb)
+    finally:
+        G.gd_ctx_destroy(c)
+
+
+def test_serve_alone_equals_in_mix(G, ctx, oracle_mod):
+    import time
+    rng = np.random.default_rng(5)
+    meshes = [synth.torus(1.0, 0.25, 40, 20), synth.geosphere(12, 0.6, 1e-3, 1), synth.gear(256, 4, teeth=16, seed=3)]
+    hs = [_mesh(G, ctx, m) for m in meshes]
+    qs = []
+    for i in range(60):
+        a, b = int(rng.integers(0, 3)), int(rng.integers(0, 3))
+        qs.append((hs[a], hs[b], _rigid(rng, 0.3), _rigid(rng, 1.5), int(rng.integers(0, 2))))
+    arr = G.make_queries(qs)
+    alone = []
+    for q in qs:
+        fn = G.gd_min_distance if q[4] == 0 else G.gd_max_distance
+        alone.append(fn(ctx, q[0], q[1], q[2], q[3]))
+    srv = G.gd_serve_start(ctx, slots=3, max_batch=16)
+    try:
+        tickets = []
+        for i in range(len(qs)):
+            rc, t = G.gd_serve_submit(srv, arr[i])
+            assert rc == 0
+            tickets.append(t)
+        got = {}
+        deadline = time.time() + 120
+        while len(got) < len(tickets) and time.time() < deadline:
+            for t in tickets:
+                if t in got:
+                    continue
+                rc, r = G.gd_serve_poll(srv, t)
+                if rc == 0:
+                    got[t] = r
+                else:
+                    assert rc == G.GD_ERR_NOT_READY
+            time.sleep(0.001)
+    finally:
+        G.gd_serve_stop(srv)
+    assert len(got) == len(tickets)
+    for i, t in enumerate(tickets):
+        r = got[t]
+        assert r.status == 0
+        assert r.d == alone[i].d
+        assert (r.tri_a, r.tri_b) == (alone[i].tri_a, alone[i].tri_b)
+    for h in hs:
+        G.gd_mesh_destroy(h)
+
+
+# ------------------------------------------------------------------ full-size workloads
+
+def test_rings_full_size_frames(G, ctx, oracle_mod):
+    """Two 7.5 M-triangle interlinked rings, the measured workload: sampled
+    frames against the oracle's float64 BVH traversal."""
+    A, B, xa, xbs = synth.config_rings(frames=100)
+    run_pair(G, ctx, oracle_mod, A, B, [(xa, xbs[i]) for i in (0, 37, 99)], kinds=("min",), bvh_oracle=True)
+
+
+def test_icospheres_full_size_min_max(G, ctx, oracle_mod):
+    """Two 1.31 M-triangle noisy spheres at a gap of 1e-5 x diag, min and max."""
+    A, B, xa, xb = synth.config_icospheres(level=8)
+    run_pair(G, ctx, oracle_mod, A, B, [(xa, xb)], bvh_oracle=True)
