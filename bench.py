@@ -273,7 +273,8 @@ def main():
                      "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
                      "kernel": "k_query<min>", "alg_bytes_per_launch": alg},
         "traversal": {k: stats[-1][k] for k in ("levels", "front", "slots", "pairs_tested", "leaf_pairs",
-                                                  "tri_pairs", "candidates", "refined", "blocks")},
+                                                  "tri_pairs", "candidates", "refined", "blocks", "probes",
+                                                  "refits", "level_us", "phase_us", "u_probe", "u_level")},
         "clocks": clk.summary(),
         "wall_s": wall,
     }

@@ -99,6 +99,12 @@ typedef struct {
     int64_t cand_capacity; /* float64 candidate slots (default 2^22) */
     int64_t max_capacity;  /* growth limit for the three above (default 2^28) */
     int64_t timeout_ns;    /* bound on every device-side wait (default 2e9) */
+    int32_t refit_mode;    /* 1: refit B's low subtrees (2^8 leaves) into A's
+                              frame when the front first reaches them (default);
+                              2: never, bound B's local boxes under the map */
+    int32_t refit_slots;   /* subtrees refit per launch (default 2^13) */
+    int32_t probes;        /* greedy probes per launch that seed the running
+                              bound (default 256; at least one per query) */
 } gd_tunables;
 
 /* Counters of the last query (or batch) run on a context. */
@@ -116,6 +122,16 @@ typedef struct {
                                     candidates), counted by the kernel */
     uint32_t retries;            /* capacity growths during the call */
     uint32_t blocks;             /* persistent CTAs launched */
+    uint32_t level_ns[32];       /* device time of each expansion level */
+    uint32_t phase_ns[12];       /* device time of: setup, subtree refits, probes,
+                                    all levels, leaf narrow phase, float64
+                                    refinement, wait for the refinement of the
+                                    other CTAs, witness selection, result
+                                    records, total, (2 unused) */
+    uint32_t probes;             /* greedy descents run to seed the bound */
+    float u_level[32];           /* running bound entering each level (query 0) */
+    float u_probe;               /* running bound after the probes (query 0) */
+    uint32_t refits;             /* B subtrees refit into A's frame */
 } gd_stats;
 
 /* ---- context ----------------------------------------------------------- */

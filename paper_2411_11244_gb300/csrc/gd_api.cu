@@ -46,6 +46,7 @@ struct gd_ctx {
     Item* leafq = nullptr;
     Cand* cand = nullptr;
     double* cand_d = nullptr;
+    double* cand_pts = nullptr;
     long long cap_front = 0, cap_leaf = 0, cap_cand = 0;
     Mailbox* mb_dev = nullptr;   // single-query results, stats and counters
     Mailbox* mb_host = nullptr;  // pinned mirror
@@ -55,6 +56,11 @@ struct gd_ctx {
     gd_result* out_dev = nullptr;
     gd_result* out_host = nullptr;
     long long cap_q = 0;
+    float* rbox = nullptr;        // refit slots
+    uint2* jobs = nullptr;
+    long long cap_slots = 0;
+    unsigned* slot_of = nullptr;  // refit-root tables
+    long long cap_table = 0;
     gd_stats last{};
     bool stats_pending = false;  // last run was device-resident: stats still on the device
     int last_grid = 0;
@@ -94,10 +100,30 @@ bool xform_ok(const double* x, std::string* why) {
 
 void free_ws(gd_ctx* c) {
     cudaFree(c->front[0]); cudaFree(c->front[1]); cudaFree(c->leafq);
-    cudaFree(c->cand); cudaFree(c->cand_d);
+    cudaFree(c->cand); cudaFree(c->cand_d); cudaFree(c->cand_pts);
+    cudaFree(c->rbox); cudaFree(c->jobs);
     c->front[0] = c->front[1] = c->leafq = nullptr;
-    c->cand = nullptr; c->cand_d = nullptr;
+    c->cand = nullptr; c->cand_d = nullptr; c->cand_pts = nullptr;
+    c->rbox = nullptr; c->jobs = nullptr;
     c->ready = false;
+}
+
+// entries of the refit-root table a query needs (0 when refit is off)
+long long table_entries(const gd_ctx* c, const gd_mesh* B) {
+    if (c->tun.refit_mode == 2) return 0;
+    int dR = B->L > kRefitH ? B->L - kRefitH : 0;
+    return 1ll << dR;
+}
+
+gd_status ensure_table(gd_ctx* c, long long n) {
+    if (n <= c->cap_table) return GD_OK;
+    cudaFree(c->slot_of);
+    c->slot_of = nullptr;
+    c->cap_table = 0;
+    long long cap = std::max<long long>(n, 1 << 16);
+    GD_CUDA(c, cudaMalloc(&c->slot_of, sizeof(unsigned) * cap));
+    c->cap_table = cap;
+    return GD_OK;
 }
 
 gd_status alloc_queues(gd_ctx* c) {
@@ -107,6 +133,10 @@ gd_status alloc_queues(gd_ctx* c) {
     GD_CUDA(c, cudaMalloc(&c->leafq, sizeof(Item) * c->cap_leaf));
     GD_CUDA(c, cudaMalloc(&c->cand, sizeof(Cand) * c->cap_cand));
     GD_CUDA(c, cudaMalloc(&c->cand_d, sizeof(double) * c->cap_cand));
+    GD_CUDA(c, cudaMalloc(&c->cand_pts, sizeof(double) * 6 * c->cap_cand));
+    c->cap_slots = std::max(1, c->tun.refit_slots);
+    GD_CUDA(c, cudaMalloc(&c->rbox, sizeof(float) * 6 * kRefitBoxes * (size_t)c->cap_slots));
+    GD_CUDA(c, cudaMalloc(&c->jobs, sizeof(uint2) * (size_t)c->cap_slots));
     c->ready = true;
     return GD_OK;
 }
@@ -166,12 +196,20 @@ void fill_common(gd_ctx* c, KArgs& a, unsigned* ctr, StatsDev* stats) {
     a.cap_leaf = (unsigned)c->cap_leaf;
     a.cand = c->cand;
     a.cand_d = c->cand_d;
+    a.cand_pts = c->cand_pts;
     a.cap_cand = (unsigned)c->cap_cand;
     a.ctr = ctr;
     a.stats = stats;
     a.work_target = c->tun.work_target;
     a.k_max = c->tun.k_max;
     a.timeout_ns = c->tun.timeout_ns;
+    a.rbox = c->rbox;
+    a.jobs = c->jobs;
+    a.cap_slots = (unsigned)c->cap_slots;
+    a.slot_of = c->slot_of;
+    a.refit = c->tun.refit_mode == 2 ? 0 : 1;
+    a.probes = c->tun.probes;
+    a.n_slot_of = 0;
 }
 
 void to_stats(const StatsDev& s, unsigned blocks, unsigned retries, gd_stats* o) {
@@ -186,6 +224,12 @@ void to_stats(const StatsDev& s, unsigned blocks, unsigned retries, gd_stats* o)
     o->alg_bytes = s.alg_bytes;
     o->retries = retries;
     o->blocks = blocks;
+    for (int i = 0; i < 32; ++i) o->level_ns[i] = s.level_ns[i];
+    for (int i = 0; i < 12; ++i) o->phase_ns[i] = s.phase_ns[i];
+    o->probes = s.probes;
+    for (int i = 0; i < 32; ++i) o->u_level[i] = s.u_level[i];
+    o->u_probe = s.u_probe;
+    o->refits = s.refits;
 }
 
 gd_status check_pair(gd_ctx* ctx, const gd_mesh* A, const gd_mesh* B) {
@@ -205,6 +249,9 @@ gd_status run_single(gd_ctx* ctx, const gd_mesh* A, const gd_mesh* B, int kind, 
     if (!xform_ok(xa, &why) || !xform_ok(xb, &why)) return fail(ctx, GD_ERR_INVALID_ARG, why);
     s = ensure_ws(ctx, 1);
     if (s != GD_OK) return s;
+    const long long tab = table_entries(ctx, B);
+    s = ensure_table(ctx, tab);
+    if (s != GD_OK) return s;
     unsigned retries = 0;
     for (;;) {
         KArgs a{};
@@ -217,6 +264,8 @@ gd_status run_single(gd_ctx* ctx, const gd_mesh* A, const gd_mesh* B, int kind, 
         std::memcpy(a.xa_val, xa, sizeof(a.xa_val));
         std::memcpy(a.xb_val, xb, sizeof(a.xb_val));
         fill_common(ctx, a, ctx->mb_dev->ctr, &ctx->mb_dev->stats);
+        a.slot_of = ctx->slot_of;
+        a.n_slot_of = (unsigned long long)tab;
         a.out = &ctx->mb_dev->out;
         int grid = grid_blocks(ctx, kind);
         GD_CUDA(ctx, launch_query(kind, a, grid, ctx->stream));
@@ -267,6 +316,9 @@ GD_API gd_status gd_ctx_create(int device, gd_ctx** out) {
     c->tun.cand_capacity = 1ll << 22;
     c->tun.max_capacity = 1ll << 28;
     c->tun.timeout_ns = 2000000000ll;
+    c->tun.refit_mode = 1;
+    c->tun.refit_slots = 1 << 13;
+    c->tun.probes = 256;
     *out = c;
     return GD_OK;
 }
@@ -280,6 +332,7 @@ GD_API void gd_ctx_destroy(gd_ctx* c) {
     cudaFreeHost(c->mb_host);
     cudaFree(c->qs); cudaFree(c->qin_dev); cudaFree(c->out_dev);
     cudaFreeHost(c->qin_host); cudaFreeHost(c->out_host);
+    cudaFree(c->slot_of);
     cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -299,6 +352,9 @@ GD_API gd_status gd_ctx_set_tunables(gd_ctx* c, const gd_tunables* t) {
     if (t->cand_capacity > 0) { c->tun.cand_capacity = t->cand_capacity; realloc = true; }
     if (t->max_capacity > 0) c->tun.max_capacity = t->max_capacity;
     if (t->timeout_ns > 0) c->tun.timeout_ns = t->timeout_ns;
+    if (t->refit_mode == 1 || t->refit_mode == 2) c->tun.refit_mode = t->refit_mode;
+    if (t->refit_slots > 0) { c->tun.refit_slots = t->refit_slots; realloc = true; }
+    if (t->probes > 0) c->tun.probes = t->probes;
     if (realloc && c->ready) {
         cudaStreamSynchronize(c->stream);
         free_ws(c);
@@ -475,7 +531,12 @@ GD_API gd_status gd_query_device(gd_ctx* ctx, const gd_mesh* A, const gd_mesh* B
     a.mB = B->d_desc;
     a.xa_src = d_xa;
     a.xb_src = d_xb;
+    const long long tab = table_entries(ctx, B);
+    s = ensure_table(ctx, tab);
+    if (s != GD_OK) return s;
     fill_common(ctx, a, ctx->mb_dev->ctr, &ctx->mb_dev->stats);
+    a.slot_of = ctx->slot_of;
+    a.n_slot_of = (unsigned long long)tab;
     a.out = d_out;
     cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
     int grid = grid_blocks(ctx, (int)kind);
@@ -507,6 +568,7 @@ GD_API gd_status gd_batch_query(gd_ctx* ctx, const gd_query* q, int64_t n, gd_re
         long long m = (long long)idx.size();
         gd_status s = ensure_ws(ctx, m);
         if (s != GD_OK) return s;
+        long long tab = 0;
         for (long long j = 0; j < m; ++j) {
             const gd_query& Q = q[idx[j]];
             QIn& in = ctx->qin_host[j];
@@ -514,12 +576,19 @@ GD_API gd_status gd_batch_query(gd_ctx* ctx, const gd_query* q, int64_t n, gd_re
             in.B = Q.b->d_desc;
             std::memcpy(in.xa, Q.xa, sizeof(in.xa));
             std::memcpy(in.xb, Q.xb, sizeof(in.xb));
+            in.slot_base = (unsigned)tab;
+            tab += table_entries(ctx, Q.b);
         }
+        if (tab > 0xfffffff0ll) return fail(ctx, GD_ERR_INVALID_ARG, "batch too large for the refit tables");
+        s = ensure_table(ctx, tab);
+        if (s != GD_OK) return s;
         GD_CUDA(ctx, cudaMemcpyAsync(ctx->qin_dev, ctx->qin_host, sizeof(QIn) * m, cudaMemcpyHostToDevice, ctx->stream));
         KArgs a{};
         a.nq = (int)m;
         a.qin = ctx->qin_dev;
         fill_common(ctx, a, ctx->mb_dev->ctr, &ctx->mb_dev->stats);
+        a.slot_of = ctx->slot_of;
+        a.n_slot_of = (unsigned long long)tab;
         a.out = ctx->out_dev;
         int grid = grid_blocks(ctx, kind);
         GD_CUDA(ctx, launch_query(kind, a, grid, ctx->stream));
@@ -561,13 +630,18 @@ GD_API gd_status gd_batch_query(gd_ctx* ctx, const gd_query* q, int64_t n, gd_re
 namespace gd {
 
 gd_status serve_launch_batch(gd_ctx* ctx, SlotBuffers& sb, const gd_query* qs, long long m, int kind) {
+    long long tab = 0;
     for (long long j = 0; j < m; ++j) {
         QIn& in = sb.qin_host[j];
         in.A = qs[j].a->d_desc;
         in.B = qs[j].b->d_desc;
         std::memcpy(in.xa, qs[j].xa, sizeof(in.xa));
         std::memcpy(in.xb, qs[j].xb, sizeof(in.xb));
+        in.slot_base = (unsigned)tab;
+        tab += table_entries(ctx, qs[j].b);
     }
+    // without room for the refit tables this batch bounds B's local boxes only
+    const bool refit = ctx->tun.refit_mode != 2 && tab <= sb.cap_table;
     GD_CUDA(ctx, cudaMemcpyAsync(sb.qin_dev, sb.qin_host, sizeof(QIn) * m, cudaMemcpyHostToDevice, sb.stream));
     KArgs a{};
     a.nq = (int)m;
@@ -580,6 +654,7 @@ gd_status serve_launch_batch(gd_ctx* ctx, SlotBuffers& sb, const gd_query* qs, l
     a.cap_leaf = (unsigned)sb.cap_leaf;
     a.cand = sb.cand;
     a.cand_d = sb.cand_d;
+    a.cand_pts = sb.cand_pts;
     a.cap_cand = (unsigned)sb.cap_cand;
     a.ctr = sb.mb_dev_ctr;
     a.stats = sb.stats_dev;
@@ -587,6 +662,13 @@ gd_status serve_launch_batch(gd_ctx* ctx, SlotBuffers& sb, const gd_query* qs, l
     a.k_max = ctx->tun.k_max;
     a.timeout_ns = ctx->tun.timeout_ns;
     a.out = sb.out_dev;
+    a.rbox = sb.rbox;
+    a.jobs = sb.jobs;
+    a.cap_slots = (unsigned)sb.cap_slots;
+    a.slot_of = sb.slot_of;
+    a.refit = refit ? 1 : 0;
+    a.probes = ctx->tun.probes;
+    a.n_slot_of = refit ? (unsigned long long)tab : 0ull;
     GD_CUDA(ctx, launch_query(kind, a, sb.grid, sb.stream));
     GD_CUDA(ctx, cudaMemcpyAsync(sb.out_host, sb.out_dev, sizeof(gd_result) * m, cudaMemcpyDeviceToHost, sb.stream));
     GD_CUDA(ctx, cudaMemcpyAsync(sb.ctr_host, sb.mb_dev_ctr, sizeof(unsigned) * kCtrWords, cudaMemcpyDeviceToHost,

@@ -72,11 +72,15 @@ __device__ __forceinline__ unsigned long long spread3(unsigned v) {
 
 __global__ void k_morton(const float* verts, const int32_t* tris, long long nt, const unsigned* flags, int bits,
                          unsigned long long* keys, unsigned* vals) {
-    float lo[3], ext[3];
+    // one scale for all three axes (cubic cells): per-axis scales would make
+    // the cells of flat or thin meshes into slabs whose boxes are far from
+    // the surface they bound
+    float lo[3], ext[3], e = 0.f;
     for (int c = 0; c < 3; ++c) {
         lo[c] = unordered(flags[2 + c]);
-        ext[c] = unordered(flags[5 + c]) - lo[c];
+        e = fmaxf(e, __fsub_rn(unordered(flags[5 + c]), lo[c]));
     }
+    for (int c = 0; c < 3; ++c) ext[c] = e;
     const float cells = (float)(1u << bits);
     const unsigned top = (1u << bits) - 1u;
     const long long stride = (long long)gridDim.x * blockDim.x;

@@ -205,6 +205,89 @@ __device__ __forceinline__ void tri_tri_min(const V3<T>* A, const V3<T>* B, V3<T
     *hit = touched;
 }
 
+// Vertex i (0..2, a runtime value) of a triangle held in registers: a
+// select chain, so that the triangle never has to live in local memory.
+template <class T>
+__device__ __forceinline__ V3<T> pick3(const V3<T>* X, int i) {
+    V3<T> r = X[0];
+    if (i == 1) r = X[1];
+    if (i == 2) r = X[2];
+    return r;
+}
+
+// One of the 21 feature pairs of tri_tri_min, for a warp that spreads them
+// over its lanes: f in [0, 9) edge-edge, [9, 12) vertex of A vs B,
+// [12, 15) vertex of B vs A, [15, 18) edge of A crossing B's plane,
+// [18, 21) edge of B crossing A's plane.  Lanes without a feature (or whose
+// edge does not cross the plane) report an infinite distance.
+template <class T>
+__device__ __forceinline__ void tri_feature(int f, const V3<T>* A, const V3<T>* B, V3<T>* P, V3<T>* Q, T* d2,
+                                            bool* hit) {
+    *hit = false;
+    bool have = true, in = false;
+    if (f < 9) {
+        const int i = f / 3, j = f - 3 * (f / 3);
+        const V3<T> a0 = pick3(A, i), a1 = pick3(A, i == 2 ? 0 : i + 1);
+        const V3<T> b0 = pick3(B, j), b1 = pick3(B, j == 2 ? 0 : j + 1);
+        closest_segment_segment(a0, a1 - a0, b0, b1 - b0, P, Q);
+    } else if (f < 12) {
+        *P = pick3(A, f - 9);
+        *Q = closest_on_triangle(*P, B[0], B[1], B[2], &in);
+    } else if (f < 15) {
+        *Q = pick3(B, f - 12);
+        *P = closest_on_triangle(*Q, A[0], A[1], A[2], &in);
+    } else if (f < 21) {
+        const bool ea = f < 18;
+        const int i = f - (ea ? 15 : 18), j = i == 2 ? 0 : i + 1;
+        // edge owner E, plane owner F, all in registers
+        const V3<T> e0 = ea ? pick3(A, i) : pick3(B, i), e1 = ea ? pick3(A, j) : pick3(B, j);
+        const V3<T> f0 = ea ? B[0] : A[0], f1 = ea ? B[1] : A[1], f2 = ea ? B[2] : A[2];
+        V3<T> n = cross(f1 - f0, f2 - f0);
+        T si = dot(n, e0 - f0), sj = dot(n, e1 - f0);
+        have = ((si <= T(0) && sj >= T(0)) || (si >= T(0) && sj <= T(0))) && (si - sj) != T(0);
+        if (have) {
+            V3<T> X = e0 + (e1 - e0) * clamp01(si / (si - sj));
+            V3<T> Y = closest_on_triangle(X, f0, f1, f2, &in);
+            if (ea) { *P = X; *Q = Y; } else { *P = Y; *Q = X; }
+            if (in) { *hit = true; *P = X; *Q = X; }
+        }
+    } else {
+        have = false;
+    }
+    if (have) {
+        V3<T> d = *P - *Q;
+        *d2 = *hit ? T(0) : dot(d, d);
+    } else {
+        *d2 = T(INFINITY);
+    }
+}
+
+// The two point sets of feature pair f of tri_feature (an edge, a vertex or a
+// whole triangle on each side), as three points each (an edge or a vertex
+// repeats a point), for separation bounds.
+template <class T>
+__device__ __forceinline__ void feature_points(int f, const V3<T>* A, const V3<T>* B, V3<T>* PA, V3<T>* PB) {
+    if (f < 9) {
+        const int i = f / 3, j = f - 3 * (f / 3);
+        PA[0] = pick3(A, i); PA[1] = pick3(A, i == 2 ? 0 : i + 1); PA[2] = PA[1];
+        PB[0] = pick3(B, j); PB[1] = pick3(B, j == 2 ? 0 : j + 1); PB[2] = PB[1];
+    } else if (f < 12) {
+        PA[0] = pick3(A, f - 9); PA[1] = PA[0]; PA[2] = PA[0];
+        PB[0] = B[0]; PB[1] = B[1]; PB[2] = B[2];
+    } else if (f < 15) {
+        PA[0] = A[0]; PA[1] = A[1]; PA[2] = A[2];
+        PB[0] = pick3(B, f - 12); PB[1] = PB[0]; PB[2] = PB[0];
+    } else if (f < 18) {
+        const int i = f - 15;
+        PA[0] = pick3(A, i); PA[1] = pick3(A, i == 2 ? 0 : i + 1); PA[2] = PA[1];
+        PB[0] = B[0]; PB[1] = B[1]; PB[2] = B[2];
+    } else {
+        const int i = f - 18;
+        PA[0] = A[0]; PA[1] = A[1]; PA[2] = A[2];
+        PB[0] = pick3(B, i); PB[1] = pick3(B, i == 2 ? 0 : i + 1); PB[2] = PB[1];
+    }
+}
+
 // Farthest vertex pair (the maximum over two triangles is attained at vertices).
 template <class T>
 __device__ __forceinline__ void tri_tri_max(const V3<T>* A, const V3<T>* B, V3<T>* P, V3<T>* Q, T* d2) {
@@ -218,6 +301,43 @@ __device__ __forceinline__ void tri_tri_max(const V3<T>* A, const V3<T>* B, V3<T
             if (n > best) { best = n; *P = A[i]; *Q = B[j]; }
         }
     *d2 = best;
+}
+
+// ---------------------------------------------------------------- double-float
+// A value carried as an unevaluated float32 sum hi + lo (about 48 significant
+// bits), built from error-free transformations on the float32 pipe.  Every
+// step uses explicitly rounded intrinsics so that no contraction or
+// reassociation can change it.
+
+struct DF {
+    float hi, lo;
+};
+
+// s + e == a + b exactly (Knuth's two-sum)
+__device__ __forceinline__ DF two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return DF{s, e};
+}
+
+// s + e == a + b exactly when |a| >= |b|
+__device__ __forceinline__ DF fast_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    return DF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    DF s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+// (hi + lo) * b for a float32 b: the product of the leading parts is exact
+// (its error term recovered by an FMA), the rest adds a relative 2^-48
+__device__ __forceinline__ DF df_mul_f(DF a, float b) {
+    float p = __fmul_rn(a.hi, b);
+    float e = __fmaf_rn(a.hi, b, -p);
+    return fast_two_sum(p, __fmaf_rn(a.lo, b, e));
 }
 
 // ---------------------------------------------------------------- transforms
@@ -280,9 +400,13 @@ __device__ __forceinline__ float upper_max_sq(const Box& a, const float* elo, co
     return s;
 }
 
-// Corner m of the mapped box b (bit k of m selects hi on axis k).
+// Corner m of box b (bit k of m selects hi on axis k), mapped by X unless the
+// box is already expressed in the working frame (AA).
+template <bool AA>
 __device__ __forceinline__ V3<float> mapped_corner(const Rigid32& X, const Box& b, int m) {
-    return map32(X, (m & 1) ? b.hi[0] : b.lo[0], (m & 2) ? b.hi[1] : b.lo[1], (m & 4) ? b.hi[2] : b.lo[2]);
+    const float x = (m & 1) ? b.hi[0] : b.lo[0], y = (m & 2) ? b.hi[1] : b.lo[1], z = (m & 4) ? b.hi[2] : b.lo[2];
+    if (AA) return mk3(x, y, z);
+    return map32(X, x, y, z);
 }
 
 // Eq. 10: squared enhanced upper bound of the min distance,
@@ -291,45 +415,40 @@ __device__ __forceinline__ V3<float> mapped_corner(const Rigid32& X, const Box& 
 // axis-aligned face i (axis k at coordinate f) is at squared distance
 //   (Q_k - f)^2 + sum over the other axes l of max((Q_l - lo_l)^2, (Q_l - hi_l)^2),
 // and the maximum over face j is attained at one of its 4 corners.
+template <bool AA>
 __device__ __forceinline__ float upper_min_sq_enhanced(const Rigid32& X, const Box& a, const Box& b) {
-    float run[6][6];
+    V3<float> c[8];
 #pragma unroll
-    for (int i = 0; i < 6; ++i)
+    for (int m = 0; m < 8; ++m) c[m] = mapped_corner<AA>(X, b, m);
+    float best = FLT_MAX;
+    // face j of b: axis l, side sl; its corners are those with bit l == sl
 #pragma unroll
-        for (int j = 0; j < 6; ++j) run[i][j] = 0.f;
+    for (int l = 0; l < 3; ++l) {
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
-        V3<float> c = mapped_corner(X, b, m);
-        float cc[3] = {c.x, c.y, c.z};
-        float dl[3], dh[3], M2[3];
+        for (int sl = 0; sl < 2; ++sl) {
+            float run[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            dl[k] = cc[k] - a.lo[k];
-            dh[k] = cc[k] - a.hi[k];
-            M2[k] = fmaxf(dl[k] * dl[k], dh[k] * dh[k]);
-        }
-        float Pk[3] = {M2[1] + M2[2], M2[0] + M2[2], M2[0] + M2[1]};
+            for (int m = 0; m < 8; ++m) {
+                if (((m >> l) & 1) != sl) continue;
+                const float cc[3] = {c[m].x, c[m].y, c[m].z};
+                float dl[3], dh[3], M2[3];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
+                for (int k = 0; k < 3; ++k) {
+                    dl[k] = cc[k] - a.lo[k];
+                    dh[k] = cc[k] - a.hi[k];
+                    M2[k] = fmaxf(dl[k] * dl[k], dh[k] * dh[k]);
+                }
+                const float Pk[3] = {M2[1] + M2[2], M2[0] + M2[2], M2[0] + M2[1]};
 #pragma unroll
-            for (int side = 0; side < 2; ++side) {
-                float d = side ? dh[k] : dl[k];
-                float v = fmaf(d, d, Pk[k]);
-                int i = 2 * k + side;
-                // corner m lies on face (axis l, side bit l of m) of b
-#pragma unroll
-                for (int l = 0; l < 3; ++l) {
-                    int j = 2 * l + ((m >> l) & 1);
-                    run[i][j] = fmaxf(run[i][j], v);
+                for (int k = 0; k < 3; ++k) {
+                    run[2 * k] = fmaxf(run[2 * k], fmaf(dl[k], dl[k], Pk[k]));
+                    run[2 * k + 1] = fmaxf(run[2 * k + 1], fmaf(dh[k], dh[k], Pk[k]));
                 }
             }
+#pragma unroll
+            for (int i = 0; i < 6; ++i) best = fminf(best, run[i]);
         }
     }
-    float best = FLT_MAX;
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-#pragma unroll
-        for (int j = 0; j < 6; ++j) best = fminf(best, run[i][j]);
     return best;
 }
 
@@ -338,10 +457,11 @@ __device__ __forceinline__ float upper_min_sq_enhanced(const Rigid32& X, const B
 //   and the axis-aligned box enclosing the 4 mapped corners of face j
 //   (that box contains face j, so its distance does not exceed the face's;
 //   with no rotation it is the face itself and the bound is Eq. 11 exactly).
+template <bool AA>
 __device__ __forceinline__ float lower_max_sq_enhanced(const Rigid32& X, const Box& a, const Box& b) {
     V3<float> c[8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) c[m] = mapped_corner(X, b, m);
+    for (int m = 0; m < 8; ++m) c[m] = mapped_corner<AA>(X, b, m);
     float best = 0.f;
 #pragma unroll
     for (int l = 0; l < 3; ++l) {

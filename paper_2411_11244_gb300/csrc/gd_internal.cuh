@@ -19,6 +19,8 @@
 namespace gd {
 
 constexpr int kBlock = 256;          // threads per CTA of the persistent kernels
+constexpr int kRefitH = 8;           // height of the B subtrees refit into A's frame
+constexpr int kRefitBoxes = 2 << kRefitH;  // boxes per refit slot (heap 1 .. 2^(h+1)-1)
 constexpr int kMaxLevels = 64;       // BVTT expansion levels per launch
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -49,6 +51,8 @@ struct QIn {
     const MeshDev* A;
     const MeshDev* B;
     double xa[12], xb[12];
+    unsigned slot_base;  // first entry of this query's refit-root table
+    unsigned pad;
 };
 
 // per-query running state and derived constants
@@ -59,10 +63,14 @@ struct __align__(16) QState {
     unsigned long long best_d;    // float64 bits of the refined extreme
     unsigned long long best_key;  // (orig a << 32 | orig b) of the witness
     float R[9], t[3];             // B-local -> A-local, float32
+    float Rl[9], tl[3];           // float32 remainders: R + Rl, t + tl carry ~48 bits
     float E_box, E_tri;           // absolute widening of box / triangle bounds
+    float E_df;                   // error of the double-float map (absolute)
     const MeshDev* A;
     const MeshDev* B;
     double xa[12], xb[12];
+    unsigned slot_base;           // refit-root table offset of this query
+    int dR;                       // depth of B's refit roots (L_B - min(L_B, kRefitH)), -1: no refit
 };
 
 constexpr unsigned kStatOverflow = 1u, kStatTimeout = 2u, kStatNoResult = 4u;
@@ -74,6 +82,9 @@ enum : int {
     kCtrLeaf = 6,     // leaf-pair count
     kCtrCand = 7,     // candidate count
     kCtrOverflow = 9, // some push exceeded its capacity
+    kCtrJobs = 10,    // refit jobs appended (slot j refits job j)
+    kCtrJobsDone = 11,// refit jobs already run
+    kCtrTailDone = 12,// CTAs done with their candidate in the one-per-CTA tail
     kCtrReset = 16,   // counters [0, kCtrReset) are cleared at kernel start
     kCtrAbort = 20,   // a wait gave up: every CTA leaves at its next barrier
     kCtrLastAbort = 21, // the abort flag of the last finished launch
@@ -90,6 +101,13 @@ struct StatsDev {
     unsigned long long pairs_tested;
     unsigned leaf_pairs, tri_pairs, candidates, refined;
     unsigned long long alg_bytes;
+    unsigned level_ns[32];  // device time of each level (CTA 0's view, barrier to barrier)
+    unsigned phase_ns[12];  // setup, refit, probe, levels, leaf, refine, tail wait, select,
+                            // finalize, total, -, -
+    unsigned probes;        // greedy probes run
+    float u_level[32];      // running bound of query 0 entering each level
+    float u_probe;          // ... right after the probes
+    unsigned refits;        // B subtrees refit into A's frame
 };
 
 struct KArgs {
@@ -108,10 +126,18 @@ struct KArgs {
     unsigned cap_leaf;
     Cand* cand;
     double* cand_d;
+    double* cand_pts;           // float64 witness points of every candidate (6 each)
     unsigned cap_cand;
     unsigned* ctr;
     StatsDev* stats;
     gd_result* out;
+    float* rbox;                // refit slots: kRefitBoxes boxes of 6 floats each
+    unsigned cap_slots;
+    unsigned* slot_of;          // refit-root table: slot of each claimed root
+    unsigned long long n_slot_of;
+    uint2* jobs;                // (query, root) of every refit slot
+    int refit;                  // 0: map B's local boxes only; 1: lazy refit
+    int probes;                 // greedy probes per launch (at least one per query)
     long long work_target;
     int k_max;
     long long timeout_ns;

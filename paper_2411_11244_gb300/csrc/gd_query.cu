@@ -13,7 +13,10 @@
 //      t >> 2k, its low bits pick the descendants in the implicit tree of
 //      Section 7.3); survivors are appended with warp-aggregated atomics and
 //      the running bound is lowered with a warp-reduced atomicMin on the float
-//      bits (Section 7.4);
+//      bits (Section 7.4).  When the front first reaches a B subtree of 2^8
+//      leaves, that subtree is refit into A's frame (the paper refits B per
+//      frame, Section 8; here only the subtrees the front reaches are refit),
+//      and right after the first refit, greedy probes seed the bound;
 //   3  leaf-pair narrow phase: float32 triangle-triangle bounds, running bound
 //      update, candidate list;
 //   4  float64 refinement of the candidates in the world frame;
@@ -28,12 +31,10 @@
 
 namespace gd {
 
-constexpr float kU = 5.9604645e-08f;   // 2^-24, unit roundoff of float32
+constexpr float kU = 5.9604645e-08f;    // 2^-24, unit roundoff of float32
 constexpr float kRelW = 9.5367432e-07f; // 2^-20: world vs working-frame slack
 constexpr unsigned kFltMaxBits = 0x7f7fffffu;
-
-template <int KIND>
-struct Kind;
+constexpr unsigned kNoSlot = 0xffffffffu, kClaimed = 0xfffffffeu;
 
 // ------------------------------------------------------------- thresholds
 // All float32 bounds are made rigorous for float64 world distances:
@@ -70,9 +71,19 @@ __device__ __forceinline__ float lower_from_sq(float s2, float E) { return lower
 
 // ------------------------------------------------------------- helpers
 
-__device__ __forceinline__ Box load_box(const float* box, unsigned i) {
+__device__ __forceinline__ Box load_box(const float* box, unsigned long long i) {
     const float2* p = reinterpret_cast<const float2*>(box + 6ull * i);
     float2 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
+    Box r;
+    r.lo[0] = a.x; r.lo[1] = a.y; r.lo[2] = b.x;
+    r.hi[0] = b.y; r.hi[1] = c.x; r.hi[2] = c.y;
+    return r;
+}
+
+// refit boxes are written during the launch: read them through L2
+__device__ __forceinline__ Box load_box_cg(const float* box, unsigned long long i) {
+    const float2* p = reinterpret_cast<const float2*>(box + 6ull * i);
+    float2 a = __ldcg(p), b = __ldcg(p + 1), c = __ldcg(p + 2);
     Box r;
     r.lo[0] = a.x; r.lo[1] = a.y; r.lo[2] = b.x;
     r.hi[0] = b.y; r.hi[1] = c.x; r.hi[2] = c.y;
@@ -97,6 +108,8 @@ __device__ __forceinline__ Tri32 load_tri(const float4* tri, unsigned j) {
 __device__ __forceinline__ unsigned leaf_first(long long T, int L, unsigned leaf) {
     return (unsigned)(((unsigned long long)leaf * (unsigned long long)T) >> L);
 }
+
+__device__ __forceinline__ int depth_of(unsigned node) { return 31 - __clz(node); }
 
 // Append v to buf if want (warp-aggregated: one atomic per warp).  Returns
 // false for a lane whose entry did not fit.
@@ -158,6 +171,8 @@ struct QView {
     const float4* triB;
     long long TA, TB;
     int LA, LB;
+    int dR;
+    unsigned slot_base;
 };
 
 __device__ __forceinline__ void view(const KArgs& A, unsigned q, QView& V) {
@@ -175,7 +190,296 @@ __device__ __forceinline__ void view(const KArgs& A, unsigned q, QView& V) {
     V.triA = ma->tri; V.triB = mb->tri;
     V.TA = ma->T; V.TB = mb->T;
     V.LA = ma->L; V.LB = mb->L;
+    V.dR = __ldcg(&s.dR);
+    V.slot_base = __ldcg(&s.slot_base);
     V.q = q;
+}
+
+// Refit slot holding B node b (depth db >= dR) in A's frame, or kNoSlot.
+__device__ __forceinline__ unsigned refit_slot(const KArgs& A, const QView& V, unsigned b, int db) {
+    if (V.dR < 0 || db < V.dR) return kNoSlot;
+    unsigned root = b >> (db - V.dR);
+    unsigned s = __ldcg(A.slot_of + V.slot_base + (root - (1u << V.dR)));
+    return s < A.cap_slots ? s : kNoSlot;
+}
+
+__device__ __forceinline__ unsigned long long refit_index(const QView& V, unsigned slot, unsigned b, int db) {
+    int rel = db - V.dR;
+    unsigned local = (1u << rel) | (b & ((1u << rel) - 1u));
+    return (unsigned long long)slot * kRefitBoxes + local;
+}
+
+// Claim the refit of root b for query q (first claimer appends the job).
+__device__ __forceinline__ void claim_root(const KArgs& A, const QView& V, unsigned q, unsigned b) {
+    unsigned* e = A.slot_of + V.slot_base + (b - (1u << V.dR));
+    if (ld_relaxed(e) != kNoSlot) return;
+    if (atomicCAS(e, kNoSlot, kClaimed) != kNoSlot) return;
+    unsigned j = atomicAdd(A.ctr + kCtrJobs, 1u);
+    if (j < A.cap_slots) A.jobs[j] = make_uint2(q, b);
+    // beyond capacity: the root stays claimed without a slot, and its subtree
+    // keeps using the mapped local boxes (valid, only looser)
+}
+
+// ------------------------------------------------------------- triangles
+
+// Bounds of one triangle pair (sorted ids ta of A, tb of B), rigorous for the
+// float64 world distance: KIND 0 bounds the pair's min distance, KIND 1 its
+// max distance.  The min lower bound is the separation of the two triangles
+// along the direction between their float32 closest points (any direction
+// gives a valid separation; this one is nearly optimal).
+// Bounds on local float32 coordinates Al (triangle of A) and Bl (triangle of
+// B) whose distances err by at most E: KIND 0 bounds the pair's min distance
+// (upper: the best feature pair; lower: the separation of the two triangles
+// along the direction between those closest points, valid for any
+// direction and nearly tight for this one), KIND 1 its max distance.
+template <int KIND>
+__device__ __forceinline__ void tri_bounds_core(const V3<float>* Al, const V3<float>* Bl, float E, float* lo,
+                                                float* up) {
+    if (KIND == 0) {
+        V3<float> P, Q;
+        float d2;
+        bool hit;
+        tri_tri_min(Al, Bl, &P, &Q, &d2, &hit);
+        *up = upper_from_sq(d2, E);
+        float l = 0.f;
+        V3<float> nrm = P - Q;
+        float nn = dot(nrm, nrm);
+        if (nn > 0.f) {
+            float amin = FLT_MAX, bmax = -FLT_MAX;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                amin = fminf(amin, dot(nrm, Al[k]));
+                bmax = fmaxf(bmax, dot(nrm, Bl[k]));
+            }
+            float sep = amin - bmax;
+            if (sep > 0.f) l = lower_from_dist(sep / sqrtf(nn), E);
+        }
+        *lo = l;
+    } else {
+        V3<float> P, Q;
+        float d2;
+        tri_tri_max(Al, Bl, &P, &Q, &d2);
+        *lo = lower_from_sq(d2, E);
+        *up = upper_from_sq(d2, E);
+    }
+}
+
+__device__ __forceinline__ float max_abs3(V3<float> v) { return fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fabsf(v.z)); }
+
+// Bounds of one triangle pair (sorted ids ta of A, tb of B), rigorous for the
+// float64 world distance, from B's float32 map into A's frame.  The pair is
+// moved to A's first vertex first: a difference of two float32 values is
+// rounded relative to the (small) result, so every later rounding error
+// scales with the pair's local extent X, not with the scene's coordinates;
+// E_box covers the mapping of B's vertices.
+template <int KIND>
+__device__ __forceinline__ void tri_pair_bounds(const QView& V, unsigned ta, unsigned tb, float* lo, float* up) {
+    Tri32 TA = load_tri(V.triA, ta), TB = load_tri(V.triB, tb);
+    const V3<float> o = TA.v[0];
+    V3<float> Al[3], Bl[3];
+    float X = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        Al[k] = TA.v[k] - o;
+        Bl[k] = map32(V.X, TB.v[k].x, TB.v[k].y, TB.v[k].z) - o;
+        X = fmaxf(X, fmaxf(max_abs3(Al[k]), max_abs3(Bl[k])));
+    }
+    tri_bounds_core<KIND>(Al, Bl, __fadd_ru(V.E_box, __fmul_ru(256.0f * kU * 1.001f, X)), lo, up);
+}
+
+// The same bounds, tight: B's vertices mapped into A's frame in double-float
+// (R + Rl, t + tl, ~48 bits) and moved to A's first vertex before rounding to
+// float32, so that neither the map nor the magnitude of the coordinates
+// leaves more than ~u times the pair's local extent (plus E_df) of error.
+// Used for pairs that pass the float32 test, so that only near-ties reach the
+// float64 refinement; it stays on the float32 pipe (float64 is slow here).
+template <int KIND>
+__device__ __forceinline__ void tri_pair_bounds_tight(const QState& s, const QView& V, unsigned ta, unsigned tb,
+                                                      float* lo, float* up) {
+    Tri32 TA = load_tri(V.triA, ta), TB = load_tri(V.triB, tb);
+    float Rl[9], tl[3];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Rl[i] = __ldcg(&s.Rl[i]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) tl[i] = __ldcg(&s.tl[i]);
+    const float Edf = __ldcg(&s.E_df);
+    const V3<float> o = TA.v[0];
+    const float oc[3] = {o.x, o.y, o.z};
+    V3<float> Al[3], Bl[3];
+    float X = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        Al[k] = mk3(__fsub_rn(TA.v[k].x, o.x), __fsub_rn(TA.v[k].y, o.y), __fsub_rn(TA.v[k].z, o.z));
+        const float p[3] = {TB.v[k].x, TB.v[k].y, TB.v[k].z};
+        float c[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            DF acc = two_sum(V.X.t[i], -oc[i]);
+            acc = df_add(acc, DF{tl[i], 0.f});
+#pragma unroll
+            for (int j = 0; j < 3; ++j) acc = df_add(acc, df_mul_f(DF{V.X.R[3 * i + j], Rl[3 * i + j]}, p[j]));
+            c[i] = __fadd_rn(acc.hi, acc.lo);
+        }
+        Bl[k] = mk3(c[0], c[1], c[2]);
+        X = fmaxf(X, fmaxf(max_abs3(Al[k]), max_abs3(Bl[k])));
+    }
+    tri_bounds_core<KIND>(Al, Bl, __fadd_ru(Edf, __fmul_ru(256.0f * kU * 1.001f, X)), lo, up);
+}
+
+// ------------------------------------------------------------- pair bounds
+
+// Bounds of node pair (ia of A, ib of B at depth db).  Returns the stored
+// culling value (KIND 0: squared lower bound of the min; KIND 1: squared upper
+// bound of the max) and whether the pair survives against Ucur; for a
+// survivor, *newU is its enhanced bound (Eq. 10 / Eq. 11) for the running
+// bound and *key orders survivors by it.
+template <int KIND>
+__device__ __forceinline__ float pair_bounds(const KArgs& A, const QView& V, unsigned ia, unsigned ib, int db,
+                                             float Ucur, bool* survive, unsigned* newU, unsigned* key) {
+    Box ba = load_box(V.boxA, ia);
+    const unsigned slot = refit_slot(A, V, ib, db);
+    float bound;
+    *key = 0xffffffffu;
+    if (slot != kNoSlot) {
+        // B's box already in A's frame (refit): plain AABB-AABB bounds
+        Box bb = load_box_cg(A.rbox, refit_index(V, slot, ib, db));
+        if (KIND == 0) {
+            bound = lower_min_sq(ba, bb.lo, bb.hi);
+            *survive = bound <= min_keep_threshold(Ucur, V.E_box);
+            if (*survive) {
+                float u2 = upper_min_sq_enhanced<true>(V.X, ba, bb);
+                *newU = __float_as_uint(upper_from_sq(u2, V.E_box));
+                *key = __float_as_uint(u2);
+            }
+        } else {
+            bound = upper_max_sq(ba, bb.lo, bb.hi);
+            *survive = bound >= max_keep_threshold(Ucur, V.E_box);
+            if (*survive) {
+                float l2 = lower_max_sq_enhanced<true>(V.X, ba, bb);
+                *newU = __float_as_uint(lower_from_sq(l2, V.E_box));
+                *key = ~__float_as_uint(l2);
+            }
+        }
+    } else {
+        Box bb = load_box(V.boxB, ib);
+        float elo[3], ehi[3];
+        enclose(V.X, bb, elo, ehi);
+        if (KIND == 0) {
+            bound = lower_min_sq(ba, elo, ehi);
+            *survive = bound <= min_keep_threshold(Ucur, V.E_box);
+            if (*survive) {
+                float u2 = upper_min_sq_enhanced<false>(V.X, ba, bb);
+                *newU = __float_as_uint(upper_from_sq(u2, V.E_box));
+                *key = __float_as_uint(u2);
+            }
+        } else {
+            bound = upper_max_sq(ba, elo, ehi);
+            *survive = bound >= max_keep_threshold(Ucur, V.E_box);
+            if (*survive) {
+                float l2 = lower_max_sq_enhanced<false>(V.X, ba, bb);
+                *newU = __float_as_uint(lower_from_sq(l2, V.E_box));
+                *key = ~__float_as_uint(l2);
+            }
+        }
+    }
+    return bound;
+}
+
+// ------------------------------------------------------------- refit
+
+// Refit the B subtree below root (depth dR, 2^h leaves, h <= kRefitH) into
+// A's frame: one thread per leaf maps its one or two triangles with the
+// query's float32 map, the CTA reduces the h levels in shared memory, and the
+// 2^(h+1) - 1 boxes go to the slot in heap order (local root 1).  Every box is
+// the exact bound of float32-mapped vertices, each within e_c of its exact
+// image, so the widening E_box keeps every bound on it valid.
+__device__ void refit_subtree(const KArgs& A, unsigned q, unsigned root, unsigned slot) {
+    __shared__ float sb[kRefitBoxes * 6];
+    QView V;
+    view(A, q, V);
+    const int h = V.LB - V.dR;
+    const unsigned nleaf = 1u << h;
+    for (unsigned i = threadIdx.x; i < nleaf; i += blockDim.x) {
+        unsigned leaf = ((root << h) | i) - (1u << V.LB);
+        unsigned t0 = leaf_first(V.TB, V.LB, leaf), t1 = leaf_first(V.TB, V.LB, leaf + 1);
+        float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+        for (unsigned t = t0; t < t1; ++t) {
+            Tri32 T = load_tri(V.triB, t);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                V3<float> p = map32(V.X, T.v[k].x, T.v[k].y, T.v[k].z);
+                lo[0] = fminf(lo[0], p.x); lo[1] = fminf(lo[1], p.y); lo[2] = fminf(lo[2], p.z);
+                hi[0] = fmaxf(hi[0], p.x); hi[1] = fmaxf(hi[1], p.y); hi[2] = fmaxf(hi[2], p.z);
+            }
+        }
+        float* o = sb + 6 * (nleaf + i);
+        o[0] = lo[0]; o[1] = lo[1]; o[2] = lo[2]; o[3] = hi[0]; o[4] = hi[1]; o[5] = hi[2];
+    }
+    __syncthreads();
+    for (int lev = h - 1; lev >= 0; --lev) {
+        for (unsigned j = threadIdx.x; j < (1u << lev); j += blockDim.x) {
+            unsigned k = (1u << lev) + j;
+            const float* l = sb + 12 * k;
+            float* o = sb + 6 * k;
+            o[0] = fminf(l[0], l[6]); o[1] = fminf(l[1], l[7]); o[2] = fminf(l[2], l[8]);
+            o[3] = fmaxf(l[3], l[9]); o[4] = fmaxf(l[4], l[10]); o[5] = fmaxf(l[5], l[11]);
+        }
+        __syncthreads();
+    }
+    float* dst = A.rbox + (unsigned long long)slot * kRefitBoxes * 6;
+    for (unsigned i = 6 + threadIdx.x; i < 6u * (2u << h); i += blockDim.x) __stcg(dst + i, sb[i]);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        A.slot_of[V.slot_base + (root - (1u << V.dR))] = slot;
+    }
+}
+
+// ------------------------------------------------------------- probes
+
+// Greedy descent from one front entry by one warp: at each step up to 32
+// descendant pairs (5 levels split between the two trees) are bounded, the
+// running bound takes their enhanced bounds (Eq. 10 / Eq. 11), and the walk
+// follows the pair with the best enhanced bound until both nodes are leaves,
+// whose triangle pairs then tighten the bound further.  Probes only move the
+// running bound by valid bounds; they add no front entries or candidates, so
+// the traversal's result does not depend on them.  They exist to reach a
+// near-final bound before the breadth-first levels widen (the sequential
+// depth-first behaviour Section 6 contrasts with).
+template <int KIND>
+__device__ void probe(const KArgs& A, Item it, const QView& V) {
+    const int lane = threadIdx.x & 31;
+    unsigned a = it.a, b = it.b;
+    const unsigned q = it.q;
+    for (int step = 0; step < 64; ++step) {
+        const int remA = V.LA - depth_of(a), remB = V.LB - depth_of(b);
+        if (remA == 0 && remB == 0) break;
+        int kA = min(remA, 3);
+        const int kB = min(remB, 5 - kA);
+        kA = min(remA, 5 - kB);
+        const bool valid = lane < (1 << (kA + kB));
+        const unsigned ia = (a << kA) | ((unsigned)lane >> kB);
+        const unsigned ib = (b << kB) | ((unsigned)lane & ((1u << kB) - 1u));
+        const float Ucur = __uint_as_float(ld_relaxed(&A.qs[q].U));
+        bool ok = false;
+        unsigned newU = KIND == 0 ? 0xffffffffu : 0u, key = 0xffffffffu;
+        if (valid) pair_bounds<KIND>(A, V, ia, ib, depth_of(b) + kB, Ucur, &ok, &newU, &key);
+        warp_bound_update<KIND>(ok, q, newU, A.qs);
+        const unsigned best = __reduce_min_sync(kFull, ok ? key : 0xffffffffu);
+        const unsigned m = __ballot_sync(kFull, ok && key == best);
+        if (m == 0) return;
+        const int src = __ffs(m) - 1;
+        a = __shfl_sync(kFull, ia, src);
+        b = __shfl_sync(kFull, ib, src);
+    }
+    const unsigned la = a - (1u << V.LA), lb = b - (1u << V.LB);
+    const unsigned a0 = leaf_first(V.TA, V.LA, la), a1 = leaf_first(V.TA, V.LA, la + 1);
+    const unsigned b0 = leaf_first(V.TB, V.LB, lb), b1 = leaf_first(V.TB, V.LB, lb + 1);
+    const unsigned ta = a0 + ((unsigned)lane >> 1), tb = b0 + ((unsigned)lane & 1u);
+    const bool valid = lane < 4 && ta < a1 && tb < b1;
+    float lo = 0.f, up = 0.f;
+    if (valid) tri_pair_bounds<KIND>(V, ta, tb, &lo, &up);
+    warp_bound_update<KIND>(valid, q, __float_as_uint(KIND == 0 ? up : lo), A.qs);
 }
 
 // ------------------------------------------------------------- phase 0
@@ -186,9 +490,11 @@ __device__ void setup_query(const KArgs& A, int q, int kind) {
     const MeshDev* mb;
     const double* xa;
     const double* xb;
+    unsigned slot_base = 0;
     if (A.qin) {
         ma = A.qin[q].A; mb = A.qin[q].B;
         xa = A.qin[q].xa; xb = A.qin[q].xb;
+        slot_base = A.qin[q].slot_base;
     } else {
         ma = A.mA; mb = A.mB;
         xa = A.xa_src ? A.xa_src : A.xa_val;
@@ -211,11 +517,15 @@ __device__ void setup_query(const KArgs& A, int q, int kind) {
     for (int i = 0; i < 3; ++i) {
         for (int j = 0; j < 3; ++j) {
             double r = Ai[3 * i] * Xb[j] + Ai[3 * i + 1] * Xb[4 + j] + Ai[3 * i + 2] * Xb[8 + j];
-            s.R[3 * i + j] = (float)r;
+            float h = (float)r;
+            s.R[3 * i + j] = h;
+            s.Rl[3 * i + j] = (float)(r - (double)h);
         }
         double tt = Ai[3 * i] * dt[0] + Ai[3 * i + 1] * dt[1] + Ai[3 * i + 2] * dt[2];
-        s.t[i] = (float)tt;
-        tinf = fmaxf(tinf, fabsf((float)tt));
+        float h = (float)tt;
+        s.t[i] = h;
+        s.tl[i] = (float)(tt - (double)h);
+        tinf = fmaxf(tinf, fabsf(h));
     }
     // widening: every mapped coordinate is within e_c of its exact value,
     // e_c = gamma_10 (sqrt(3) P_B + |t|_inf); E_box = sqrt(3) e_c; the
@@ -230,6 +540,10 @@ __device__ void setup_query(const KArgs& A, int q, int kind) {
     double Et = Eb + 256.0 * u * Xm;
     s.E_box = __double2float_ru(Eb);
     s.E_tri = __double2float_ru(Et);
+    // double-float map (including the shift to A's vertex): about a dozen
+    // roundings of relative size 2^-46 on terms of magnitude
+    // <= P_A + sqrt(3) P_B + |t|, plus the float64 relative map itself
+    s.E_df = __double2float_ru(1e-12 * (PA + 1.7320508075688772 * PB + (double)tinf + 1.0));
     s.A = ma;
     s.B = mb;
     for (int i = 0; i < 12; ++i) { s.xa[i] = Xa[i]; s.xb[i] = Xb[i]; }
@@ -237,6 +551,8 @@ __device__ void setup_query(const KArgs& A, int q, int kind) {
     s.status = 0u;
     s.best_d = kind == 0 ? 0x7ff0000000000000ull : 0ull;  // +inf / +0
     s.best_key = 0xffffffffffffffffull;
+    s.slot_base = slot_base;
+    s.dR = A.refit ? max(0, mb->L - kRefitH) : -1;
 }
 
 // ------------------------------------------------------------- phase 2
@@ -271,10 +587,11 @@ __device__ void expand_level(const KArgs& A, int level, unsigned n, int s, unsig
         }
         unsigned q = it.q;
         view(A, q, V);
-        const int dA = 31 - __clz(it.a), dB = 31 - __clz(it.b);
+        const int dA = depth_of(it.a), dB = depth_of(it.b);
         const int remA = V.LA - dA, remB = V.LB - dB;
         int kA = min((s + 1) >> 1, remA);
         int kB = min(s - kA, remB);
+        if (V.dR >= 0 && dB < V.dR) kB = min(kB, V.dR - dB);  // stop on the refit roots
         kA = min(s - kB, remA);
         unsigned local = (unsigned)(vt & mask);
         valid = valid && local < (1u << (kA + kB));
@@ -284,25 +601,14 @@ __device__ void expand_level(const KArgs& A, int level, unsigned n, int s, unsig
         if (valid && local == 0) bytes += 16ull + 24ull * ((1ull << kA) + (1ull << kB));
         unsigned ia = (it.a << kA) | (local >> kB);
         unsigned ib = (it.b << kB) | (local & ((1u << kB) - 1u));
+        const int dBc = dB + kB;
         bool leafpair = (kA == remA) && (kB == remB);
         bool survive = false;
         float bound = 0.f;
-        unsigned newU = KIND == 0 ? 0xffffffffu : 0u;
+        unsigned newU = KIND == 0 ? 0xffffffffu : 0u, key;
         if (valid) {
             ++pairs;
-            Box ba = load_box(V.boxA, ia);
-            Box bb = load_box(V.boxB, ib);
-            float elo[3], ehi[3];
-            enclose(V.X, bb, elo, ehi);
-            if (KIND == 0) {
-                bound = lower_min_sq(ba, elo, ehi);
-                survive = bound <= min_keep_threshold(Ucur, V.E_box);
-                if (survive) newU = __float_as_uint(upper_from_sq(upper_min_sq_enhanced(V.X, ba, bb), V.E_box));
-            } else {
-                bound = upper_max_sq(ba, elo, ehi);
-                survive = bound >= max_keep_threshold(Ucur, V.E_box);
-                if (survive) newU = __float_as_uint(lower_from_sq(lower_max_sq_enhanced(V.X, ba, bb), V.E_box));
-            }
+            bound = pair_bounds<KIND>(A, V, ia, ib, dBc, Ucur, &survive, &newU, &key);
         }
         warp_bound_update<KIND>(survive, q, newU, A.qs);
         Item o = {ia, ib, bound, q};
@@ -310,6 +616,7 @@ __device__ void expand_level(const KArgs& A, int level, unsigned n, int s, unsig
         bool ok2 = warp_push(survive && leafpair, o, A.leafq, leaf_cnt, A.cap_leaf);
         if (!ok1 || !ok2) mark_overflow(A, q);
         if (survive) bytes += 16ull;
+        if (survive && !leafpair && dBc == V.dR) claim_root(A, V, q, ib);
         // remaining depth of the entries pushed to the next front
         unsigned rem = (survive && !leafpair) ? (unsigned)(remA - kA + remB - kB) : 0u;
         rem = __reduce_max_sync(kFull, rem);
@@ -353,41 +660,14 @@ __device__ void leaf_phase(const KArgs& A, unsigned nleaf, unsigned& tripairs, u
         bool have = false;
         if (valid) {
             ++tripairs;
-            Tri32 TA = load_tri(V.triA, ta), TB = load_tri(V.triB, tb);
-            V3<float> Bw[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) Bw[k] = map32(V.X, TB.v[k].x, TB.v[k].y, TB.v[k].z);
+            float lo, up;
+            tri_pair_bounds_tight<KIND>(A.qs[q], V, ta, tb, &lo, &up);
+            have = true;
             if (KIND == 0) {
-                V3<float> P, Q;
-                float d2;
-                bool hit;
-                tri_tri_min(TA.v, Bw, &P, &Q, &d2, &hit);
-                float up = upper_from_sq(d2, V.E_tri);
-                // lower bound: separation of the two triangles along P - Q
-                float lo = 0.f;
-                V3<float> nrm = P - Q;
-                float nn = dot(nrm, nrm);
-                if (nn > 0.f) {
-                    float amin = FLT_MAX, bmax = -FLT_MAX;
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        amin = fminf(amin, dot(nrm, TA.v[k]));
-                        bmax = fmaxf(bmax, dot(nrm, Bw[k]));
-                    }
-                    float sep = amin - bmax;
-                    if (sep > 0.f) lo = lower_from_dist(sep / sqrtf(nn), V.E_tri);
-                }
-                have = true;
                 newU = __float_as_uint(up);
                 cb = lo;
                 emit = lo <= fminf(Ucur, up);
             } else {
-                V3<float> P, Q;
-                float d2;
-                tri_tri_max(TA.v, Bw, &P, &Q, &d2);
-                float lo = lower_from_sq(d2, V.E_tri);
-                float up = upper_from_sq(d2, V.E_tri);
-                have = true;
                 newU = __float_as_uint(lo);
                 cb = up;
                 emit = up >= fmaxf(Ucur, lo);
@@ -402,34 +682,129 @@ __device__ void leaf_phase(const KArgs& A, unsigned nleaf, unsigned& tripairs, u
 
 // ------------------------------------------------------------- phases 4-6
 
-__device__ __forceinline__ void world_tri(const float4* tri, unsigned j, const double* X, V3<double>* W, int* id) {
-    Tri32 t = load_tri(tri, j);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) W[k] = map64(X, (double)t.v[k].x, (double)t.v[k].y, (double)t.v[k].z);
-    *id = t.id;
-}
-
+// float64 distance of one triangle pair in the world frame, computed by a whole
+// warp.  Min kind: lane f owns feature pair f of tri_feature (21 lanes).  A
+// float32 pass on local coordinates first bounds every feature from both
+// sides (upper: its closest pair; lower: separation of its two point sets,
+// or the plane gap for an edge that does not cross the other plane); only
+// features whose lower bound does not exceed the best upper bound can hold
+// the minimum, and only those run in float64.  Max kind: lane v < 9 owns one
+// vertex pair.  Every lane returns the warp's result; P, Q are a closest
+// (farthest) pair, *ida, *idb the original triangle indices.
 template <int KIND>
-__device__ __forceinline__ double refine_pair(const QState& s, unsigned ta, unsigned tb, V3<double>* P,
-                                              V3<double>* Q, int* ida, int* idb) {
+__device__ __forceinline__ double refine_pair_warp(const QState& s, unsigned ta, unsigned tb, V3<double>* P,
+                                                   V3<double>* Q, int* ida, int* idb) {
+    const int lane = threadIdx.x & 31;
+    Tri32 TA = load_tri(s.A->tri, ta), TB = load_tri(s.B->tri, tb);
+    *ida = TA.id;
+    *idb = TB.id;
+    // lanes 0..5 map one vertex each, then share them
+    V3<double> w = mk3(0.0, 0.0, 0.0);
+    if (lane < 3) w = map64(s.xa, (double)TA.v[lane].x, (double)TA.v[lane].y, (double)TA.v[lane].z);
+    else if (lane < 6)
+        w = map64(s.xb, (double)TB.v[lane - 3].x, (double)TB.v[lane - 3].y, (double)TB.v[lane - 3].z);
     V3<double> Aw[3], Bw[3];
-    world_tri(s.A->tri, ta, s.xa, Aw, ida);
-    world_tri(s.B->tri, tb, s.xb, Bw, idb);
-    double d2;
-    if (KIND == 0) {
-        bool hit;
-        tri_tri_min(Aw, Bw, P, Q, &d2, &hit);
-        if (hit) return 0.0;
-    } else {
-        tri_tri_max(Aw, Bw, P, Q, &d2);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        Aw[k] = mk3(__shfl_sync(kFull, w.x, k), __shfl_sync(kFull, w.y, k), __shfl_sync(kFull, w.z, k));
+        Bw[k] = mk3(__shfl_sync(kFull, w.x, 3 + k), __shfl_sync(kFull, w.y, 3 + k), __shfl_sync(kFull, w.z, 3 + k));
     }
-    return sqrt(d2);
+    V3<double> p = Aw[0], qq = Bw[0];
+    double d2 = INFINITY;
+    bool hit = false;
+    if (KIND == 0) {
+        // float32 pre-pass on coordinates local to A's first vertex
+        V3<float> Al[3], Bl[3];
+        float X = 0.f;
+        double W = 0.0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            V3<double> a = Aw[k] - Aw[0], b = Bw[k] - Aw[0];
+            Al[k] = mk3((float)a.x, (float)a.y, (float)a.z);
+            Bl[k] = mk3((float)b.x, (float)b.y, (float)b.z);
+            X = fmaxf(X, fmaxf(max_abs3(Al[k]), max_abs3(Bl[k])));
+            W = fmax(W, fmax(fmax(fabs(Aw[k].x), fabs(Aw[k].y)), fabs(Aw[k].z)));
+            W = fmax(W, fmax(fmax(fabs(Bw[k].x), fabs(Bw[k].y)), fabs(Bw[k].z)));
+        }
+        const float E = __fadd_ru(__double2float_ru(1e-15 * (W + 1.0)), __fmul_ru(256.0f * kU * 1.001f, X));
+        float upf = INFINITY, lof = INFINITY;
+        if (lane < 21) {
+            V3<float> p32, q32;
+            float d32;
+            bool h32;
+            tri_feature(lane, Al, Bl, &p32, &q32, &d32, &h32);
+            V3<float> FA[3], FB[3];
+            feature_points(lane, Al, Bl, FA, FB);
+            if (d32 < INFINITY) {
+                upf = upper_from_sq(d32, E);
+                lof = 0.f;
+                V3<float> n = p32 - q32;
+                float nn = dot(n, n);
+                if (!h32 && nn > 0.f) {
+                    float amin = FLT_MAX, bmax = -FLT_MAX;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        amin = fminf(amin, dot(n, FA[k]));
+                        bmax = fmaxf(bmax, dot(n, FB[k]));
+                    }
+                    if (amin - bmax > 0.f) lof = lower_from_dist((amin - bmax) / sqrtf(nn), E);
+                }
+            } else {
+                // an edge that does not cross the other triangle's plane: the
+                // plane keeps it at least its nearer endpoint's plane distance away
+                const bool ea = lane < 18;
+                const V3<float>* F = ea ? Bl : Al;
+                const V3<float>* Ed = ea ? FA : FB;
+                V3<float> n = cross(F[1] - F[0], F[2] - F[0]);
+                float nn = dot(n, n);
+                lof = 0.f;
+                if (nn > 0.f) {
+                    float s0 = dot(n, Ed[0] - F[0]), s1 = dot(n, Ed[1] - F[0]);
+                    if ((s0 > 0.f && s1 > 0.f) || (s0 < 0.f && s1 < 0.f))
+                        lof = lower_from_dist(fminf(fabsf(s0), fabsf(s1)) / sqrtf(nn), E);
+                }
+            }
+        }
+        // non-negative floats order like their bit patterns
+        const float minUp = __uint_as_float(__reduce_min_sync(kFull, __float_as_uint(upf)));
+        if (lane < 21 && lof <= minUp) tri_feature(lane, Aw, Bw, &p, &qq, &d2, &hit);
+    } else {
+        if (lane < 9) {
+            p = Aw[lane / 3];
+            qq = Bw[lane % 3];
+            V3<double> d = p - qq;
+            d2 = -dot(d, d);  // reduce with min
+        }
+    }
+    const unsigned hits = __ballot_sync(kFull, hit);
+    int win;
+    double best;
+    if (hits) {
+        win = __ffs(hits) - 1;
+        best = 0.0;
+    } else {
+        // (d2, lane) lexicographic minimum over the warp
+        best = d2;
+        win = lane;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            double ob = __shfl_xor_sync(kFull, best, o);
+            int ow = __shfl_xor_sync(kFull, win, o);
+            if (ob < best || (ob == best && ow < win)) { best = ob; win = ow; }
+        }
+    }
+    P->x = __shfl_sync(kFull, p.x, win); P->y = __shfl_sync(kFull, p.y, win); P->z = __shfl_sync(kFull, p.z, win);
+    Q->x = __shfl_sync(kFull, qq.x, win); Q->y = __shfl_sync(kFull, qq.y, win); Q->z = __shfl_sync(kFull, qq.z, win);
+    if (KIND == 0) return hits ? 0.0 : sqrt(best);
+    return sqrt(-best);
 }
 
+// float64 refinement, one warp per candidate (warps first_warp, +wstride, ...)
 template <int KIND>
-__device__ void refine_phase(const KArgs& A, unsigned ncand, unsigned& refined, unsigned long long& bytes) {
-    const unsigned long long gstride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < ncand; i += gstride) {
+__device__ void refine_phase(const KArgs& A, unsigned ncand, unsigned& refined, unsigned long long& bytes,
+                             unsigned long long first_warp, unsigned long long wstride) {
+    const int lane = threadIdx.x & 31;
+    for (unsigned long long i = first_warp; i < ncand; i += wstride) {
         float4 raw = __ldcg(reinterpret_cast<const float4*>(A.cand + i));
         Cand c = *reinterpret_cast<Cand*>(&raw);
         QState& s = A.qs[c.q];
@@ -439,20 +814,23 @@ __device__ void refine_phase(const KArgs& A, unsigned ncand, unsigned& refined, 
         if (keep) {
             V3<double> P, Q;
             int ia, ib;
-            d = refine_pair<KIND>(s, c.ta, c.tb, &P, &Q, &ia, &ib);
-            unsigned long long bits = (unsigned long long)__double_as_longlong(d);
-            if (KIND == 0) atomicMin(&s.best_d, bits);
-            else atomicMax(&s.best_d, bits);
-            ++refined;
-            bytes += 16ull + 72ull;
+            d = refine_pair_warp<KIND>(s, c.ta, c.tb, &P, &Q, &ia, &ib);
+            if (lane == 0) {
+                double* w = A.cand_pts + 6ull * i;
+                w[0] = P.x; w[1] = P.y; w[2] = P.z; w[3] = Q.x; w[4] = Q.y; w[5] = Q.z;
+                unsigned long long bits = (unsigned long long)__double_as_longlong(d);
+                if (KIND == 0) atomicMin(&s.best_d, bits);
+                else atomicMax(&s.best_d, bits);
+                ++refined;
+                bytes += 16ull + 72ull;
+            }
         }
-        A.cand_d[i] = d;
+        if (lane == 0) A.cand_d[i] = d;
     }
 }
 
-__device__ void select_phase(const KArgs& A, unsigned ncand) {
-    const unsigned long long gstride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < ncand; i += gstride) {
+__device__ void select_phase(const KArgs& A, unsigned ncand, unsigned long long first, unsigned long long gstride) {
+    for (unsigned long long i = first; i < ncand; i += gstride) {
         double d = __ldcg(A.cand_d + i);
         float4 raw = __ldcg(reinterpret_cast<const float4*>(A.cand + i));
         Cand c = *reinterpret_cast<Cand*>(&raw);
@@ -465,10 +843,10 @@ __device__ void select_phase(const KArgs& A, unsigned ncand) {
     }
 }
 
-template <int KIND>
-__device__ void finalize_phase(const KArgs& A, unsigned ncand) {
-    const unsigned long long gstride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < ncand; i += gstride) {
+// the witness record of each query: the candidate at the extreme with the
+// smallest original (tri_a, tri_b); its points were stored by the refinement
+__device__ void finalize_phase(const KArgs& A, unsigned ncand, unsigned long long first, unsigned long long gstride) {
+    for (unsigned long long i = first; i < ncand; i += gstride) {
         double d = __ldcg(A.cand_d + i);
         float4 raw = __ldcg(reinterpret_cast<const float4*>(A.cand + i));
         Cand c = *reinterpret_cast<Cand*>(&raw);
@@ -477,22 +855,18 @@ __device__ void finalize_phase(const KArgs& A, unsigned ncand) {
         unsigned ia = (unsigned)__float_as_int(__ldg(s.A->tri + 3ull * c.ta + 2).y);
         unsigned ib = (unsigned)__float_as_int(__ldg(s.B->tri + 3ull * c.tb + 2).y);
         if ((((unsigned long long)ia << 32) | ib) != ld_relaxed64(&s.best_key)) continue;
-        V3<double> P, Q;
-        int da, db;
-        double dd = refine_pair<KIND>(s, c.ta, c.tb, &P, &Q, &da, &db);
+        const double* w = A.cand_pts + 6ull * i;
         gd_result& r = A.out[c.q];
-        r.d = dd;
+        r.d = d;
         r.tri_a = ia;
         r.tri_b = ib;
-        r.pa[0] = P.x; r.pa[1] = P.y; r.pa[2] = P.z;
-        r.pb[0] = Q.x; r.pb[1] = Q.y; r.pb[2] = Q.z;
+        r.pa[0] = __ldcg(w); r.pa[1] = __ldcg(w + 1); r.pa[2] = __ldcg(w + 2);
+        r.pb[0] = __ldcg(w + 3); r.pb[1] = __ldcg(w + 4); r.pb[2] = __ldcg(w + 5);
     }
 }
 
-__device__ void status_phase(const KArgs& A) {
-    const unsigned long long gstride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < (unsigned)A.nq;
-         q += gstride) {
+__device__ void status_phase(const KArgs& A, unsigned long long first, unsigned long long gstride) {
+    for (unsigned long long q = first; q < (unsigned)A.nq; q += gstride) {
         QState& s = A.qs[q];
         unsigned st = s.status;
         if (s.best_key == 0xffffffffffffffffull) st |= kStatNoResult;
@@ -510,30 +884,66 @@ __device__ void status_phase(const KArgs& A) {
     }
 }
 
+// Run the refit jobs appended since the last call (one job per CTA at a time);
+// returns false if the grid barrier after them failed; *ran tells whether
+// there were any.
+__device__ bool refit_jobs(const KArgs& A, bool lead, unsigned& refits, bool* ran) {
+    unsigned jobs = ld_relaxed(A.ctr + kCtrJobs), done = ld_relaxed(A.ctr + kCtrJobsDone);
+    if (jobs > A.cap_slots) jobs = A.cap_slots;
+    *ran = jobs > done;
+    if (jobs <= done) return true;
+    for (unsigned j = done + blockIdx.x; j < jobs; j += gridDim.x) {
+        uint2 job = __ldcg(A.jobs + j);
+        refit_subtree(A, job.x, job.y, j);
+    }
+    if (!grid_sync(A)) return false;
+    if (lead) {
+        A.ctr[kCtrJobsDone] = jobs;
+        refits = jobs;
+    }
+    return true;
+}
+
 // ------------------------------------------------------------- kernel
 
 template <int KIND>
 __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
     unsigned long long pairs = 0, bytes = 0;
-    unsigned tripairs = 0, refined = 0;
+    unsigned tripairs = 0, refined = 0, refits = 0;
+    bool probed = false;
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    const unsigned long long gfirst = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned long long gstride = (unsigned long long)gridDim.x * blockDim.x;
+    unsigned long long t_start = globaltimer(), t_mark = t_start, t_levels = 0;
+    auto lap = [&](int slot) {
+        if (lead) {
+            unsigned long long now = globaltimer();
+            if (slot >= 0) A.stats->phase_ns[slot] += (unsigned)(now - t_mark);
+            t_mark = now;
+        }
+    };
 
     // phase 0
     if (blockIdx.x == 0)
         for (int i = threadIdx.x; i < kCtrReset; i += blockDim.x) A.ctr[i] = 0u;
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < A.nq; q += gridDim.x * blockDim.x)
-        setup_query(A, q, KIND);
+    for (int q = (int)gfirst; q < A.nq; q += (int)gstride) setup_query(A, q, KIND);
+    for (unsigned long long i = gfirst; i < A.n_slot_of; i += gstride) A.slot_of[i] = kNoSlot;
     if (lead) {
         StatsDev* S = A.stats;
         S->levels = 0;
         S->pairs_tested = 0;
         S->leaf_pairs = S->tri_pairs = S->candidates = S->refined = 0;
         S->alg_bytes = 0;
+        S->probes = 0;
+        S->refits = 0;
+        S->u_probe = 0.f;
+        for (int i = 0; i < 12; ++i) S->phase_ns[i] = 0;
+        for (int i = 0; i < 32; ++i) { S->level_ns[i] = 0; S->u_level[i] = 0.f; }
     }
     if (!grid_sync(A)) goto done;
 
     // phase 1: root pairs
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < A.nq; q += gridDim.x * blockDim.x) {
+    for (int q = (int)gfirst; q < A.nq; q += (int)gstride) {
         const QState& s = A.qs[q];
         int LA = s.A->L, LB = s.B->L;
         Item it = {1u, 1u, KIND == 0 ? 0.f : FLT_MAX, (unsigned)q};
@@ -544,9 +954,15 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
             unsigned i = atomicAdd(A.ctr + kCtrCnt, 1u);
             if (i < A.cap_front) A.front0[i] = it; else mark_overflow(A, q);
             atomicMax(A.ctr + kCtrRem, (unsigned)(LA + LB));
+            if (s.dR == 0) {
+                QView V;
+                view(A, q, V);
+                claim_root(A, V, q, 1u);
+            }
         }
     }
     if (!grid_sync(A)) goto done;
+    lap(0);
 
     // phase 2: BVTT levels
     for (int level = 0;; ++level) {
@@ -557,6 +973,33 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
             if (lead) atomicOr(A.ctr + kCtrOverflow, 2u);
             break;
         }
+        bool ran = false;
+        if (!refit_jobs(A, lead, refits, &ran)) goto done;
+        if (ran) lap(1);
+        if (!probed && (A.refit ? ran : level == 1)) {
+            // probes start where B's boxes are first exact in A's frame (or
+            // at level 1 without refit), so that their greedy choices follow
+            // tight boxes
+            probed = true;
+            // greedy probes from entries spread evenly over the front: every
+            // warp takes one (at least one per query when the grid allows)
+            const unsigned nwarps = gridDim.x * (blockDim.x >> 5);
+            const unsigned wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+            const unsigned P = min(n, min(nwarps, max((unsigned)A.nq, (unsigned)A.probes)));
+            const Item* in = (level & 1) ? A.front1 : A.front0;
+            QView V;
+            for (unsigned p = wid; p < P; p += nwarps) {
+                unsigned idx = (unsigned)(((unsigned long long)p * n) / P);
+                float4 raw = __ldcg(reinterpret_cast<const float4*>(in + idx));
+                Item it = *reinterpret_cast<Item*>(&raw);
+                view(A, it.q, V);
+                probe<KIND>(A, it, V);
+            }
+            if (lead) A.stats->probes = P;
+            if (!grid_sync(A)) goto done;
+            if (lead) A.stats->u_probe = __uint_as_float(ld_relaxed(&A.qs[0].U));
+            lap(2);
+        }
         unsigned rmax = ld_relaxed(A.ctr + kCtrRem + level % 3);
         int k = adaptive_k(n, A.work_target, A.k_max);
         int s = min(2 * k, (int)rmax);
@@ -564,12 +1007,23 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
         if (lead) {
             A.ctr[kCtrCnt + (level + 2) % 3] = 0u;
             A.ctr[kCtrRem + (level + 2) % 3] = 0u;
-            if (level < 32) { A.stats->front[level] = n; A.stats->slots[level] = (unsigned)s; }
+            if (level < 32) {
+                A.stats->front[level] = n;
+                A.stats->slots[level] = (unsigned)s;
+                A.stats->u_level[level] = __uint_as_float(ld_relaxed(&A.qs[0].U));
+            }
             A.stats->levels = level + 1;
         }
         expand_level<KIND>(A, level, n, s, pairs, bytes);
         if (!grid_sync(A)) goto done;
+        if (lead) {
+            unsigned long long now = globaltimer();
+            if (level < 32) A.stats->level_ns[level] = (unsigned)(now - t_mark);
+            t_levels += now - t_mark;
+            t_mark = now;
+        }
     }
+    if (lead) A.stats->phase_ns[3] = (unsigned)t_levels;
 
     // phase 3
     {
@@ -579,29 +1033,71 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
         leaf_phase<KIND>(A, nleaf, tripairs, bytes);
     }
     if (!grid_sync(A)) goto done;
-    // phase 4
+    lap(4);
     {
         unsigned nc = ld_relaxed(A.ctr + kCtrCand);
         if (nc > A.cap_cand) nc = A.cap_cand;
         if (lead) A.stats->candidates = nc;
-        refine_phase<KIND>(A, nc, refined, bytes);
+        if (nc <= gridDim.x) {
+            // few candidates: one per CTA (its warp 0), spread over the SMs'
+            // float64 pipes; CTA 0 waits for the others (bounded) and then
+            // selects the witness alone, so no grid-wide barrier is needed
+            if (threadIdx.x < 32) refine_phase<KIND>(A, nc, refined, bytes, blockIdx.x, gridDim.x);
+            __syncthreads();
+            lap(5);
+            if (threadIdx.x == 0 && blockIdx.x < nc) {
+                __threadfence();
+                atomicAdd(A.ctr + kCtrTailDone, 1u);
+            }
+            if (blockIdx.x == 0) {
+                __shared__ int s_go;
+                if (threadIdx.x == 0) {
+                    int go = 1;
+                    unsigned long long t0 = globaltimer();
+                    while (ld_acquire(A.ctr + kCtrTailDone) < nc) {
+                        if (ld_relaxed(A.ctr + kCtrAbort)) { go = 0; break; }
+                        if ((long long)(globaltimer() - t0) > A.timeout_ns) {
+                            atomicExch(A.ctr + kCtrAbort, 1u);
+                            go = 0;
+                            break;
+                        }
+                        __nanosleep(32);
+                    }
+                    __threadfence();
+                    s_go = go;
+                }
+                __syncthreads();
+                if (s_go) {
+                    lap(6);
+                    select_phase(A, nc, threadIdx.x, blockDim.x);
+                    __syncthreads();
+                    lap(7);
+                    finalize_phase(A, nc, threadIdx.x, blockDim.x);
+                    __syncthreads();
+                    status_phase(A, threadIdx.x, blockDim.x);
+                    __syncthreads();
+                    lap(8);
+                }
+            }
+            goto done;
+        }
+        refine_phase<KIND>(A, nc, refined, bytes, gfirst >> 5, gstride >> 5);
+        if (!grid_sync(A)) goto done;
+        lap(5);
+        select_phase(A, nc, gfirst, gstride);
+        if (!grid_sync(A)) goto done;
+        lap(7);
+        finalize_phase(A, nc, gfirst, gstride);
+        if (!grid_sync(A)) goto done;
+        status_phase(A, gfirst, gstride);
+        lap(8);
     }
-    if (!grid_sync(A)) goto done;
-    {
-        unsigned nc = ld_relaxed(A.ctr + kCtrCand);
-        if (nc > A.cap_cand) nc = A.cap_cand;
-        select_phase(A, nc);
-    }
-    if (!grid_sync(A)) goto done;
-    {
-        unsigned nc = ld_relaxed(A.ctr + kCtrCand);
-        if (nc > A.cap_cand) nc = A.cap_cand;
-        finalize_phase<KIND>(A, nc);
-    }
-    if (!grid_sync(A)) goto done;
-    status_phase(A);
 
 done:
+    if (lead) {
+        A.stats->phase_ns[9] = (unsigned)(globaltimer() - t_start);
+        A.stats->refits = refits;
+    }
     // per-CTA statistics
     {
         __shared__ unsigned long long s_pairs, s_bytes;

@@ -68,8 +68,9 @@ namespace {
 void free_slot(Slot& s) {
     SlotBuffers& b = s.b;
     if (b.stream) cudaStreamSynchronize(b.stream);
-    cudaFree(b.front[0]); cudaFree(b.front[1]); cudaFree(b.leafq); cudaFree(b.cand); cudaFree(b.cand_d);
+    cudaFree(b.front[0]); cudaFree(b.front[1]); cudaFree(b.leafq); cudaFree(b.cand); cudaFree(b.cand_d); cudaFree(b.cand_pts);
     cudaFree(b.qs); cudaFree(b.qin_dev); cudaFree(b.out_dev); cudaFree(b.mb_dev_ctr); cudaFree(b.stats_dev);
+    cudaFree(b.rbox); cudaFree(b.jobs); cudaFree(b.slot_of);
     cudaFreeHost(b.qin_host); cudaFreeHost(b.out_host); cudaFreeHost(b.ctr_host);
     if (b.stream) cudaStreamDestroy(b.stream);
     b = SlotBuffers{};
@@ -90,6 +91,7 @@ bool alloc_slot(Slot& s, long long budget, long long max_batch, int grid) {
     ok = ok && cudaMalloc(&b.leafq, sizeof(Item) * b.cap_leaf) == cudaSuccess;
     ok = ok && cudaMalloc(&b.cand, sizeof(Cand) * b.cap_cand) == cudaSuccess;
     ok = ok && cudaMalloc(&b.cand_d, sizeof(double) * b.cap_cand) == cudaSuccess;
+    ok = ok && cudaMalloc(&b.cand_pts, sizeof(double) * 6 * b.cap_cand) == cudaSuccess;
     ok = ok && cudaMalloc(&b.qs, sizeof(QState) * b.cap_q) == cudaSuccess;
     ok = ok && cudaMalloc(&b.qin_dev, sizeof(QIn) * b.cap_q) == cudaSuccess;
     ok = ok && cudaMalloc(&b.out_dev, sizeof(gd_result) * b.cap_q) == cudaSuccess;
@@ -99,6 +101,12 @@ bool alloc_slot(Slot& s, long long budget, long long max_batch, int grid) {
     ok = ok && cudaMallocHost(&b.qin_host, sizeof(QIn) * b.cap_q) == cudaSuccess;
     ok = ok && cudaMallocHost(&b.out_host, sizeof(gd_result) * b.cap_q) == cudaSuccess;
     ok = ok && cudaMallocHost(&b.ctr_host, sizeof(unsigned) * kCtrWords) == cudaSuccess;
+    // refit slots (12 KB each) and root tables for up to 4096 roots per query
+    b.cap_slots = 2048;
+    b.cap_table = 4096ll * max_batch;
+    ok = ok && cudaMalloc(&b.rbox, sizeof(float) * 6 * kRefitBoxes * (size_t)b.cap_slots) == cudaSuccess;
+    ok = ok && cudaMalloc(&b.jobs, sizeof(uint2) * (size_t)b.cap_slots) == cudaSuccess;
+    ok = ok && cudaMalloc(&b.slot_of, sizeof(unsigned) * (size_t)b.cap_table) == cudaSuccess;
     return ok;
 }
 

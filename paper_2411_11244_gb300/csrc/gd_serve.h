@@ -14,6 +14,7 @@ struct SlotBuffers {
     Item* leafq = nullptr;
     Cand* cand = nullptr;
     double* cand_d = nullptr;
+    double* cand_pts = nullptr;
     long long cap_front = 0, cap_leaf = 0, cap_cand = 0;
     QState* qs = nullptr;
     QIn* qin_dev = nullptr;
@@ -23,6 +24,11 @@ struct SlotBuffers {
     unsigned* mb_dev_ctr = nullptr;
     unsigned* ctr_host = nullptr;
     StatsDev* stats_dev = nullptr;
+    float* rbox = nullptr;
+    uint2* jobs = nullptr;
+    long long cap_slots = 0;
+    unsigned* slot_of = nullptr;
+    long long cap_table = 0;
     long long cap_q = 0;
     int grid = 0;
 };

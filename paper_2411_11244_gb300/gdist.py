@@ -54,21 +54,30 @@ class gd_build_opts(C.Structure):
 class gd_tunables(C.Structure):
     _fields_ = [("work_target", C.c_int64), ("k_max", C.c_int32), ("blocks_per_sm", C.c_int32),
                 ("front_capacity", C.c_int64), ("leaf_capacity", C.c_int64), ("cand_capacity", C.c_int64),
-                ("max_capacity", C.c_int64), ("timeout_ns", C.c_int64)]
+                ("max_capacity", C.c_int64), ("timeout_ns", C.c_int64), ("refit_mode", C.c_int32),
+                ("refit_slots", C.c_int32), ("probes", C.c_int32)]
 
 
 class gd_stats(C.Structure):
     _fields_ = [("levels", C.c_uint32), ("front", C.c_uint32 * 32), ("slots", C.c_uint32 * 32),
                 ("pairs_tested", C.c_uint64), ("leaf_pairs", C.c_uint32), ("tri_pairs", C.c_uint32),
                 ("candidates", C.c_uint32), ("refined", C.c_uint32), ("alg_bytes", C.c_uint64),
-                ("retries", C.c_uint32), ("blocks", C.c_uint32)]
+                ("retries", C.c_uint32), ("blocks", C.c_uint32), ("level_ns", C.c_uint32 * 32),
+                ("phase_ns", C.c_uint32 * 12), ("probes", C.c_uint32), ("u_level", C.c_float * 32),
+                ("u_probe", C.c_float), ("refits", C.c_uint32)]
+
+    PHASES = ("setup", "refit", "probe", "levels", "leaf", "refine", "tail_wait", "select", "finalize", "total")
 
     def as_dict(self):
         n = self.levels
         return {"levels": n, "front": list(self.front[:min(n, 32)]), "slots": list(self.slots[:min(n, 32)]),
                 "pairs_tested": self.pairs_tested, "leaf_pairs": self.leaf_pairs, "tri_pairs": self.tri_pairs,
                 "candidates": self.candidates, "refined": self.refined, "alg_bytes": self.alg_bytes,
-                "retries": self.retries, "blocks": self.blocks}
+                "retries": self.retries, "blocks": self.blocks,
+                "level_us": [x / 1000.0 for x in self.level_ns[:min(n, 32)]],
+                "phase_us": {k: self.phase_ns[i] / 1000.0 for i, k in enumerate(self.PHASES)},
+                "probes": self.probes, "u_level": list(self.u_level[:min(n, 32)]), "u_probe": self.u_probe,
+                "refits": self.refits}
 
 
 class gd_serve_opts(C.Structure):

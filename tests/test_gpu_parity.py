@@ -90,7 +90,7 @@ def _morton_np(v, t, bits=21):
     used = v[np.unique(t)]
     lo = used.min(0)
     hi = used.max(0)
-    ext = (hi - lo).astype(np.float32)
+    ext = np.full(3, (hi - lo).astype(np.float32).max(), dtype=np.float32)
     s = (v[t[:, 0]] + v[t[:, 1]]).astype(np.float32) + v[t[:, 2]]
     x = (s * np.float32(1.0 / 3.0)).astype(np.float32) - lo
     cells = np.float32(1 << bits)
@@ -261,6 +261,29 @@ def test_batch_matches_single(G, ctx, oracle_mod):
         assert (out[i].tri_a, out[i].tri_b) == (r.tri_a, r.tri_b)
     for h in (ma, mb, mt):
         G.gd_mesh_destroy(h)
+
+
+def test_refit_modes_agree(G, oracle_mod):
+    """Refitting B's low subtrees only tightens bounds: the answer (value and
+    witness) is the same with and without it."""
+    rng = np.random.default_rng(31)
+    c = G.gd_ctx_create(0)
+    try:
+        A = synth.torus(1.0, 0.1, 96, 40)
+        B = synth.geosphere(20, 0.5, 1e-3, 3)
+        ma, mb = _mesh(G, c, A), _mesh(G, c, B)
+        for i in range(6):
+            xa, xb = _rigid(rng, 0.3), _rigid(rng, 1.2)
+            for fn in (G.gd_min_distance, G.gd_max_distance):
+                G.gd_ctx_set_tunables(c, refit_mode=1)
+                r1 = fn(c, ma, mb, xa, xb)
+                G.gd_ctx_set_tunables(c, refit_mode=2)
+                r2 = fn(c, ma, mb, xa, xb)
+                assert r1.d == r2.d and (r1.tri_a, r1.tri_b) == (r2.tri_a, r2.tri_b)
+        G.gd_mesh_destroy(ma)
+        G.gd_mesh_destroy(mb)
+    finally:
+        G.gd_ctx_destroy(c)
 
 
 def test_device_resident_query(G, ctx, oracle_mod):
