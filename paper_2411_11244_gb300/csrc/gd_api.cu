@@ -275,6 +275,8 @@ gd_status run_single(gd_ctx* ctx, const gd_mesh* A, const gd_mesh* B, int kind, 
         to_stats(m.stats, (unsigned)grid, retries, &ctx->last);
         ctx->stats_pending = false;
         if (m.ctr[kCtrLastAbort]) return fail(ctx, GD_ERR_TIMEOUT, "a device-side wait timed out");
+        if (m.ctr[kCtrBadIndex])
+            return fail(ctx, GD_ERR_CUDA, "internal index check failed (sites " + std::to_string(m.ctr[kCtrBadIndex]) + ")");
         if (m.out.status == GD_ERR_OVERFLOW) {
             if (!grow(ctx)) return fail(ctx, GD_ERR_OVERFLOW, "work queues exceeded max_capacity");
             ++retries;
@@ -607,6 +609,9 @@ GD_API gd_status gd_batch_query(gd_ctx* ctx, const gd_query* q, int64_t n, gd_re
         agg.blocks = st.blocks;
         for (int i = 0; i < 32; ++i) { agg.front[i] += st.front[i]; agg.slots[i] = std::max(agg.slots[i], st.slots[i]); }
         if (ctx->mb_host->ctr[kCtrLastAbort]) return fail(ctx, GD_ERR_TIMEOUT, "a device-side wait timed out");
+        if (ctx->mb_host->ctr[kCtrBadIndex])
+            return fail(ctx, GD_ERR_CUDA,
+                        "internal index check failed (sites " + std::to_string(ctx->mb_host->ctr[kCtrBadIndex]) + ")");
         std::vector<int64_t> redo;
         for (long long j = 0; j < m; ++j) {
             out[idx[j]] = ctx->out_host[j];

@@ -155,6 +155,20 @@ __device__ __forceinline__ void warp_bound_update(bool have, unsigned q, unsigne
     }
 }
 
+// Defensive index checks: a record read back from a work buffer must name a
+// query of this launch and nodes / triangles of its meshes.  A failed check
+// sets a bit in the counters (the host reports an internal error) and the
+// access is skipped, so a bad record can never become an out-of-range load.
+enum : unsigned {
+    kBadFront = 1u, kBadLeaf = 2u, kBadCand = 4u, kBadJob = 8u, kBadProbe = 16u,
+};
+
+__device__ __forceinline__ bool item_ok(const KArgs& A, const Item& it) {
+    return it.q < (unsigned)A.nq && it.a >= 1u && it.b >= 1u;
+}
+
+__device__ __forceinline__ void flag_bad(const KArgs& A, unsigned bit) { atomicOr(A.ctr + kCtrBadIndex, bit); }
+
 __device__ __forceinline__ void mark_overflow(const KArgs& A, unsigned q) {
     atomicOr(&A.qs[q].status, kStatOverflow);
     atomicOr(A.ctr + kCtrOverflow, 1u);
@@ -584,11 +598,22 @@ __device__ void expand_level(const KArgs& A, int level, unsigned n, int s, unsig
         if (valid) {
             float4 raw = __ldcg(reinterpret_cast<const float4*>(in + (vt >> s)));
             it = *reinterpret_cast<Item*>(&raw);
+            if (!item_ok(A, it)) {
+                flag_bad(A, kBadFront);
+                it = Item{1u, 1u, 0.f, 0u};
+                valid = false;
+            }
         }
         unsigned q = it.q;
         view(A, q, V);
         const int dA = depth_of(it.a), dB = depth_of(it.b);
-        const int remA = V.LA - dA, remB = V.LB - dB;
+        int remA = V.LA - dA, remB = V.LB - dB;
+        if (remA < 0 || remB < 0) {
+            if (valid) flag_bad(A, kBadFront);
+            valid = false;
+            remA = max(remA, 0);
+            remB = max(remB, 0);
+        }
         int kA = min((s + 1) >> 1, remA);
         int kB = min(s - kA, remB);
         if (V.dR >= 0 && dB < V.dR) kB = min(kB, V.dR - dB);  // stop on the refit roots
@@ -641,9 +666,18 @@ __device__ void leaf_phase(const KArgs& A, unsigned nleaf, unsigned& tripairs, u
         if (valid) {
             float4 raw = __ldcg(reinterpret_cast<const float4*>(A.leafq + (vt >> 2)));
             it = *reinterpret_cast<Item*>(&raw);
+            if (!item_ok(A, it)) {
+                flag_bad(A, kBadLeaf);
+                it = Item{1u, 1u, 0.f, 0u};
+                valid = false;
+            }
         }
         unsigned q = it.q;
         view(A, q, V);
+        if (valid && (depth_of(it.a) != V.LA || depth_of(it.b) != V.LB)) {
+            flag_bad(A, kBadLeaf);
+            valid = false;
+        }
         unsigned sub = (unsigned)(vt & 3);
         unsigned la = it.a - (1u << V.LA), lb = it.b - (1u << V.LB);
         unsigned a0 = leaf_first(V.TA, V.LA, la), a1 = leaf_first(V.TA, V.LA, la + 1);
@@ -807,6 +841,14 @@ __device__ void refine_phase(const KArgs& A, unsigned ncand, unsigned& refined, 
     for (unsigned long long i = first_warp; i < ncand; i += wstride) {
         float4 raw = __ldcg(reinterpret_cast<const float4*>(A.cand + i));
         Cand c = *reinterpret_cast<Cand*>(&raw);
+        if (c.q >= (unsigned)A.nq || c.ta >= (unsigned)A.qs[c.q < (unsigned)A.nq ? c.q : 0].A->T ||
+            c.tb >= (unsigned)A.qs[c.q < (unsigned)A.nq ? c.q : 0].B->T) {
+            if (lane == 0) {
+                flag_bad(A, kBadCand);
+                A.cand_d[i] = __longlong_as_double(-1ll);
+            }
+            continue;
+        }
         QState& s = A.qs[c.q];
         float U = __uint_as_float(ld_relaxed(&s.U));
         bool keep = KIND == 0 ? (c.bound <= U) : (c.bound >= U);
@@ -834,6 +876,7 @@ __device__ void select_phase(const KArgs& A, unsigned ncand, unsigned long long 
         double d = __ldcg(A.cand_d + i);
         float4 raw = __ldcg(reinterpret_cast<const float4*>(A.cand + i));
         Cand c = *reinterpret_cast<Cand*>(&raw);
+        if (c.q >= (unsigned)A.nq) continue;  // flagged by the refinement
         QState& s = A.qs[c.q];
         if ((unsigned long long)__double_as_longlong(d) == ld_relaxed64(&s.best_d)) {
             unsigned ia = (unsigned)__float_as_int(__ldg(s.A->tri + 3ull * c.ta + 2).y);
@@ -850,6 +893,7 @@ __device__ void finalize_phase(const KArgs& A, unsigned ncand, unsigned long lon
         double d = __ldcg(A.cand_d + i);
         float4 raw = __ldcg(reinterpret_cast<const float4*>(A.cand + i));
         Cand c = *reinterpret_cast<Cand*>(&raw);
+        if (c.q >= (unsigned)A.nq) continue;  // flagged by the refinement
         QState& s = A.qs[c.q];
         if ((unsigned long long)__double_as_longlong(d) != ld_relaxed64(&s.best_d)) continue;
         unsigned ia = (unsigned)__float_as_int(__ldg(s.A->tri + 3ull * c.ta + 2).y);
@@ -894,7 +938,13 @@ __device__ bool refit_jobs(const KArgs& A, bool lead, unsigned& refits, bool* ra
     if (jobs <= done) return true;
     for (unsigned j = done + blockIdx.x; j < jobs; j += gridDim.x) {
         uint2 job = __ldcg(A.jobs + j);
-        refit_subtree(A, job.x, job.y, j);
+        bool ok = job.x < (unsigned)A.nq && job.y >= 1u;
+        if (ok) {
+            const QState& qsj = A.qs[job.x];
+            ok = qsj.dR >= 0 && depth_of(job.y) == qsj.dR && qsj.B->L >= qsj.dR;
+        }
+        if (ok) refit_subtree(A, job.x, job.y, j);
+        else if (threadIdx.x == 0) flag_bad(A, kBadJob);
     }
     if (!grid_sync(A)) return false;
     if (lead) {
@@ -992,7 +1042,15 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
                 unsigned idx = (unsigned)(((unsigned long long)p * n) / P);
                 float4 raw = __ldcg(reinterpret_cast<const float4*>(in + idx));
                 Item it = *reinterpret_cast<Item*>(&raw);
+                if (!item_ok(A, it)) {
+                    if ((threadIdx.x & 31) == 0) flag_bad(A, kBadProbe);
+                    continue;
+                }
                 view(A, it.q, V);
+                if (depth_of(it.a) > V.LA || depth_of(it.b) > V.LB) {
+                    if ((threadIdx.x & 31) == 0) flag_bad(A, kBadProbe);
+                    continue;
+                }
                 probe<KIND>(A, it, V);
             }
             if (lead) A.stats->probes = P;
@@ -1131,8 +1189,15 @@ done:
 
 // ------------------------------------------------------------- host side
 
+// Both kinds get the same shared-memory carveout, so that CTAs of a min and a
+// max launch can share an SM (an SM holds CTAs of one carveout at a time).
 template <int KIND>
 static int occupancy_blocks() {
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(k_query<KIND>, cudaFuncAttributePreferredSharedMemoryCarveout, 25);
+        configured = true;
+    }
     int nb = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_query<KIND>, kBlock, 0);
     return nb;

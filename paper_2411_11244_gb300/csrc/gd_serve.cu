@@ -113,14 +113,16 @@ bool alloc_slot(Slot& s, long long budget, long long max_batch, int grid) {
 void harvest(gd_server* S, Slot& s) {
     std::vector<std::pair<Request, gd_result>> redo;
     bool aborted = s.b.ctr_host[kCtrLastAbort] != 0;
+    const bool bad = s.b.ctr_host[kCtrBadIndex] != 0;  // an internal index check failed
     {
         std::lock_guard<std::mutex> g(S->mu);
         for (size_t j = 0; j < s.reqs.size(); ++j) {
             gd_result r = s.b.out_host[j];
-            if (aborted) {
-                r.status = GD_ERR_TIMEOUT;
-            }
-            if (r.status == GD_ERR_OVERFLOW) {
+            if (aborted) r.status = GD_ERR_TIMEOUT;
+            if (bad) r.status = GD_ERR_CUDA;
+            // work beyond the slot's buffers, or a slot launch whose bounded
+            // waits gave up: rerun alone below
+            if (r.status == GD_ERR_OVERFLOW || r.status == GD_ERR_TIMEOUT) {
                 redo.push_back({s.reqs[j], r});
                 continue;
             }
@@ -128,7 +130,11 @@ void harvest(gd_server* S, Slot& s) {
             S->done[s.reqs[j].ticket] = r;
         }
     }
-    // work beyond the slot's buffers: rerun alone on the context's own buffers
+    // rerun alone on the context's own buffers, with the device otherwise idle
+    // (this runs on the serving thread, so no slot is launched meanwhile)
+    if (!redo.empty())
+        for (Slot& o : S->slots)
+            if (o.busy && &o != &s) cudaStreamSynchronize(o.b.stream);
     for (auto& pr : redo) {
         gd_result r{};
         gd_status st = serve_single(S->ctx, pr.first.q, &r);
@@ -145,10 +151,26 @@ void run_loop(gd_server* S) {
     cudaSetDevice(serve_device(S->ctx));
     for (;;) {
         bool worked = false;
-        // harvest finished slots
+        // harvest finished slots; a slot whose stream reports an error (the
+        // context is unusable then) fails its requests instead of being
+        // waited for forever
         for (Slot& s : S->slots) {
-            if (s.busy && cudaStreamQuery(s.b.stream) == cudaSuccess) {
+            if (!s.busy) continue;
+            cudaError_t q = cudaStreamQuery(s.b.stream);
+            if (q == cudaSuccess) {
                 harvest(S, s);
+                worked = true;
+            } else if (q != cudaErrorNotReady) {
+                std::lock_guard<std::mutex> g(S->mu);
+                for (auto& r : s.reqs) {
+                    gd_result res{};
+                    res.status = GD_ERR_CUDA;
+                    S->pending.erase(r.ticket);
+                    S->done[r.ticket] = res;
+                }
+                s.reqs.clear();
+                s.busy = false;
+                S->loop_error = GD_ERR_CUDA;
                 worked = true;
             }
         }
@@ -237,8 +259,20 @@ GD_API gd_status gd_serve_start(gd_ctx* ctx, const gd_serve_opts* opts, gd_serve
     S->ctx = ctx;
     S->opts = o;
     S->slot_budget = o.memory_budget / o.slots;
+    // Every slot's cooperative grid must stay resident while the other slots
+    // run theirs.  The CTAs of a grid are spread over the GPU's partitions, so
+    // an exact split of the full capacity can leave one partition
+    // over-subscribed (a 3-way split, 3 x 101 CTAs, was seen to leave a grid
+    // partly unscheduled until its bounded barrier wait gave up): the slots
+    // share 90% of the capacity, in grids of a multiple of 16 CTAs.
     int occ = std::max(1, std::min(query_max_blocks_per_sm(0), query_max_blocks_per_sm(1)));
-    int per = std::max(1, (occ * serve_sms(ctx)) / o.slots);
+    int cap = occ * serve_sms(ctx);
+    int per = cap;
+    if (o.slots > 1) {
+        per = (cap * 9 / 10) / o.slots;
+        per -= per % 16;
+        if (per < 16) per = std::min(16, cap);
+    }
     S->slots.resize(o.slots);
     for (Slot& s : S->slots) {
         if (!alloc_slot(s, S->slot_budget, o.max_batch, per)) {
