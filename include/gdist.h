@@ -188,6 +188,23 @@ GD_API gd_status gd_max_distance(gd_ctx *ctx, const gd_mesh *A, const gd_mesh *B
  * d_out->status. */
 GD_API gd_status gd_query_device(gd_ctx *ctx, const gd_mesh *A, const gd_mesh *B, gd_kind kind,
                                  const double *d_xa, const double *d_xb, gd_result *d_out, void *stream);
+/* Device-resident query that allocates nothing (the paper has no counterpart:
+ * this is for callers that must not allocate device memory while they run,
+ * such as a per-frame control loop where a cudaMalloc could stall or fail, or
+ * a process whose device memory is held by another allocator).  Same inputs
+ * and output as gd_query_device (device pointers; stream is a cudaStream_t,
+ * NULL = the legacy default stream); A and B must belong to one context,
+ * whose tunables are read.  Every work buffer comes from one 32 MiB array
+ * compiled into the library (held by every GPU that loads the library, until
+ * exit).  The first call on a device looks up that array's device address:
+ * make it before any stream capture.  Limits: B with at most 24 tree levels
+ * (fewer than 2^25 triangles; larger B: GD_ERR_INVALID_ARG); at most 2^18
+ * front entries, 2^18 leaf pairs and 2^16 float64 candidates per call
+ * (beyond them d_out->status is GD_ERR_OVERFLOW: use gd_query_device).
+ * Calls share the array: calls whose work overlaps on the GPU race, so
+ * serialise them.  Asynchronous; returns argument and launch errors only. */
+GD_API gd_status gd_query_device_noalloc(const gd_mesh *A, const gd_mesh *B, gd_kind kind, const double *d_xa,
+                                         const double *d_xb, gd_result *d_out, void *stream);
 /* n independent queries (any mix of meshes and kinds) in persistent
  * launches (one per kind present), results in out[0..n).  Synchronous.
  * A query whose work exceeds the buffers is retried alone with grown buffers. */

@@ -695,4 +695,9 @@ bool serve_query_ok(gd_ctx* ctx, const gd_query& q, std::string* why) {
 }
 long long serve_mesh_tris(const gd_mesh* m) { return m ? m->nt : 0; }
 
+// ---- read-only views used by the allocation-free entry point (gd_noalloc.cu)
+gd_ctx* mesh_ctx(const gd_mesh* m) { return m ? m->ctx : nullptr; }
+const MeshDev* mesh_desc(const gd_mesh* m) { return m && m->built ? m->d_desc : nullptr; }
+int mesh_levels(const gd_mesh* m) { return m ? m->L : 0; }
+
 }  // namespace gd

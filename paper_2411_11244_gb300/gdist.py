@@ -28,7 +28,8 @@ STATUS_NAMES = {
 EXPORTS = [
     "gd_ctx_create", "gd_ctx_destroy", "gd_last_error", "gd_ctx_set_tunables", "gd_ctx_get_tunables",
     "gd_get_stats", "gd_ctx_stream", "gd_mesh_create", "gd_bvh_build", "gd_mesh_destroy", "gd_mesh_info",
-    "gd_mesh_download", "gd_min_distance", "gd_max_distance", "gd_query_device", "gd_batch_query",
+    "gd_mesh_download", "gd_min_distance", "gd_max_distance", "gd_query_device", "gd_query_device_noalloc",
+    "gd_batch_query",
     "gd_serve_start", "gd_serve_submit", "gd_serve_poll", "gd_serve_stop",
 ]
 
@@ -115,6 +116,7 @@ def load(path: str = LIB_PATH):
         "gd_min_distance": (C.c_int, [_vp, _vp, _vp, _dp, _dp, C.POINTER(gd_result)]),
         "gd_max_distance": (C.c_int, [_vp, _vp, _vp, _dp, _dp, C.POINTER(gd_result)]),
         "gd_query_device": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp, _vp, _vp, _vp]),
+        "gd_query_device_noalloc": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _vp, _vp]),
         "gd_batch_query": (C.c_int, [_vp, C.POINTER(gd_query), C.c_int64, C.POINTER(gd_result)]),
         "gd_serve_start": (C.c_int, [_vp, C.POINTER(gd_serve_opts), C.POINTER(_vp)]),
         "gd_serve_submit": (C.c_int, [_vp, C.POINTER(gd_query), C.POINTER(C.c_uint64)]),
@@ -241,6 +243,12 @@ def gd_max_distance(ctx, A, B, xa, xb) -> gd_result:
 def gd_query_device(ctx, A, B, kind: int, d_xa: int, d_xb: int, d_out: int, stream: int = 0):
     """Device-resident query: d_xa, d_xb, d_out are device addresses (ints)."""
     _check(load().gd_query_device(ctx, A, B, int(kind), d_xa, d_xb, d_out, stream or None), ctx)
+
+
+def gd_query_device_noalloc(A, B, kind: int, d_xa: int, d_xb: int, d_out: int, stream: int = 0):
+    """Device-resident query whose work buffers come from a fixed array inside
+    the library (no allocation); device addresses as ints."""
+    _check(load().gd_query_device_noalloc(A, B, int(kind), d_xa, d_xb, d_out, stream or None))
 
 
 def make_queries(items):
