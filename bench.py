@@ -14,6 +14,11 @@ already resident in HBM; `e2e` is the same through the synchronous C ABI call
 with host transforms and a host result (launch parameters in, result record
 out).  `--impl reference` times the FP64 CPU oracle on the same frames.
 
+Also reported (same run): "batched" -- 4,096 rigid transforms of one gear pair
+(204,800 triangles each) in one persistent launch against one launch per
+query; "served" -- a pool of 64 resident meshes under Poisson arrivals,
+continuous batching against one call per request, p50/p99 latency.
+
 Multi-GPU: queries are independent, so N ranks run replicas (each its own
 frames, no collective); value = queries of all ranks / max rank time.
 """
@@ -32,7 +37,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "ms/query at 2x7.5M tris (rings, min distance)"
+METRIC = "ms/query at 2x7.5M tris; batched queries/s + p50/p99 vs plain path"
 WORKLOAD = "rings: 2 tori R=1 r=0.05, 2500x1500 quads = 7.5M tris each, gap 1e-3, B spun per frame"
 
 
@@ -122,6 +127,126 @@ def cpu_baseline(A, xa, xbs, frames, threads=None):
                       f"oracle BVH build {build_s:.1f} s excluded"}
 
 
+def bench_batched(G, ctx, n=4096, reps=3):
+    """4,096 rigid transforms of one gear pair (204,800 triangles each):
+    queries/s of the batched form (one persistent launch, gd_batch_query)
+    against the plain form (one gd_min_distance call per query)."""
+    from paper_2411_11244_gb300 import synth
+    A, B, xa, xbs = synth.config_gears(n)
+    ma, mb = G.gd_mesh_create(ctx, *A), G.gd_mesh_create(ctx, *B)
+    G.gd_bvh_build(ma, ctx=ctx)
+    G.gd_bvh_build(mb, ctx=ctx)
+    arr = G.make_queries([(ma, mb, xa, xb, G.GD_MIN) for xb in xbs])
+    out = G.gd_batch_query(ctx, arr)  # warm-up, sizes the buffers
+    walls = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        out = G.gd_batch_query(ctx, arr)
+        walls.append(time.perf_counter() - t0)
+    st = G.gd_get_stats(ctx)
+    bad = sum(1 for i in range(n) if out[i].status != 0)
+    zero = sum(1 for i in range(n) if out[i].status == 0 and out[i].d == 0.0)
+    lat = []
+    for xb in xbs:
+        t0 = time.perf_counter()
+        r = G.gd_min_distance(ctx, ma, mb, xa, xb)
+        lat.append(1000.0 * (time.perf_counter() - t0))
+        assert r.status == 0
+    lat.sort()
+    wall = statistics.median(walls)
+    G.gd_mesh_destroy(ma)
+    G.gd_mesh_destroy(mb)
+    return {
+        "workload": f"gears: 2 x {len(A[1])} tris, {n} seeded rigid transforms (min distance)",
+        "batched_qps": n / wall, "batched_ms_per_batch": 1000.0 * wall,
+        "batched_latency_ms": {"p50": 1000.0 * wall, "p99": 1000.0 * wall},
+        "plain_qps": 1000.0 * n / sum(lat),
+        "plain_latency_ms": {"p50": lat[n // 2], "p99": lat[min(n - 1, int(0.99 * n))]},
+        "speedup_qps": (n / wall) / (1000.0 * n / sum(lat)),
+        "mix": {"intersecting": zero, "errors": bad, "separate": n - zero - bad},
+        "batch_kernel": {"levels": st["levels"], "leaf_pairs": st["leaf_pairs"], "candidates": st["candidates"]},
+    }
+
+
+def bench_served(G, ctx, rates=(1000, 3000, 10000, 30000), n_req=1500, seed=0):
+    """A pool of 64 meshes (tori, geodesic spheres, gears; 1e3..4e6 triangles,
+    BVHs resident) and a stream of random mesh pairs and transforms arriving
+    as a Poisson process of rate lambda.  Served: gd_serve_submit/poll
+    (continuous batching over stream slots).  Plain: one gd_min_distance per
+    request in arrival order.  Latency = completion - arrival."""
+    import numpy as np
+    from paper_2411_11244_gb300 import synth
+    pool = synth.mesh_pool(64, seed=seed)
+    hs = []
+    rad = []
+    for m in pool:
+        h = G.gd_mesh_create(ctx, *m)
+        G.gd_bvh_build(h, ctx=ctx)
+        hs.append(h)
+        rad.append(float(np.max(np.linalg.norm(m[0].astype(np.float64), axis=1))))
+    rng = np.random.default_rng(seed + 7)
+    reqs = []
+    for _ in range(n_req):
+        a, b = int(rng.integers(0, 64)), int(rng.integers(0, 64))
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        dist = rng.uniform(0.5, 1.5) * (rad[a] + rad[b])
+        reqs.append((hs[a], hs[b], synth.identity_xform(),
+                     synth.xform(synth.random_rotation(rng), d * dist), G.GD_MIN))
+    arr = G.make_queries(reqs)
+    total_tris = sum(len(m[1]) for m in pool)
+    res = {"workload": f"pool of 64 meshes, {total_tris} tris resident; {n_req} requests per rate",
+           "rates": []}
+    for lam in rates:
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, size=n_req))
+        # served
+        srv = G.gd_serve_start(ctx, slots=4, max_batch=256)
+        lat = [None] * n_req
+        tick = [0] * n_req
+        t0 = time.perf_counter()
+        nxt = 0
+        pending = []
+        while nxt < n_req or pending:
+            now = time.perf_counter() - t0
+            while nxt < n_req and arrivals[nxt] <= now:
+                rc, t = G.gd_serve_submit(srv, arr[nxt])
+                if rc != 0:
+                    break
+                tick[nxt] = t
+                pending.append(nxt)
+                nxt += 1
+            still = []
+            for i in pending:
+                rc, r = G.gd_serve_poll(srv, tick[i])
+                if rc == 0:
+                    lat[i] = 1000.0 * ((time.perf_counter() - t0) - arrivals[i])
+                else:
+                    still.append(i)
+            pending = still
+        wall = time.perf_counter() - t0
+        G.gd_serve_stop(srv)
+        sl = sorted(lat)
+        # plain: in arrival order, one call per request
+        plat = []
+        t0 = time.perf_counter()
+        for i in range(n_req):
+            while time.perf_counter() - t0 < arrivals[i]:
+                pass
+            q = reqs[i]
+            G.gd_min_distance(ctx, q[0], q[1], q[2], q[3])
+            plat.append(1000.0 * ((time.perf_counter() - t0) - arrivals[i]))
+        pwall = time.perf_counter() - t0
+        pl = sorted(plat)
+        res["rates"].append({
+            "lambda_qps": lam,
+            "served": {"qps": n_req / wall, "p50_ms": sl[n_req // 2], "p99_ms": sl[int(0.99 * n_req)]},
+            "plain": {"qps": n_req / pwall, "p50_ms": pl[n_req // 2], "p99_ms": pl[int(0.99 * n_req)]},
+        })
+    for h in hs:
+        G.gd_mesh_destroy(h)
+    return res
+
+
 def run_reference(args):
     rank, world, _ = _dist()
     if rank != 0:
@@ -159,6 +284,8 @@ def main():
     ap.add_argument("--impl", default="gdist", choices=["gdist", "reference"])
     ap.add_argument("--cpu-frames", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -278,11 +405,15 @@ def main():
         "clocks": clk.summary(),
         "wall_s": wall,
     }
+    G.gd_mesh_destroy(ma)
+    G.gd_mesh_destroy(mb)
+    if not args.no_batched:
+        line["batched"] = bench_batched(G, ctx)
+    if not args.no_served:
+        line["served"] = bench_served(G, ctx)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(A, xa, xbs, args.cpu_frames)
     print(json.dumps(line), flush=True)
-    G.gd_mesh_destroy(ma)
-    G.gd_mesh_destroy(mb)
     G.gd_ctx_destroy(ctx)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -142,7 +142,7 @@ def geosphere(freq: int, radius: float = 1.0, noise: float = 0.0, seed: int = 0,
     n = int(freq)
     assert n >= 1
     cv, cf = _icosahedron()
-    # canonical edges (lo, hi) -> id
+    # canonical edges (lo, hi) -> id, so that faces sharing an edge share its points
     edges = {}
     for f in cf:
         for k in range(3):
@@ -156,42 +156,35 @@ def geosphere(freq: int, radius: float = 1.0, noise: float = 0.0, seed: int = 0,
     V = 12 + ne * nv_edge + 20 * nv_face
     pts = np.zeros((V, 3), dtype=np.float64)
     pts[:12] = cv
+    s_ = np.arange(1, n, dtype=np.float64)[:, None] / n
     for (a, b), e in edges.items():
-        s = np.arange(1, n, dtype=np.float64)[:, None] / n
-        pts[12 + e * nv_edge: 12 + (e + 1) * nv_edge] = cv[a] * (1 - s) + cv[b] * s
-    tris = []
+        pts[12 + e * nv_edge: 12 + (e + 1) * nv_edge] = cv[a] * (1 - s_) + cv[b] * s_
     face_base = 12 + ne * nv_edge
+    # grid (i, j), i + j <= n: point = A + i/n (B - A) + j/n (C - A)
+    I, J = np.meshgrid(np.arange(n + 1), np.arange(n + 1), indexing="ij")
+    inner = (I > 0) & (J > 0) & (I + J < n)
+    ii_in, jj_in = I[inner], J[inner]  # row-major order of interior points
+    tris = []
     for fi, (A, B, C) in enumerate(cf):
         A, B, C = int(A), int(B), int(C)
-        # grid index (i, j): point = A + i/n (B - A) + j/n (C - A), i + j <= n
         idx = -np.ones((n + 1, n + 1), dtype=np.int64)
 
-        def edge_pt(a, b, k):
-            # k-th point (1..n-1) from a toward b on the canonical edge
+        def edge_run(a, b, k):
+            # points k (1..n-1) from a toward b on the canonical edge
             e = edges[(min(a, b), max(a, b))]
             kk = k if a < b else n - k
             return 12 + e * nv_edge + (kk - 1)
 
-        interior = face_base + fi * nv_face
-        cnt = 0
-        for i in range(n + 1):
-            for j in range(n + 1 - i):
-                if i == 0 and j == 0:
-                    idx[i, j] = A
-                elif i == n:
-                    idx[i, j] = B
-                elif j == n:
-                    idx[i, j] = C
-                elif j == 0:
-                    idx[i, j] = edge_pt(A, B, i)
-                elif i == 0:
-                    idx[i, j] = edge_pt(A, C, j)
-                elif i + j == n:
-                    idx[i, j] = edge_pt(B, C, j)
-                else:
-                    idx[i, j] = interior + cnt
-                    pts[interior + cnt] = cv[A] + (i / n) * (cv[B] - cv[A]) + (j / n) * (cv[C] - cv[A])
-                    cnt += 1
+        k = np.arange(1, n)
+        idx[0, 0], idx[n, 0], idx[0, n] = A, B, C
+        if n > 1:
+            idx[k, 0] = edge_run(A, B, k)
+            idx[0, k] = edge_run(A, C, k)
+            idx[n - k, k] = edge_run(B, C, k)
+        base = face_base + fi * nv_face
+        idx[ii_in, jj_in] = base + np.arange(len(ii_in))
+        pts[base: base + len(ii_in)] = (cv[A][None, :] + (ii_in[:, None] / n) * (cv[B] - cv[A])[None, :]
+                                        + (jj_in[:, None] / n) * (cv[C] - cv[A])[None, :])
         ii, jj = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
         m = ii + jj <= n - 1
         i0, j0 = ii[m], jj[m]
