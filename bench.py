@@ -203,6 +203,7 @@ def bench_served(G, ctx, rates=(1000, 3000, 10000, 30000), n_req=1500, seed=0):
         srv = G.gd_serve_start(ctx, slots=4, max_batch=256)
         lat = [None] * n_req
         tick = [0] * n_req
+        serr = 0
         t0 = time.perf_counter()
         nxt = 0
         pending = []
@@ -218,29 +219,37 @@ def bench_served(G, ctx, rates=(1000, 3000, 10000, 30000), n_req=1500, seed=0):
             still = []
             for i in pending:
                 rc, r = G.gd_serve_poll(srv, tick[i])
-                if rc == 0:
-                    lat[i] = 1000.0 * ((time.perf_counter() - t0) - arrivals[i])
-                else:
+                if rc == G.GD_ERR_NOT_READY:
                     still.append(i)
+                    continue
+                lat[i] = 1000.0 * ((time.perf_counter() - t0) - arrivals[i])
+                if rc != 0 or r.status != 0:
+                    serr += 1
             pending = still
         wall = time.perf_counter() - t0
         G.gd_serve_stop(srv)
         sl = sorted(lat)
         # plain: in arrival order, one call per request
         plat = []
+        perr = 0
         t0 = time.perf_counter()
         for i in range(n_req):
             while time.perf_counter() - t0 < arrivals[i]:
                 pass
             q = reqs[i]
-            G.gd_min_distance(ctx, q[0], q[1], q[2], q[3])
+            try:
+                G.gd_min_distance(ctx, q[0], q[1], q[2], q[3])
+            except G.GdError:
+                perr += 1
             plat.append(1000.0 * ((time.perf_counter() - t0) - arrivals[i]))
         pwall = time.perf_counter() - t0
         pl = sorted(plat)
         res["rates"].append({
             "lambda_qps": lam,
-            "served": {"qps": n_req / wall, "p50_ms": sl[n_req // 2], "p99_ms": sl[int(0.99 * n_req)]},
-            "plain": {"qps": n_req / pwall, "p50_ms": pl[n_req // 2], "p99_ms": pl[int(0.99 * n_req)]},
+            "served": {"qps": n_req / wall, "p50_ms": sl[n_req // 2], "p99_ms": sl[int(0.99 * n_req)],
+                       "errors": serr},
+            "plain": {"qps": n_req / pwall, "p50_ms": pl[n_req // 2], "p99_ms": pl[int(0.99 * n_req)],
+                      "errors": perr},
         })
     for h in hs:
         G.gd_mesh_destroy(h)

@@ -67,7 +67,11 @@ typedef struct gd_server gd_server;
 /* One query answer.  For GD_MIN, pa and pb are a closest pair (pa on tri_a
  * of mesh A, pb on tri_b of mesh B); for GD_MAX, a farthest vertex pair.
  * status is a gd_status for this query; flags bit 0 = meshes intersect
- * (d == 0). */
+ * (d == 0); flags bit 1 = the traversal stopped early because a triangle pair
+ * at float64 distance exactly 0 was found (Section 8: with penetration the
+ * minimum distance is zero).  The witness of d > 0 is the pair at the extreme
+ * with the smallest (tri_a, tri_b); the witness of d == 0 is that first
+ * proving pair, any intersecting pair, and may differ between runs. */
 typedef struct {
     double d;
     int64_t tri_a, tri_b;
@@ -91,7 +95,7 @@ typedef struct {
 /* Traversal tunables of a context.  Zero fields keep the current value. */
 typedef struct {
     int64_t work_target;   /* C of Section 6: a level expands n front entries by
-                              k levels per side with n * 4^k < C (default 2^20) */
+                              k levels per side with n * 4^k < C (default 2^19) */
     int32_t k_max;         /* cap on k (default 5) */
     int32_t blocks_per_sm; /* persistent CTAs per SM (default: occupancy limit) */
     int64_t front_capacity;/* BVTT entries per front buffer (default 2^24) */
@@ -105,6 +109,11 @@ typedef struct {
     int32_t refit_slots;   /* subtrees refit per launch (default 2^13) */
     int32_t probes;        /* greedy probes per launch that seed the running
                               bound (default 256; at least one per query) */
+    int64_t batch_budget;  /* batches of >= 2 queries: the queues are sized for
+                              this many entries per query and level (up to
+                              max_capacity); a query that pushes more than its
+                              share in one level leaves the batch and runs
+                              alone afterwards (default 2^16) */
 } gd_tunables;
 
 /* Counters of the last query (or batch) run on a context. */

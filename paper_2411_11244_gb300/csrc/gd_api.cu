@@ -180,6 +180,36 @@ bool grow(gd_ctx* c) {
     return alloc_queues(c) == GD_OK;
 }
 
+// Entries one query of an m-query batch may push per level: every query at
+// its limit fills a front buffer, or half the leaf queue (the traversal
+// empties the leaf queue once it is half full).
+unsigned batch_share(long long cap_front, long long cap_leaf, long long m) {
+    if (m < 2) return 0u;
+    long long b = std::min(cap_front / m, cap_leaf / (2 * m));
+    return (unsigned)std::max(1ll, std::min(b, 0xffffffffll));
+}
+
+// Queues of a batch of m queries: room for batch_budget entries per query and
+// level, within max_capacity (they only grow).
+gd_status size_for_batch(gd_ctx* c, long long m) {
+    if (m < 2) return GD_OK;
+    const long long lim = std::min<long long>(c->tun.max_capacity, 0xffffffffll);
+    long long want = std::min(lim, 2 * m * std::max<long long>(1, c->tun.batch_budget));
+    long long p = 1;
+    while (p < want) p <<= 1;
+    want = std::min(lim, p);
+    if (c->cap_front >= want && c->cap_leaf >= want) return GD_OK;
+    c->cap_front = std::max(c->cap_front, want);
+    c->cap_leaf = std::max(c->cap_leaf, want);
+    gd_status s = alloc_queues(c);
+    if (s != GD_OK) {
+        // fall back to the configured sizes; the batch then evicts more
+        c->ready = false;
+        return ensure_ws(c, m);
+    }
+    return GD_OK;
+}
+
 int grid_blocks(gd_ctx* c, int kind) {
     int occ = query_max_blocks_per_sm(kind);
     int b = c->tun.blocks_per_sm > 0 ? std::min(c->tun.blocks_per_sm, occ) : occ;
@@ -288,6 +318,69 @@ gd_status run_single(gd_ctx* ctx, const gd_mesh* A, const gd_mesh* B, int kind, 
     }
 }
 
+// One launch over the queries ids (all of one kind); results go to out, the
+// queries that ran out of queue space to *redo, the launch's counters add to
+// *agg.
+gd_status batch_pass(gd_ctx* ctx, const gd_query* q, const std::vector<int64_t>& ids, int kind, gd_result* out,
+                     gd_stats* agg, std::vector<int64_t>* redo) {
+    const long long m = (long long)ids.size();
+    gd_status s = ensure_ws(ctx, m);
+    if (s != GD_OK) return s;
+    s = size_for_batch(ctx, m);
+    if (s != GD_OK) return s;
+    long long tab = 0;
+    for (long long j = 0; j < m; ++j) {
+        const gd_query& Q = q[ids[j]];
+        QIn& in = ctx->qin_host[j];
+        in.A = Q.a->d_desc;
+        in.B = Q.b->d_desc;
+        std::memcpy(in.xa, Q.xa, sizeof(in.xa));
+        std::memcpy(in.xb, Q.xb, sizeof(in.xb));
+        in.slot_base = (unsigned)tab;
+        tab += table_entries(ctx, Q.b);
+    }
+    if (tab > 0xfffffff0ll) return fail(ctx, GD_ERR_INVALID_ARG, "batch too large for the refit tables");
+    s = ensure_table(ctx, tab);
+    if (s != GD_OK) return s;
+    GD_CUDA(ctx, cudaMemcpyAsync(ctx->qin_dev, ctx->qin_host, sizeof(QIn) * m, cudaMemcpyHostToDevice, ctx->stream));
+    KArgs a{};
+    a.nq = (int)m;
+    a.qin = ctx->qin_dev;
+    fill_common(ctx, a, ctx->mb_dev->ctr, &ctx->mb_dev->stats);
+    a.slot_of = ctx->slot_of;
+    a.n_slot_of = (unsigned long long)tab;
+    a.out = ctx->out_dev;
+    a.q_budget = batch_share(ctx->cap_front, ctx->cap_leaf, m);
+    int grid = grid_blocks(ctx, kind);
+    GD_CUDA(ctx, launch_query(kind, a, grid, ctx->stream));
+    GD_CUDA(ctx, cudaMemcpyAsync(ctx->out_host, ctx->out_dev, sizeof(gd_result) * m, cudaMemcpyDeviceToHost, ctx->stream));
+    GD_CUDA(ctx, cudaMemcpyAsync(ctx->mb_host, ctx->mb_dev, sizeof(Mailbox), cudaMemcpyDeviceToHost, ctx->stream));
+    GD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    gd_stats st;
+    to_stats(ctx->mb_host->stats, (unsigned)grid, 0, &st);
+    agg->levels = std::max(agg->levels, st.levels);
+    agg->pairs_tested += st.pairs_tested;
+    agg->leaf_pairs += st.leaf_pairs;
+    agg->tri_pairs += st.tri_pairs;
+    agg->candidates += st.candidates;
+    agg->refined += st.refined;
+    agg->alg_bytes += st.alg_bytes;
+    agg->blocks = st.blocks;
+    for (int i = 0; i < 32; ++i) {
+        agg->front[i] += st.front[i];
+        agg->slots[i] = std::max(agg->slots[i], st.slots[i]);
+    }
+    if (ctx->mb_host->ctr[kCtrLastAbort]) return fail(ctx, GD_ERR_TIMEOUT, "a device-side wait timed out");
+    if (ctx->mb_host->ctr[kCtrBadIndex])
+        return fail(ctx, GD_ERR_CUDA,
+                    "internal index check failed (sites " + std::to_string(ctx->mb_host->ctr[kCtrBadIndex]) + ")");
+    for (long long j = 0; j < m; ++j) {
+        out[ids[j]] = ctx->out_host[j];
+        if (ctx->out_host[j].status == GD_ERR_OVERFLOW) redo->push_back(ids[j]);
+    }
+    return GD_OK;
+}
+
 }  // namespace
 
 // =========================================================== C ABI
@@ -321,6 +414,7 @@ GD_API gd_status gd_ctx_create(int device, gd_ctx** out) {
     c->tun.refit_mode = 1;
     c->tun.refit_slots = 1 << 13;
     c->tun.probes = 256;
+    c->tun.batch_budget = 1ll << 16;
     *out = c;
     return GD_OK;
 }
@@ -357,6 +451,7 @@ GD_API gd_status gd_ctx_set_tunables(gd_ctx* c, const gd_tunables* t) {
     if (t->refit_mode == 1 || t->refit_mode == 2) c->tun.refit_mode = t->refit_mode;
     if (t->refit_slots > 0) { c->tun.refit_slots = t->refit_slots; realloc = true; }
     if (t->probes > 0) c->tun.probes = t->probes;
+    if (t->batch_budget > 0) c->tun.batch_budget = t->batch_budget;
     if (realloc && c->ready) {
         cudaStreamSynchronize(c->stream);
         free_ws(c);
@@ -567,56 +662,11 @@ GD_API gd_status gd_batch_query(gd_ctx* ctx, const gd_query* q, int64_t n, gd_re
         for (int64_t i = 0; i < n; ++i)
             if ((int)q[i].kind == kind) idx.push_back(i);
         if (idx.empty()) continue;
-        long long m = (long long)idx.size();
-        gd_status s = ensure_ws(ctx, m);
-        if (s != GD_OK) return s;
-        long long tab = 0;
-        for (long long j = 0; j < m; ++j) {
-            const gd_query& Q = q[idx[j]];
-            QIn& in = ctx->qin_host[j];
-            in.A = Q.a->d_desc;
-            in.B = Q.b->d_desc;
-            std::memcpy(in.xa, Q.xa, sizeof(in.xa));
-            std::memcpy(in.xb, Q.xb, sizeof(in.xb));
-            in.slot_base = (unsigned)tab;
-            tab += table_entries(ctx, Q.b);
-        }
-        if (tab > 0xfffffff0ll) return fail(ctx, GD_ERR_INVALID_ARG, "batch too large for the refit tables");
-        s = ensure_table(ctx, tab);
-        if (s != GD_OK) return s;
-        GD_CUDA(ctx, cudaMemcpyAsync(ctx->qin_dev, ctx->qin_host, sizeof(QIn) * m, cudaMemcpyHostToDevice, ctx->stream));
-        KArgs a{};
-        a.nq = (int)m;
-        a.qin = ctx->qin_dev;
-        fill_common(ctx, a, ctx->mb_dev->ctr, &ctx->mb_dev->stats);
-        a.slot_of = ctx->slot_of;
-        a.n_slot_of = (unsigned long long)tab;
-        a.out = ctx->out_dev;
-        int grid = grid_blocks(ctx, kind);
-        GD_CUDA(ctx, launch_query(kind, a, grid, ctx->stream));
-        GD_CUDA(ctx, cudaMemcpyAsync(ctx->out_host, ctx->out_dev, sizeof(gd_result) * m, cudaMemcpyDeviceToHost, ctx->stream));
-        GD_CUDA(ctx, cudaMemcpyAsync(ctx->mb_host, ctx->mb_dev, sizeof(Mailbox), cudaMemcpyDeviceToHost, ctx->stream));
-        GD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-        gd_stats st;
-        to_stats(ctx->mb_host->stats, (unsigned)grid, 0, &st);
-        agg.levels = std::max(agg.levels, st.levels);
-        agg.pairs_tested += st.pairs_tested;
-        agg.leaf_pairs += st.leaf_pairs;
-        agg.tri_pairs += st.tri_pairs;
-        agg.candidates += st.candidates;
-        agg.refined += st.refined;
-        agg.alg_bytes += st.alg_bytes;
-        agg.blocks = st.blocks;
-        for (int i = 0; i < 32; ++i) { agg.front[i] += st.front[i]; agg.slots[i] = std::max(agg.slots[i], st.slots[i]); }
-        if (ctx->mb_host->ctr[kCtrLastAbort]) return fail(ctx, GD_ERR_TIMEOUT, "a device-side wait timed out");
-        if (ctx->mb_host->ctr[kCtrBadIndex])
-            return fail(ctx, GD_ERR_CUDA,
-                        "internal index check failed (sites " + std::to_string(ctx->mb_host->ctr[kCtrBadIndex]) + ")");
+        // queries evicted from the batch (or short of queue space) run alone,
+        // where the queues grow as far as one query needs
         std::vector<int64_t> redo;
-        for (long long j = 0; j < m; ++j) {
-            out[idx[j]] = ctx->out_host[j];
-            if (ctx->out_host[j].status == GD_ERR_OVERFLOW) redo.push_back(idx[j]);
-        }
+        gd_status s = batch_pass(ctx, q, idx, kind, out, &agg, &redo);
+        if (s != GD_OK) return s;
         for (int64_t i : redo) {
             gd_status r = run_single(ctx, q[i].a, q[i].b, kind, q[i].xa, q[i].xb, &out[i]);
             total_retries += 1 + ctx->last.retries;
@@ -674,6 +724,7 @@ gd_status serve_launch_batch(gd_ctx* ctx, SlotBuffers& sb, const gd_query* qs, l
     a.refit = refit ? 1 : 0;
     a.probes = ctx->tun.probes;
     a.n_slot_of = refit ? (unsigned long long)tab : 0ull;
+    a.q_budget = batch_share(sb.cap_front, sb.cap_leaf, m);
     GD_CUDA(ctx, launch_query(kind, a, sb.grid, sb.stream));
     GD_CUDA(ctx, cudaMemcpyAsync(sb.out_host, sb.out_dev, sizeof(gd_result) * m, cudaMemcpyDeviceToHost, sb.stream));
     GD_CUDA(ctx, cudaMemcpyAsync(sb.ctr_host, sb.mb_dev_ctr, sizeof(unsigned) * kCtrWords, cudaMemcpyDeviceToHost,

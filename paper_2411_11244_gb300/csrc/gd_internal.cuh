@@ -10,6 +10,7 @@
 //   leaf l owns sorted triangles [floor(l T / 2^L), floor((l+1) T / 2^L)):
 //          one or two each, no per-leaf storage (the f12 rule of Section 7.3).
 #pragma once
+#include <cstddef>
 
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -71,9 +72,20 @@ struct __align__(16) QState {
     double xa[12], xb[12];
     unsigned slot_base;           // refit-root table offset of this query
     int dR;                       // depth of B's refit roots (L_B - min(L_B, kRefitH)), -1: no refit
+    unsigned cert;                // float64 intersection checks started (min kind)
+    unsigned pushed[2];           // batch: entries pushed at the current level (by parity)
 };
 
-constexpr unsigned kStatOverflow = 1u, kStatTimeout = 2u, kStatNoResult = 4u;
+// kStatZero: a pair at float64 distance exactly 0 is a candidate, so D_min = 0
+// and the query's traversal stops; kStatEvict: a query of a batch pushed more
+// than its share of the queues in one level, so it stops and is run again
+// alone.  (The status word shares an aligned 8-byte word with U, so one load
+// gives both.)
+constexpr unsigned kStatOverflow = 1u, kStatTimeout = 2u, kStatNoResult = 4u, kStatZero = 8u, kStatEvict = 16u;
+constexpr unsigned kStatStop = kStatZero | kStatEvict;
+constexpr unsigned kCertMax = 64;  // float64 intersection checks per query and launch
+static_assert(offsetof(QState, status) == offsetof(QState, U) + 4 && offsetof(QState, U) % 8 == 0,
+              "U and status must form one aligned 8-byte word");
 
 // global counters, one uint32 array per context
 enum : int {
@@ -90,8 +102,7 @@ enum : int {
     kCtrAbort = 20,   // a wait gave up: every CTA leaves at its next barrier
     kCtrLastAbort = 21, // the abort flag of the last finished launch
     kCtrExit = 22,    // CTAs that left the kernel (the last one resets the barrier)
-    kCtrBarCount = 32,
-    kCtrBarGen = 33,
+    kCtrBarCount = 32,// grid-barrier arrivals of this launch (top bit: abort)
     kCtrWords = 64,
 };
 
@@ -142,6 +153,7 @@ struct KArgs {
     long long work_target;
     int k_max;
     long long timeout_ns;
+    unsigned q_budget;          // batch: entries one query may push per level (0: no limit)
 };
 
 // ------------------------------------------------------------------ memory
@@ -176,38 +188,56 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
-// Grid-wide barrier for a cooperative launch (all CTAs co-resident).  Every
-// wait is bounded: after timeout_ns the CTA raises the abort flag and returns
-// false, and every other CTA returns false at its next barrier.
+__device__ __forceinline__ unsigned atom_add_release(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+constexpr unsigned kBarAbort = 0x80000000u;  // abort bit of the barrier word
+
+// Raise the abort flag: every CTA waiting at (or reaching) a grid barrier
+// returns false, and so does every later barrier of the launch.
+__device__ __forceinline__ void raise_abort(const KArgs& A) {
+    atomicExch(A.ctr + kCtrAbort, 1u);
+    atomicOr(A.ctr + kCtrBarCount, kBarAbort);
+}
+
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident).  One
+// word counts arrivals over the whole launch: a CTA arriving as number c
+// waits until the count reaches the next multiple of the grid size.  The
+// arrival is a release and the wait an acquire at GPU scope, so every write
+// made by any thread of a CTA before the barrier (ordered by __syncthreads)
+// is visible to every thread after it; no other fence is needed.  The top
+// bit of the same word is the abort flag, so the wait sees an abort with no
+// extra load.  Every wait is bounded: after timeout_ns the CTA raises the
+// abort and returns false.
 __device__ __forceinline__ bool grid_sync(const KArgs& A) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned* count = A.ctr + kCtrBarCount;
-        unsigned* gen = A.ctr + kCtrBarGen;
-        unsigned* abort_flag = A.ctr + kCtrAbort;
-        unsigned g = ld_acquire(gen);
-        __threadfence();
-        unsigned arrived = atomicAdd(count, 1u);
-        int ok = 1;
-        if (arrived == gridDim.x - 1) {
-            atomicExch(count, 0u);
-            __threadfence();
-            atomicAdd(gen, 1u);
-        } else {
-            unsigned long long t0 = globaltimer();
-            while (ld_acquire(gen) == g) {
-                if (ld_relaxed(abort_flag)) { ok = 0; break; }
-                if ((long long)(globaltimer() - t0) > A.timeout_ns) {
-                    atomicExch(abort_flag, 1u);
-                    ok = 0;
-                    break;
+        const unsigned G = gridDim.x;
+        const unsigned old = atom_add_release(count, 1u);
+        int ok = (old & kBarAbort) == 0u;
+        if (ok) {
+            const unsigned target = ((old & ~kBarAbort) / G + 1u) * G;
+            unsigned long long t0 = 0;
+            for (unsigned spin = 0;; ++spin) {
+                const unsigned v = ld_acquire(count);
+                if (v & kBarAbort) { ok = 0; break; }
+                if (v >= target) break;
+                if ((spin & 63u) == 0u) {
+                    const unsigned long long now = globaltimer();
+                    if (t0 == 0) t0 = now;
+                    else if ((long long)(now - t0) > A.timeout_ns) {
+                        raise_abort(A);
+                        ok = 0;
+                        break;
+                    }
                 }
-                __nanosleep(32);
             }
         }
-        __threadfence();
-        if (ld_acquire(abort_flag)) ok = 0;
         s_ok = ok;
     }
     __syncthreads();

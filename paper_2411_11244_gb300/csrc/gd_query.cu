@@ -174,6 +174,15 @@ __device__ __forceinline__ void mark_overflow(const KArgs& A, unsigned q) {
     atomicOr(A.ctr + kCtrOverflow, 1u);
 }
 
+// The running bound U of a query and whether its traversal has stopped
+// (D_min = 0 proven, or evicted from a batch), in one relaxed load (U and
+// status are adjacent in an 8-byte aligned word).
+__device__ __forceinline__ float load_U(const QState& s, bool* stop) {
+    const unsigned long long w = ld_relaxed64(reinterpret_cast<const unsigned long long*>(&s.U));
+    *stop = ((unsigned)(w >> 32) & kStatStop) != 0u;
+    return __uint_as_float((unsigned)w);
+}
+
 // cached per-thread view of one query's constants
 struct QView {
     unsigned q = 0xffffffffu;
@@ -308,9 +317,8 @@ __device__ __forceinline__ void tri_pair_bounds(const QView& V, unsigned ta, uns
 // Used for pairs that pass the float32 test, so that only near-ties reach the
 // float64 refinement; it stays on the float32 pipe (float64 is slow here).
 template <int KIND>
-__device__ __forceinline__ void tri_pair_bounds_tight(const QState& s, const QView& V, unsigned ta, unsigned tb,
-                                                      float* lo, float* up) {
-    Tri32 TA = load_tri(V.triA, ta), TB = load_tri(V.triB, tb);
+__device__ __forceinline__ void tri_pair_bounds_tight(const QState& s, const QView& V, const Tri32& TA,
+                                                      const Tri32& TB, float* lo, float* up) {
     float Rl[9], tl[3];
 #pragma unroll
     for (int i = 0; i < 9; ++i) Rl[i] = __ldcg(&s.Rl[i]);
@@ -338,6 +346,52 @@ __device__ __forceinline__ void tri_pair_bounds_tight(const QState& s, const QVi
         X = fmaxf(X, fmaxf(max_abs3(Al[k]), max_abs3(Bl[k])));
     }
     tri_bounds_core<KIND>(Al, Bl, __fadd_ru(Edf, __fmul_ru(256.0f * kU * 1.001f, X)), lo, up);
+}
+
+// Cheap float32 test run before the tight bounds of a leaf's triangle pair:
+// false only if the pair cannot hold the extreme.  Min kind: the separation of
+// the two triangles along the line between their centroids (a valid lower
+// bound of their distance for any direction, widened as in tri_bounds_core)
+// exceeds the running bound U.  Max kind: the largest float32 vertex-pair
+// distance, widened upward, is below the running bound.  Triangles with long
+// thin shapes have boxes far larger than themselves, so most leaf pairs that
+// pass the box test fail this one at a tenth of the cost of the tight bounds.
+template <int KIND>
+__device__ __forceinline__ bool tri_pair_may_hold(const QView& V, const Tri32& TA, const Tri32& TB, float U) {
+    const V3<float> o = TA.v[0];
+    V3<float> Al[3], Bl[3];
+    float X = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        Al[k] = TA.v[k] - o;
+        Bl[k] = map32(V.X, TB.v[k].x, TB.v[k].y, TB.v[k].z) - o;
+        X = fmaxf(X, fmaxf(max_abs3(Al[k]), max_abs3(Bl[k])));
+    }
+    const float E = __fadd_ru(V.E_box, __fmul_ru(256.0f * kU * 1.001f, X));
+    if (KIND == 0) {
+        const V3<float> n = (Al[0] + Al[1] + Al[2]) - (Bl[0] + Bl[1] + Bl[2]);
+        const float nn = dot(n, n);
+        if (!(nn > 0.f)) return true;
+        float amin = FLT_MAX, bmax = -FLT_MAX;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            amin = fminf(amin, dot(n, Al[k]));
+            bmax = fmaxf(bmax, dot(n, Bl[k]));
+        }
+        const float sep = amin - bmax;
+        if (!(sep > 0.f)) return true;
+        return lower_from_dist(sep / sqrtf(nn), E) <= U;
+    } else {
+        float m2 = 0.f;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const V3<float> d = Al[i] - Bl[j];
+                m2 = fmaxf(m2, dot(d, d));
+            }
+        return upper_from_sq(m2, E) >= U;
+    }
 }
 
 // ------------------------------------------------------------- pair bounds
@@ -451,6 +505,33 @@ __device__ void refit_subtree(const KArgs& A, unsigned q, unsigned root, unsigne
 
 // ------------------------------------------------------------- probes
 
+template <int KIND>
+__device__ __forceinline__ double refine_pair_warp(const QState& s, unsigned ta, unsigned tb, V3<double>* P,
+                                                   V3<double>* Q, int* ida, int* idb);
+
+// Proof of D_min = 0 (min kind), run by a whole warp on one pair (ta, tb) of
+// query q whose float32 lower bound is 0: the float64 distance of the pair,
+// computed exactly as the refinement does.  If it is exactly 0 the query is
+// done: no pair can be closer, so kStatZero stops its traversal, and the pair
+// enters the candidates with bound -1, the only mark the refinement keeps once
+// kStatZero is set.  A query starts at most kCertMax checks per launch, so
+// touching but disjoint pairs cannot make the proof attempts dominate.
+__device__ void certify_zero(const KArgs& A, unsigned q, unsigned ta, unsigned tb) {
+    QState& s = A.qs[q];
+    const int lane = threadIdx.x & 31;
+    unsigned go = 0;
+    if (lane == 0) go = !(ld_relaxed(&s.status) & kStatZero) && atomicAdd(&s.cert, 1u) < kCertMax;
+    if (!__shfl_sync(kFull, go, 0)) return;
+    V3<double> P, Q;
+    int ia, ib;
+    const double d = refine_pair_warp<0>(s, ta, tb, &P, &Q, &ia, &ib);
+    if (d == 0.0 && lane == 0 && !(atomicOr(&s.status, kStatZero) & kStatZero)) {
+        unsigned i = atomicAdd(A.ctr + kCtrCand, 1u);
+        if (i < A.cap_cand) A.cand[i] = Cand{ta, tb, -1.f, q};
+        else mark_overflow(A, q);
+    }
+}
+
 // Greedy descent from one front entry by one warp: at each step up to 32
 // descendant pairs (5 levels split between the two trees) are bounded, the
 // running bound takes their enhanced bounds (Eq. 10 / Eq. 11), and the walk
@@ -474,7 +555,9 @@ __device__ void probe(const KArgs& A, Item it, const QView& V) {
         const bool valid = lane < (1 << (kA + kB));
         const unsigned ia = (a << kA) | ((unsigned)lane >> kB);
         const unsigned ib = (b << kB) | ((unsigned)lane & ((1u << kB) - 1u));
-        const float Ucur = __uint_as_float(ld_relaxed(&A.qs[q].U));
+        bool stop;
+        const float Ucur = load_U(A.qs[q], &stop);
+        if (__any_sync(kFull, stop)) return;
         bool ok = false;
         unsigned newU = KIND == 0 ? 0xffffffffu : 0u, key = 0xffffffffu;
         if (valid) pair_bounds<KIND>(A, V, ia, ib, depth_of(b) + kB, Ucur, &ok, &newU, &key);
@@ -494,6 +577,13 @@ __device__ void probe(const KArgs& A, Item it, const QView& V) {
     float lo = 0.f, up = 0.f;
     if (valid) tri_pair_bounds<KIND>(V, ta, tb, &lo, &up);
     warp_bound_update<KIND>(valid, q, __float_as_uint(KIND == 0 ? up : lo), A.qs);
+    if (KIND == 0) {
+        const unsigned m = __ballot_sync(kFull, valid && lo <= 0.f);
+        if (m) {
+            const int src = __ffs(m) - 1;
+            certify_zero(A, q, __shfl_sync(kFull, ta, src), __shfl_sync(kFull, tb, src));
+        }
+    }
 }
 
 // ------------------------------------------------------------- phase 0
@@ -567,6 +657,8 @@ __device__ void setup_query(const KArgs& A, int q, int kind) {
     s.best_key = 0xffffffffffffffffull;
     s.slot_base = slot_base;
     s.dR = A.refit ? max(0, mb->L - kRefitH) : -1;
+    s.cert = 0u;
+    s.pushed[0] = s.pushed[1] = 0u;
 }
 
 // ------------------------------------------------------------- phase 2
@@ -620,7 +712,9 @@ __device__ void expand_level(const KArgs& A, int level, unsigned n, int s, unsig
         kA = min(s - kB, remA);
         unsigned local = (unsigned)(vt & mask);
         valid = valid && local < (1u << (kA + kB));
-        float Ucur = __uint_as_float(ld_relaxed(&A.qs[q].U));
+        bool stop;
+        float Ucur = load_U(A.qs[q], &stop);
+        valid = valid && !stop;
         if (KIND == 0) valid = valid && it.bound <= min_keep_threshold(Ucur, V.E_box);
         else valid = valid && it.bound >= max_keep_threshold(Ucur, V.E_box);
         if (valid && local == 0) bytes += 16ull + 24ull * ((1ull << kA) + (1ull << kB));
@@ -636,6 +730,23 @@ __device__ void expand_level(const KArgs& A, int level, unsigned n, int s, unsig
             bound = pair_bounds<KIND>(A, V, ia, ib, dBc, Ucur, &survive, &newU, &key);
         }
         warp_bound_update<KIND>(survive, q, newU, A.qs);
+        if (A.q_budget) {
+            // a batch query that pushes more than its share of the queues in
+            // this level leaves the batch (kStatEvict) and runs alone later,
+            // so that a few very large queries cannot crowd out the rest
+            const unsigned peers = __match_any_sync(kFull, survive ? q : 0xffffffffu);
+            const int leader = __ffs(peers) - 1;
+            unsigned over = 0u;
+            if (survive && lane == leader) {
+                const unsigned cnt = __popc(peers);
+                const unsigned old = atomicAdd(&A.qs[q].pushed[(level + 1) & 1], cnt);
+                if (old + cnt > A.q_budget) {
+                    over = 1u;
+                    atomicOr(&A.qs[q].status, kStatEvict);
+                }
+            }
+            if (__shfl_sync(kFull, over, leader)) survive = false;
+        }
         Item o = {ia, ib, bound, q};
         bool ok1 = warp_push(survive && !leafpair, o, out, out_cnt, A.cap_front);
         bool ok2 = warp_push(survive && leafpair, o, A.leafq, leaf_cnt, A.cap_leaf);
@@ -684,7 +795,9 @@ __device__ void leaf_phase(const KArgs& A, unsigned nleaf, unsigned& tripairs, u
         unsigned b0 = leaf_first(V.TB, V.LB, lb), b1 = leaf_first(V.TB, V.LB, lb + 1);
         unsigned ta = a0 + (sub >> 1), tb = b0 + (sub & 1);
         valid = valid && ta < a1 && tb < b1;
-        float Ucur = __uint_as_float(ld_relaxed(&A.qs[q].U));
+        bool stop;
+        float Ucur = load_U(A.qs[q], &stop);
+        valid = valid && !stop;
         if (KIND == 0) valid = valid && it.bound <= min_keep_threshold(Ucur, V.E_box);
         else valid = valid && it.bound >= max_keep_threshold(Ucur, V.E_box);
         if (valid && sub == 0) bytes += 16ull + 36ull * ((a1 - a0) + (b1 - b0));
@@ -692,10 +805,16 @@ __device__ void leaf_phase(const KArgs& A, unsigned nleaf, unsigned& tripairs, u
         float cb = 0.f;
         unsigned newU = KIND == 0 ? 0xffffffffu : 0u;
         bool have = false;
+        Tri32 TA, TB;
+        if (valid) {
+            TA = load_tri(V.triA, ta);
+            TB = load_tri(V.triB, tb);
+            valid = tri_pair_may_hold<KIND>(V, TA, TB, Ucur);
+        }
         if (valid) {
             ++tripairs;
             float lo, up;
-            tri_pair_bounds_tight<KIND>(A.qs[q], V, ta, tb, &lo, &up);
+            tri_pair_bounds_tight<KIND>(A.qs[q], V, TA, TB, &lo, &up);
             have = true;
             if (KIND == 0) {
                 newU = __float_as_uint(up);
@@ -711,6 +830,15 @@ __device__ void leaf_phase(const KArgs& A, unsigned nleaf, unsigned& tripairs, u
         Cand c = {ta, tb, cb, q};
         if (!warp_push(emit, c, A.cand, cand_cnt, A.cap_cand)) mark_overflow(A, q);
         if (emit) bytes += 16ull;
+        if (KIND == 0) {
+            // a pair that may touch: try to prove D_min = 0 with it
+            const unsigned m = __ballot_sync(kFull, emit && cb <= 0.f);
+            if (m) {
+                const int src = __ffs(m) - 1;
+                certify_zero(A, __shfl_sync(kFull, q, src), __shfl_sync(kFull, ta, src),
+                             __shfl_sync(kFull, tb, src));
+            }
+        }
     }
 }
 
@@ -850,8 +978,13 @@ __device__ void refine_phase(const KArgs& A, unsigned ncand, unsigned& refined, 
             continue;
         }
         QState& s = A.qs[c.q];
-        float U = __uint_as_float(ld_relaxed(&s.U));
-        bool keep = KIND == 0 ? (c.bound <= U) : (c.bound >= U);
+        bool stop;
+        const float U = load_U(s, &stop);
+        const unsigned st = ld_relaxed(&s.status);
+        // once D_min = 0 is proven only the proving pair (bound -1) is refined;
+        // an evicted query is answered by its own launch later
+        bool keep = KIND == 0 ? (stop ? (st & kStatZero) && c.bound < 0.f : c.bound <= U)
+                              : (!stop && c.bound >= U);
         double d = __longlong_as_double(-1ll);  // NaN: never selected
         if (keep) {
             V3<double> P, Q;
@@ -916,11 +1049,16 @@ __device__ void status_phase(const KArgs& A, unsigned long long first, unsigned 
         if (s.best_key == 0xffffffffffffffffull) st |= kStatNoResult;
         gd_result& r = A.out[q];
         unsigned code = GD_OK;
+        // a proven D_min = 0 stands even if some entries were lost to full
+        // queues or the query was evicted from its batch
+        if (st & kStatEvict) st |= kStatOverflow;
+        if ((st & kStatZero) && !(st & kStatNoResult)) st &= ~kStatOverflow;
         if (st & kStatOverflow) code = GD_ERR_OVERFLOW;
         else if (st & kStatTimeout) code = GD_ERR_TIMEOUT;
         else if (st & kStatNoResult) code = GD_ERR_CUDA;
         r.status = code;
         r.flags = (code == GD_OK && __ldcg(&r.d) == 0.0) ? 1u : 0u;
+        if (code == GD_OK && (st & kStatZero)) r.flags |= 2u;
         if (code != GD_OK) {
             r.d = __longlong_as_double(0x7ff8000000000000ll);
             r.tri_a = r.tri_b = -1;
@@ -960,6 +1098,7 @@ template <int KIND>
 __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
     unsigned long long pairs = 0, bytes = 0;
     unsigned tripairs = 0, refined = 0, refits = 0;
+    unsigned leaf_flushed = 0;
     bool probed = false;
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
     const unsigned long long gfirst = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1026,10 +1165,13 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
         bool ran = false;
         if (!refit_jobs(A, lead, refits, &ran)) goto done;
         if (ran) lap(1);
-        if (!probed && (A.refit ? ran : level == 1)) {
-            // probes start where B's boxes are first exact in A's frame (or
-            // at level 1 without refit), so that their greedy choices follow
-            // tight boxes
+        // probes start where B's boxes are first exact in A's frame (or at
+        // level 1 without refit), so that their greedy choices follow tight
+        // boxes; the min kind probes again on every level whose front has
+        // outgrown 4x the work target, where the descents to leaves may also
+        // prove D_min = 0 and so stop the growth
+        const bool reprobe = KIND == 0 && probed && (long long)n >= 4 * A.work_target;
+        if (reprobe || (!probed && (A.refit ? ran : level == 1))) {
             probed = true;
             // greedy probes from entries spread evenly over the front: every
             // warp takes one (at least one per query when the grid allows)
@@ -1053,9 +1195,9 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
                 }
                 probe<KIND>(A, it, V);
             }
-            if (lead) A.stats->probes = P;
+            if (lead) A.stats->probes += P;
             if (!grid_sync(A)) goto done;
-            if (lead) A.stats->u_probe = __uint_as_float(ld_relaxed(&A.qs[0].U));
+            if (lead && !reprobe) A.stats->u_probe = __uint_as_float(ld_relaxed(&A.qs[0].U));
             lap(2);
         }
         unsigned rmax = ld_relaxed(A.ctr + kCtrRem + level % 3);
@@ -1072,6 +1214,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
             }
             A.stats->levels = level + 1;
         }
+        if (A.q_budget)  // the counters of this level's pushes are those of level + 2
+            for (int q = (int)gfirst; q < A.nq; q += (int)gstride) A.qs[q].pushed[level & 1] = 0u;
         expand_level<KIND>(A, level, n, s, pairs, bytes);
         if (!grid_sync(A)) goto done;
         if (lead) {
@@ -1080,6 +1224,22 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
             t_levels += now - t_mark;
             t_mark = now;
         }
+        // a leaf queue at half its capacity is emptied through the leaf phase
+        // now (every CTA reads the same count: no push happens between the
+        // barrier above and the next level), so that the queue never has to
+        // hold the leaf pairs of all levels at once
+        unsigned nl = ld_relaxed(A.ctr + kCtrLeaf);
+        if (nl >= A.cap_leaf / 2) {
+            if (nl > A.cap_leaf) nl = A.cap_leaf;
+            leaf_phase<KIND>(A, nl, tripairs, bytes);
+            if (!grid_sync(A)) goto done;
+            if (lead) {
+                A.ctr[kCtrLeaf] = 0u;
+                leaf_flushed += nl;
+            }
+            if (!grid_sync(A)) goto done;
+            lap(4);
+        }
     }
     if (lead) A.stats->phase_ns[3] = (unsigned)t_levels;
 
@@ -1087,7 +1247,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
     {
         unsigned nleaf = ld_relaxed(A.ctr + kCtrLeaf);
         if (nleaf > A.cap_leaf) nleaf = A.cap_leaf;
-        if (lead) A.stats->leaf_pairs = nleaf;
+        if (lead) A.stats->leaf_pairs = leaf_flushed + nleaf;
         leaf_phase<KIND>(A, nleaf, tripairs, bytes);
     }
     if (!grid_sync(A)) goto done;
@@ -1115,7 +1275,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
                     while (ld_acquire(A.ctr + kCtrTailDone) < nc) {
                         if (ld_relaxed(A.ctr + kCtrAbort)) { go = 0; break; }
                         if ((long long)(globaltimer() - t0) > A.timeout_ns) {
-                            atomicExch(A.ctr + kCtrAbort, 1u);
+                            raise_abort(A);
                             go = 0;
                             break;
                         }

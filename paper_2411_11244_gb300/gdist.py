@@ -56,7 +56,7 @@ class gd_tunables(C.Structure):
     _fields_ = [("work_target", C.c_int64), ("k_max", C.c_int32), ("blocks_per_sm", C.c_int32),
                 ("front_capacity", C.c_int64), ("leaf_capacity", C.c_int64), ("cand_capacity", C.c_int64),
                 ("max_capacity", C.c_int64), ("timeout_ns", C.c_int64), ("refit_mode", C.c_int32),
-                ("refit_slots", C.c_int32), ("probes", C.c_int32)]
+                ("refit_slots", C.c_int32), ("probes", C.c_int32), ("batch_budget", C.c_int64)]
 
 
 class gd_stats(C.Structure):

@@ -203,12 +203,14 @@ def geosphere(freq: int, radius: float = 1.0, noise: float = 0.0, seed: int = 0,
 
 def gear(M: int = 2048, K: int = 24, teeth: int = 64, seed: int = 0,
          r_root: float = 0.9, tooth_h: float = 0.1, r_in: float = 0.4,
-         thick: float = 0.2, noise_frac: float = 0.01):
-    """Annular gear extruded along z: 4*M*K + 4*M triangles.
+         thick: float = 0.2, noise_frac: float = 0.01, cap_rings: int = 1):
+    """Annular gear extruded along z: 4*M*K + 4*M*cap_rings triangles.
 
     The outer profile has M points (M / teeth per tooth, trapezoidal teeth of
     height tooth_h, radial noise of noise_frac * tooth_h), the inner wall is a
-    circle of M points, K layers of quads on both walls, and two annular caps.
+    circle of M points, K layers of quads on both walls, and two annular caps
+    of cap_rings rings of quads each (1: one quad from the outer profile
+    straight to the inner circle).
     """
     rng = np.random.default_rng(seed)
     th = 2 * np.pi * np.arange(M) / M
@@ -243,17 +245,40 @@ def gear(M: int = 2048, K: int = 24, teeth: int = 64, seed: int = 0,
             t1, t2 = np.stack([a, b, c], -1), np.stack([a, c, d], -1)
         return np.stack([t1.reshape(-1, 3), t2.reshape(-1, 3)], axis=1).reshape(-1, 3)
 
+    extra = []  # intermediate cap rings (top then bottom), appended after the walls
+
+    def ring_ids(layer, k):
+        # vertex ids of ring k (0: outer profile, cap_rings: inner circle) of a cap
+        if k == 0:
+            return layer * M + np.arange(M)
+        if k == cap_rings:
+            return off_in + layer * M + np.arange(M)
+        return ring_base[layer] + (k - 1) * M + np.arange(M)
+
+    ring_base = {}
+    nv = len(verts)
+    for layer in (K, 0):
+        ring_base[layer] = nv + sum(len(e) for e in extra)
+        for k in range(1, cap_rings):
+            f = k / cap_rings
+            r = r_out + (r_in - r_out) * f
+            extra.append(np.stack([r * np.cos(th), r * np.sin(th), np.full(M, z[layer])], axis=-1))
+    if extra:
+        verts = np.concatenate([verts] + extra, axis=0)
+
     def cap(layer, flip):
-        m = np.arange(M)
-        a = layer * M + m
-        b = layer * M + (m + 1) % M
-        c = off_in + layer * M + (m + 1) % M
-        d = off_in + layer * M + m
-        if flip:
-            t1, t2 = np.stack([a, c, b], -1), np.stack([a, d, c], -1)
-        else:
-            t1, t2 = np.stack([a, b, c], -1), np.stack([a, c, d], -1)
-        return np.stack([t1, t2], axis=1).reshape(-1, 3)
+        out = []
+        for k in range(cap_rings):
+            o = ring_ids(layer, k)
+            i = ring_ids(layer, k + 1)
+            a, b = o, np.roll(o, -1)
+            c, d = np.roll(i, -1), i
+            if flip:
+                t1, t2 = np.stack([a, c, b], -1), np.stack([a, d, c], -1)
+            else:
+                t1, t2 = np.stack([a, b, c], -1), np.stack([a, c, d], -1)
+            out.append(np.stack([t1, t2], axis=1).reshape(-1, 3))
+        return np.concatenate(out, axis=0)
 
     tris = np.concatenate([wall(0, False), wall(off_in, True), cap(K, False), cap(0, True)], axis=0)
     return _f32(verts), _i32(tris)
@@ -378,10 +403,12 @@ def mesh_pool(n: int = 64, seed: int = 0, tmin: float = 1e3, tmax: float = 4e6):
             f = max(1, int(round(math.sqrt(T / 20))))
             m = geosphere(f, 1.0, 1e-3, seed * 1000 + k)
         else:
-            # 4 M K + 4 M = T, with K = 8 layers -> M = T / 36
-            Kl = 8
+            # near-square cells: wall layers K ~ M (thickness / circumference),
+            # cap rings ~ M (annulus width / circumference); T = 4 M K + 4 M rings
             teeth = 16
-            M = max(teeth * 2, int(round(T / (4 * Kl + 4) / teeth)) * teeth)
-            m = gear(M, Kl, teeth=teeth, seed=seed * 1000 + k)
+            M = max(teeth * 2, int(round(math.sqrt(T / 0.445) / teeth)) * teeth)
+            Kl = max(1, int(round(0.2 * M / (2 * math.pi))))
+            rings = max(1, int(round(0.5 * M / (2 * math.pi))))
+            m = gear(M, Kl, teeth=teeth, seed=seed * 1000 + k, cap_rings=rings)
         out.append(m)
     return out

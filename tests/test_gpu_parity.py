@@ -55,6 +55,21 @@ def check(r, A, xa, B, xb, kind, ref, diag, oracle):
     assert (r.flags & 1) == (1 if r.d == 0.0 else 0)
 
 
+def same_answer(r1, r2, oracle, A, xa, B, xb, kind):
+    """Two answers to one query agree: equal value; for d > 0 the same witness
+    (the smallest original (tri_a, tri_b) at the extreme is unique); for a min
+    of 0 each witness is a pair the oracle finds intersecting (the traversal
+    stops at the first such pair it proves, so the pair may differ)."""
+    assert r1.status == 0 and r2.status == 0, (r1.status, r2.status)
+    assert r1.d == r2.d, (r1.d, r2.d)
+    if r1.d != 0.0 or kind != "min":
+        assert (r1.tri_a, r1.tri_b) == (r2.tri_a, r2.tri_b)
+        return
+    for r in (r1, r2):
+        dw, _, _ = oracle.witness_distance(A, xa, B, xb, r.tri_a, r.tri_b, "min")
+        assert dw == 0.0, (r.tri_a, r.tri_b, dw)
+
+
 def run_pair(G, ctx, oracle, A, B, xforms, kinds=("min", "max"), bvh_oracle=False):
     ma, mb = _mesh(G, ctx, A), _mesh(G, ctx, B)
     oa = ob = None
@@ -244,23 +259,50 @@ def test_batch_matches_single(G, ctx, oracle_mod):
     rng = np.random.default_rng(77)
     A = synth.gear(256, 4, teeth=16, seed=2)
     B = synth.geosphere(9, 0.5, 1e-3, 5)
+    Tm = synth.torus(1.0, 0.2, 24, 10)
     ma, mb = _mesh(G, ctx, A), _mesh(G, ctx, B)
-    mt = _mesh(G, ctx, synth.torus(1.0, 0.2, 24, 10))
-    items = []
+    mt = _mesh(G, ctx, Tm)
+    items, data = [], []
     for i in range(40):
         xa = _rigid(rng, 0.2)
         xb = _rigid(rng, 1.2)
         pair = [(ma, mb), (mb, mt), (mt, ma)][i % 3]
+        data.append([(A, B), (B, Tm), (Tm, A)][i % 3])
         items.append((pair[0], pair[1], xa, xb, i % 2))
     out = G.gd_batch_query(ctx, items)
     for i, (a, b, xa, xb, kind) in enumerate(items):
         fn = G.gd_min_distance if kind == 0 else G.gd_max_distance
         r = fn(ctx, a, b, xa, xb)
-        assert out[i].status == 0
-        assert out[i].d == r.d
-        assert (out[i].tri_a, out[i].tri_b) == (r.tri_a, r.tri_b)
+        same_answer(out[i], r, oracle_mod, data[i][0], xa, data[i][1], xb, "min" if kind == 0 else "max")
     for h in (ma, mb, mt):
         G.gd_mesh_destroy(h)
+
+
+def test_batch_eviction_matches_single(G, oracle_mod):
+    """A query of a batch that pushes more than its share of the queues in one
+    level leaves the batch and runs alone.  With queues of 1024 entries and 24
+    queries the share is 21 entries per level, so most queries are evicted;
+    every answer still equals the single-query answer."""
+    c = G.gd_ctx_create(0)
+    try:
+        rng = np.random.default_rng(91)
+        A = synth.gear(256, 4, teeth=16, seed=2)
+        B = synth.geosphere(9, 0.5, 1e-3, 5)
+        ma, mb = _mesh(G, c, A), _mesh(G, c, B)
+        items = [(ma, mb, _rigid(rng, 0.2), _rigid(rng, 1.2), i % 2) for i in range(24)]
+        alone = []
+        for a, b, xa, xb, kind in items:
+            fn = G.gd_min_distance if kind == 0 else G.gd_max_distance
+            alone.append(fn(c, a, b, xa, xb))
+        G.gd_ctx_set_tunables(c, front_capacity=1024, leaf_capacity=1024, batch_budget=8)
+        out = G.gd_batch_query(c, items)
+        assert G.gd_get_stats(c)["retries"] > 0
+        for i, (a, b, xa, xb, kind) in enumerate(items):
+            same_answer(out[i], alone[i], oracle_mod, A, xa, B, xb, "min" if kind == 0 else "max")
+        G.gd_mesh_destroy(ma)
+        G.gd_mesh_destroy(mb)
+    finally:
+        G.gd_ctx_destroy(c)
 
 
 def test_refit_modes_agree(G, oracle_mod):
@@ -274,12 +316,12 @@ def test_refit_modes_agree(G, oracle_mod):
         ma, mb = _mesh(G, c, A), _mesh(G, c, B)
         for i in range(6):
             xa, xb = _rigid(rng, 0.3), _rigid(rng, 1.2)
-            for fn in (G.gd_min_distance, G.gd_max_distance):
+            for kind, fn in (("min", G.gd_min_distance), ("max", G.gd_max_distance)):
                 G.gd_ctx_set_tunables(c, refit_mode=1)
                 r1 = fn(c, ma, mb, xa, xb)
                 G.gd_ctx_set_tunables(c, refit_mode=2)
                 r2 = fn(c, ma, mb, xa, xb)
-                assert r1.d == r2.d and (r1.tri_a, r1.tri_b) == (r2.tri_a, r2.tri_b)
+                same_answer(r1, r2, oracle_mod, A, xa, B, xb, kind)
         G.gd_mesh_destroy(ma)
         G.gd_mesh_destroy(mb)
     finally:
@@ -307,22 +349,53 @@ def test_device_resident_query(G, ctx, oracle_mod):
 def test_overflow_grows_then_reports(G, oracle_mod):
     """Capacity faults are injected on the host: tiny queues must grow and
     still give the oracle's answer; a growth limit below the need reports
-    GD_ERR_OVERFLOW."""
+    GD_ERR_OVERFLOW.  Two parallel grids 0.01 apart: every facing pair is at
+    the minimum, so the fronts are large and nothing intersects."""
     c = G.gd_ctx_create(0)
     try:
-        A = synth.torus(1.0, 0.3, 32, 32)
+        A = synth.grid(32, 1.0, 0.0)
+        B = synth.grid(32, 1.0, 0.01)
         I = synth.identity_xform()
-        xb = synth.xform(np.eye(3), (0.4, 0.0, 0.0))  # heavy overlap: large fronts
-        ma, mb = _mesh(G, c, A), _mesh(G, c, A)
+        ma, mb = _mesh(G, c, A), _mesh(G, c, B)
         G.gd_ctx_set_tunables(c, front_capacity=64, leaf_capacity=64, cand_capacity=16, max_capacity=1 << 24)
-        r = G.gd_min_distance(c, ma, mb, I, xb)
-        ref = oracle_mod.brute(A, I, A, xb)
-        check(r, A, I, A, xb, "min", ref, oracle_mod.diag(A, I, A, xb), oracle_mod)
+        r = G.gd_min_distance(c, ma, mb, I, I)
+        ref = oracle_mod.brute(A, I, B, I)
+        check(r, A, I, B, I, "min", ref, oracle_mod.diag(A, I, B, I), oracle_mod)
         assert G.gd_get_stats(c)["retries"] > 0
         G.gd_ctx_set_tunables(c, front_capacity=64, leaf_capacity=64, cand_capacity=16, max_capacity=128)
         with pytest.raises(G.GdError) as e:
-            G.gd_min_distance(c, ma, mb, I, xb)
+            G.gd_min_distance(c, ma, mb, I, I)
         assert e.value.status == G.GD_ERR_OVERFLOW
+        G.gd_mesh_destroy(ma)
+        G.gd_mesh_destroy(mb)
+    finally:
+        G.gd_ctx_destroy(c)
+
+
+def test_zero_proof_stops_traversal(G, oracle_mod):
+    """D_min = 0 (Section 8, penetration): a pair proven to intersect in
+    float64 ends the query.  Coincident copies of one mesh overlap everywhere,
+    so without the proof the fronts need far more than 128 entries; with it
+    the answer is 0 (flags bit 1 set) and its witness intersects in the
+    oracle.  Two tori crossing each other give 0 with a valid witness too."""
+    c = G.gd_ctx_create(0)
+    try:
+        rng = np.random.default_rng(12)
+        A = synth.torus(1.0, 0.25, 64, 32)
+        x = _rigid(rng, 0.5)
+        ma, mb = _mesh(G, c, A), _mesh(G, c, A)
+        G.gd_ctx_set_tunables(c, front_capacity=64, leaf_capacity=64, cand_capacity=16, max_capacity=128)
+        r = G.gd_min_distance(c, ma, mb, x, x)
+        assert r.status == 0 and r.d == 0.0 and r.flags == 3, (r.status, r.d, r.flags)
+        dw, _, _ = oracle_mod.witness_distance(A, x, A, x, r.tri_a, r.tri_b, "min")
+        assert dw == 0.0
+        G.gd_ctx_set_tunables(c, front_capacity=1 << 16, leaf_capacity=1 << 16, cand_capacity=1 << 14,
+                              max_capacity=1 << 26)
+        xb = synth.compose(x, synth.xform(np.eye(3), (0.4, 0.0, 0.0)))
+        r = G.gd_min_distance(c, ma, mb, x, xb)
+        ref = oracle_mod.brute(A, x, A, xb)
+        assert ref.d == 0.0
+        check(r, A, x, A, xb, "min", ref, oracle_mod.diag(A, x, A, xb), oracle_mod)
         G.gd_mesh_destroy(ma)
         G.gd_mesh_destroy(mb)
     finally:
@@ -362,9 +435,10 @@ def test_serve_alone_equals_in_mix(G, ctx, oracle_mod):
     rng = np.random.default_rng(5)
     meshes = [synth.torus(1.0, 0.25, 40, 20), synth.geosphere(12, 0.6, 1e-3, 1), synth.gear(256, 4, teeth=16, seed=3)]
     hs = [_mesh(G, ctx, m) for m in meshes]
-    qs = []
+    qs, ids = [], []
     for i in range(60):
         a, b = int(rng.integers(0, 3)), int(rng.integers(0, 3))
+        ids.append((a, b))
         qs.append((hs[a], hs[b], _rigid(rng, 0.3), _rigid(rng, 1.5), int(rng.integers(0, 2))))
     arr = G.make_queries(qs)
     alone = []
@@ -394,10 +468,9 @@ def test_serve_alone_equals_in_mix(G, ctx, oracle_mod):
         G.gd_serve_stop(srv)
     assert len(got) == len(tickets)
     for i, t in enumerate(tickets):
-        r = got[t]
-        assert r.status == 0
-        assert r.d == alone[i].d
-        assert (r.tri_a, r.tri_b) == (alone[i].tri_a, alone[i].tri_b)
+        a, b = ids[i]
+        same_answer(got[t], alone[i], oracle_mod, meshes[a], qs[i][2], meshes[b], qs[i][3],
+                    "min" if qs[i][4] == 0 else "max")
     for h in hs:
         G.gd_mesh_destroy(h)
 
