@@ -211,8 +211,11 @@ __device__ __forceinline__ void raise_abort(const KArgs& A) {
 // is visible to every thread after it; no other fence is needed.  The top
 // bit of the same word is the abort flag, so the wait sees an abort with no
 // extra load.  Every wait is bounded: after timeout_ns the CTA raises the
-// abort and returns false.
-__device__ __forceinline__ bool grid_sync(const KArgs& A) {
+// abort and returns false.  post() runs on thread 0 after a successful wait,
+// before the CTA's closing __syncthreads (it refreshes CTA-shared copies of
+// global state).
+template <class F>
+__device__ __forceinline__ bool grid_sync(const KArgs& A, F&& post) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -238,10 +241,15 @@ __device__ __forceinline__ bool grid_sync(const KArgs& A) {
                 }
             }
         }
+        if (ok) post();
         s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+__device__ __forceinline__ bool grid_sync(const KArgs& A) {
+    return grid_sync(A, [] {});
 }
 
 }  // namespace gd

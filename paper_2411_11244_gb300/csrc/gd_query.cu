@@ -131,10 +131,170 @@ __device__ __forceinline__ bool warp_push(bool want, const E& v, E* buf, unsigne
     return false;
 }
 
+// Defensive index checks: a record read back from a work buffer must name a
+// query of this launch and nodes / triangles of its meshes.  A failed check
+// sets a bit in the counters (the host reports an internal error) and the
+// access is skipped, so a bad record can never become an out-of-range load.
+enum : unsigned {
+    kBadFront = 1u, kBadLeaf = 2u, kBadCand = 4u, kBadJob = 8u, kBadProbe = 16u,
+};
+
+__device__ __forceinline__ bool item_ok(const KArgs& A, const Item& it) {
+    return it.q < (unsigned)A.nq && it.a >= 1u && it.b >= 1u;
+}
+
+__device__ __forceinline__ void flag_bad(const KArgs& A, unsigned bit) { atomicOr(A.ctr + kCtrBadIndex, bit); }
+
+__device__ __forceinline__ void mark_overflow(const KArgs& A, unsigned q) {
+    atomicOr(&A.qs[q].status, kStatOverflow);
+    atomicOr(A.ctr + kCtrOverflow, 1u);
+}
+
+// the constants of one query that the traversal reads
+struct QConst {
+    Rigid32 X;
+    float E_box, E_tri;
+    const float* boxA;
+    const float* boxB;
+    const float4* triA;
+    const float4* triB;
+    long long TA, TB;
+    int LA, LB;
+    int dR;
+    unsigned slot_base;
+};
+
+// cached per-thread view of one query's constants
+struct QView : QConst {
+    unsigned q = 0xffffffffu;
+};
+
+// Per-CTA shared copies of global state, refreshed by thread 0 right after
+// every grid barrier (the barrier's closing __syncthreads publishes them):
+// the counters, and in a single-query launch the query's constants and its
+// running bound and status.  Reading these from shared memory instead of
+// L2 keeps 2,000+ warps from queueing on the same few words; a CTA's own
+// bound improvements lower its copy at once and reach the global bound by one
+// atomic each.
+struct CtaState {
+    QConst v;                 // query 0 (single-query launches)
+    float Rl[9], tl[3], E_df; // its double-float map remainders
+    unsigned ctr[kCtrReset];  // counters at the last barrier
+    unsigned U, stat;         // its running bound (lowered by this CTA) and status
+    unsigned cnt[2][2];       // entries this CTA appends in one iteration (by parity, queue)
+    unsigned base[2];         // their first index in each queue
+    unsigned rem;             // max remaining depth this CTA pushed in this level
+    int ready;                // v, Rl, tl, E_df loaded
+};
+
+__device__ __forceinline__ CtaState& cta() {
+    __shared__ CtaState s;
+    return s;
+}
+
+__device__ __forceinline__ void load_qconst(const QState& s, QConst& V) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) V.X.R[i] = s.R[i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) V.X.t[i] = s.t[i];
+    V.E_box = s.E_box;
+    V.E_tri = s.E_tri;
+    const MeshDev* ma = s.A;
+    const MeshDev* mb = s.B;
+    V.boxA = ma->box; V.boxB = mb->box;
+    V.triA = ma->tri; V.triB = mb->tri;
+    V.TA = ma->T; V.TB = mb->T;
+    V.LA = ma->L; V.LB = mb->L;
+    V.dR = s.dR;
+    V.slot_base = s.slot_base;
+}
+
+// The constant fields of a QState are written once, in phase 0, before the
+// first barrier, and no CTA reads them earlier in the launch: plain (L1
+// cached) loads are safe for them.  U, status and the other fields written
+// during the traversal are always read with relaxed GPU-scope loads.
+__device__ __forceinline__ void view(const KArgs& A, unsigned q, QView& V) {
+    if (V.q == q) return;
+    if (A.nq == 1) static_cast<QConst&>(V) = cta().v;
+    else load_qconst(A.qs[q], V);
+    V.q = q;
+}
+
+// Thread 0's refresh of the CTA state after a barrier.
+__device__ __forceinline__ void cta_refresh(const KArgs& A) {
+    CtaState& c = cta();
+    unsigned v[kCtrReset];
+#pragma unroll
+    for (int i = 0; i < kCtrReset; ++i) v[i] = ld_relaxed(A.ctr + i);
+#pragma unroll
+    for (int i = 0; i < kCtrReset; ++i) c.ctr[i] = v[i];
+    if (A.nq == 1) {
+        const unsigned long long w = ld_relaxed64(reinterpret_cast<const unsigned long long*>(&A.qs[0].U));
+        c.U = (unsigned)w;
+        c.stat = (unsigned)(w >> 32);
+        if (!c.ready) {
+            const QState& s = A.qs[0];
+            load_qconst(s, c.v);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) c.Rl[i] = s.Rl[i];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) c.tl[i] = s.tl[i];
+            c.E_df = s.E_df;
+            c.ready = 1;
+        }
+    }
+    c.cnt[0][0] = c.cnt[0][1] = c.cnt[1][0] = c.cnt[1][1] = 0u;
+    c.rem = 0u;
+}
+
+__device__ __forceinline__ bool sync(const KArgs& A) {
+    return grid_sync(A, [&] { cta_refresh(A); });
+}
+
+// The running bound U of a query and whether its traversal has stopped
+// (D_min = 0 proven, or evicted from a batch), in one relaxed load (U and
+// status are adjacent in an 8-byte aligned word).
+__device__ __forceinline__ float load_U(const QState& s, bool* stop) {
+    const unsigned long long w = ld_relaxed64(reinterpret_cast<const unsigned long long*>(&s.U));
+    *stop = ((unsigned)(w >> 32) & kStatStop) != 0u;
+    return __uint_as_float((unsigned)w);
+}
+
+// The same for query q of this launch: a single-query launch reads the CTA's
+// copy (the bound at the last barrier, lowered by this CTA since).
+__device__ __forceinline__ float load_Uq(const KArgs& A, unsigned q, bool* stop) {
+    if (A.nq == 1) {
+        const volatile CtaState& c = cta();
+        *stop = (c.stat & kStatStop) != 0u;
+        return __uint_as_float(c.U);
+    }
+    return load_U(A.qs[q], stop);
+}
+
 // Lower (KIND 0) or raise (KIND 1) the running bound of query q by bits v.
-// All lanes of the warp call this; lanes with have == false pass nothing.
+// All lanes of the warp call this; lanes with have == false pass nothing.  A
+// single-query launch lowers the CTA's copy first and sends the global atomic
+// only for a warp value that beats it.
 template <int KIND>
-__device__ __forceinline__ void warp_bound_update(bool have, unsigned q, unsigned v, QState* qs) {
+__device__ __forceinline__ void warp_bound_update(const KArgs& A, bool have, unsigned q, unsigned v) {
+    if (A.nq == 1) {
+        const unsigned r = KIND == 0 ? __reduce_min_sync(kFull, have ? v : 0xffffffffu)
+                                     : __reduce_max_sync(kFull, have ? v : 0u);
+        if ((threadIdx.x & 31) == 0) {
+            volatile unsigned* cu = &cta().U;
+            if (KIND == 0 ? r < *cu : r > *cu) {
+                if (KIND == 0) {
+                    atomicMin(const_cast<unsigned*>(cu), r);
+                    atomicMin(&A.qs[0].U, r);
+                } else {
+                    atomicMax(const_cast<unsigned*>(cu), r);
+                    atomicMax(&A.qs[0].U, r);
+                }
+            }
+        }
+        return;
+    }
+    QState* qs = A.qs;
     unsigned q0 = __shfl_sync(kFull, q, 0);
     bool uniform = __all_sync(kFull, q == q0);
     if (uniform) {
@@ -155,67 +315,49 @@ __device__ __forceinline__ void warp_bound_update(bool have, unsigned q, unsigne
     }
 }
 
-// Defensive index checks: a record read back from a work buffer must name a
-// query of this launch and nodes / triangles of its meshes.  A failed check
-// sets a bit in the counters (the host reports an internal error) and the
-// access is skipped, so a bad record can never become an out-of-range load.
-enum : unsigned {
-    kBadFront = 1u, kBadLeaf = 2u, kBadCand = 4u, kBadJob = 8u, kBadProbe = 16u,
-};
-
-__device__ __forceinline__ bool item_ok(const KArgs& A, const Item& it) {
-    return it.q < (unsigned)A.nq && it.a >= 1u && it.b >= 1u;
-}
-
-__device__ __forceinline__ void flag_bad(const KArgs& A, unsigned bit) { atomicOr(A.ctr + kCtrBadIndex, bit); }
-
-__device__ __forceinline__ void mark_overflow(const KArgs& A, unsigned q) {
-    atomicOr(&A.qs[q].status, kStatOverflow);
-    atomicOr(A.ctr + kCtrOverflow, 1u);
-}
-
-// The running bound U of a query and whether its traversal has stopped
-// (D_min = 0 proven, or evicted from a batch), in one relaxed load (U and
-// status are adjacent in an 8-byte aligned word).
-__device__ __forceinline__ float load_U(const QState& s, bool* stop) {
-    const unsigned long long w = ld_relaxed64(reinterpret_cast<const unsigned long long*>(&s.U));
-    *stop = ((unsigned)(w >> 32) & kStatStop) != 0u;
-    return __uint_as_float((unsigned)w);
-}
-
-// cached per-thread view of one query's constants
-struct QView {
-    unsigned q = 0xffffffffu;
-    Rigid32 X;
-    float E_box, E_tri;
-    const float* boxA;
-    const float* boxB;
-    const float4* triA;
-    const float4* triB;
-    long long TA, TB;
-    int LA, LB;
-    int dR;
-    unsigned slot_base;
-};
-
-__device__ __forceinline__ void view(const KArgs& A, unsigned q, QView& V) {
-    if (V.q == q) return;
-    const QState& s = A.qs[q];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) V.X.R[i] = __ldcg(&s.R[i]);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) V.X.t[i] = __ldcg(&s.t[i]);
-    V.E_box = __ldcg(&s.E_box);
-    V.E_tri = __ldcg(&s.E_tri);
-    const MeshDev* ma = s.A;
-    const MeshDev* mb = s.B;
-    V.boxA = ma->box; V.boxB = mb->box;
-    V.triA = ma->tri; V.triB = mb->tri;
-    V.TA = ma->T; V.TB = mb->T;
-    V.LA = ma->L; V.LB = mb->L;
-    V.dR = __ldcg(&s.dR);
-    V.slot_base = __ldcg(&s.slot_base);
-    V.q = q;
+// Append the entries of one CTA-wide iteration to two queues (want0 -> buf0,
+// want1 -> buf1) with one global atomic per queue and CTA: the warps count
+// into shared memory, threads 0 and 32 reserve the CTA's ranges.  Every
+// thread of the CTA calls it in the same iteration it (its parity picks the
+// shared counters, the other parity is cleared for the next iteration).
+// Returns false for a lane whose entry did not fit.
+template <class E>
+__device__ __forceinline__ bool cta_push2(int it, const E& v, bool want0, E* buf0, unsigned* cnt0, unsigned cap0,
+                                          bool want1, E* buf1, unsigned* cnt1, unsigned cap1) {
+    CtaState& c = cta();
+    const int lane = threadIdx.x & 31, p = it & 1;
+    const unsigned m0 = __ballot_sync(kFull, want0), m1 = __ballot_sync(kFull, want1);
+    unsigned o0 = 0u, o1 = 0u;
+    if (lane == 0) {
+        if (m0) o0 = atomicAdd(&c.cnt[p][0], (unsigned)__popc(m0));
+        if (m1) o1 = atomicAdd(&c.cnt[p][1], (unsigned)__popc(m1));
+    }
+    o0 = __shfl_sync(kFull, o0, 0);
+    o1 = __shfl_sync(kFull, o1, 0);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned n = c.cnt[p][0];
+        c.base[0] = n ? atomicAdd(cnt0, n) : 0u;
+        c.cnt[p ^ 1][0] = 0u;
+    } else if (threadIdx.x == 32) {
+        const unsigned n = c.cnt[p][1];
+        c.base[1] = n ? atomicAdd(cnt1, n) : 0u;
+        c.cnt[p ^ 1][1] = 0u;
+    }
+    __syncthreads();
+    const unsigned lt = lanemask_lt();
+    bool ok = true;
+    if (want0) {
+        const unsigned idx = c.base[0] + o0 + __popc(m0 & lt);
+        if (idx < cap0) __stcg(reinterpret_cast<float4*>(buf0 + idx), *reinterpret_cast<const float4*>(&v));
+        else ok = false;
+    }
+    if (want1) {
+        const unsigned idx = c.base[1] + o1 + __popc(m1 & lt);
+        if (idx < cap1) __stcg(reinterpret_cast<float4*>(buf1 + idx), *reinterpret_cast<const float4*>(&v));
+        else ok = false;
+    }
+    return ok;
 }
 
 // Refit slot holding B node b (depth db >= dR) in A's frame, or kNoSlot.
@@ -317,14 +459,24 @@ __device__ __forceinline__ void tri_pair_bounds(const QView& V, unsigned ta, uns
 // Used for pairs that pass the float32 test, so that only near-ties reach the
 // float64 refinement; it stays on the float32 pipe (float64 is slow here).
 template <int KIND>
-__device__ __forceinline__ void tri_pair_bounds_tight(const QState& s, const QView& V, const Tri32& TA,
+__device__ __forceinline__ void tri_pair_bounds_tight(const KArgs& A, unsigned q, const QView& V, const Tri32& TA,
                                                       const Tri32& TB, float* lo, float* up) {
-    float Rl[9], tl[3];
+    float Rl[9], tl[3], Edf;
+    if (A.nq == 1) {
+        const CtaState& c = cta();
 #pragma unroll
-    for (int i = 0; i < 9; ++i) Rl[i] = __ldcg(&s.Rl[i]);
+        for (int i = 0; i < 9; ++i) Rl[i] = c.Rl[i];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) tl[i] = __ldcg(&s.tl[i]);
-    const float Edf = __ldcg(&s.E_df);
+        for (int i = 0; i < 3; ++i) tl[i] = c.tl[i];
+        Edf = c.E_df;
+    } else {
+        const QState& s = A.qs[q];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) Rl[i] = s.Rl[i];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) tl[i] = s.tl[i];
+        Edf = s.E_df;
+    }
     const V3<float> o = TA.v[0];
     const float oc[3] = {o.x, o.y, o.z};
     V3<float> Al[3], Bl[3];
@@ -525,10 +677,13 @@ __device__ void certify_zero(const KArgs& A, unsigned q, unsigned ta, unsigned t
     V3<double> P, Q;
     int ia, ib;
     const double d = refine_pair_warp<0>(s, ta, tb, &P, &Q, &ia, &ib);
-    if (d == 0.0 && lane == 0 && !(atomicOr(&s.status, kStatZero) & kStatZero)) {
-        unsigned i = atomicAdd(A.ctr + kCtrCand, 1u);
-        if (i < A.cap_cand) A.cand[i] = Cand{ta, tb, -1.f, q};
-        else mark_overflow(A, q);
+    if (d == 0.0 && lane == 0) {
+        if (A.nq == 1) atomicOr(&cta().stat, kStatZero);
+        if (!(atomicOr(&s.status, kStatZero) & kStatZero)) {
+            unsigned i = atomicAdd(A.ctr + kCtrCand, 1u);
+            if (i < A.cap_cand) A.cand[i] = Cand{ta, tb, -1.f, q};
+            else mark_overflow(A, q);
+        }
     }
 }
 
@@ -556,12 +711,12 @@ __device__ void probe(const KArgs& A, Item it, const QView& V) {
         const unsigned ia = (a << kA) | ((unsigned)lane >> kB);
         const unsigned ib = (b << kB) | ((unsigned)lane & ((1u << kB) - 1u));
         bool stop;
-        const float Ucur = load_U(A.qs[q], &stop);
+        const float Ucur = load_Uq(A, q, &stop);
         if (__any_sync(kFull, stop)) return;
         bool ok = false;
         unsigned newU = KIND == 0 ? 0xffffffffu : 0u, key = 0xffffffffu;
         if (valid) pair_bounds<KIND>(A, V, ia, ib, depth_of(b) + kB, Ucur, &ok, &newU, &key);
-        warp_bound_update<KIND>(ok, q, newU, A.qs);
+        warp_bound_update<KIND>(A, ok, q, newU);
         const unsigned best = __reduce_min_sync(kFull, ok ? key : 0xffffffffu);
         const unsigned m = __ballot_sync(kFull, ok && key == best);
         if (m == 0) return;
@@ -576,7 +731,7 @@ __device__ void probe(const KArgs& A, Item it, const QView& V) {
     const bool valid = lane < 4 && ta < a1 && tb < b1;
     float lo = 0.f, up = 0.f;
     if (valid) tri_pair_bounds<KIND>(V, ta, tb, &lo, &up);
-    warp_bound_update<KIND>(valid, q, __float_as_uint(KIND == 0 ? up : lo), A.qs);
+    warp_bound_update<KIND>(A, valid, q, __float_as_uint(KIND == 0 ? up : lo));
     if (KIND == 0) {
         const unsigned m = __ballot_sync(kFull, valid && lo <= 0.f);
         if (m) {
@@ -682,9 +837,12 @@ __device__ void expand_level(const KArgs& A, int level, unsigned n, int s, unsig
     const unsigned long long mask = (1ull << s) - 1;
     const int lane = threadIdx.x & 31;
     QView V;
-    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
-         base < total; base += gstride) {
-        unsigned long long vt = base + lane;
+    // CTA-uniform loop: every thread of a CTA runs the same iterations, so
+    // that the appends can be counted per CTA (cta_push2)
+    int iter = 0;
+    for (unsigned long long cbase = (unsigned long long)blockIdx.x * blockDim.x; cbase < total;
+         cbase += gstride, ++iter) {
+        unsigned long long vt = cbase + threadIdx.x;
         bool valid = vt < total;
         Item it = {1u, 1u, 0.f, 0u};
         if (valid) {
@@ -713,7 +871,7 @@ __device__ void expand_level(const KArgs& A, int level, unsigned n, int s, unsig
         unsigned local = (unsigned)(vt & mask);
         valid = valid && local < (1u << (kA + kB));
         bool stop;
-        float Ucur = load_U(A.qs[q], &stop);
+        float Ucur = load_Uq(A, q, &stop);
         valid = valid && !stop;
         if (KIND == 0) valid = valid && it.bound <= min_keep_threshold(Ucur, V.E_box);
         else valid = valid && it.bound >= max_keep_threshold(Ucur, V.E_box);
@@ -729,7 +887,7 @@ __device__ void expand_level(const KArgs& A, int level, unsigned n, int s, unsig
             ++pairs;
             bound = pair_bounds<KIND>(A, V, ia, ib, dBc, Ucur, &survive, &newU, &key);
         }
-        warp_bound_update<KIND>(survive, q, newU, A.qs);
+        warp_bound_update<KIND>(A, survive, q, newU);
         if (A.q_budget) {
             // a batch query that pushes more than its share of the queues in
             // this level leaves the batch (kStatEvict) and runs alone later,
@@ -748,15 +906,20 @@ __device__ void expand_level(const KArgs& A, int level, unsigned n, int s, unsig
             if (__shfl_sync(kFull, over, leader)) survive = false;
         }
         Item o = {ia, ib, bound, q};
-        bool ok1 = warp_push(survive && !leafpair, o, out, out_cnt, A.cap_front);
-        bool ok2 = warp_push(survive && leafpair, o, A.leafq, leaf_cnt, A.cap_leaf);
-        if (!ok1 || !ok2) mark_overflow(A, q);
+        if (!cta_push2(iter, o, survive && !leafpair, out, out_cnt, A.cap_front, survive && leafpair, A.leafq,
+                       leaf_cnt, A.cap_leaf))
+            mark_overflow(A, q);
         if (survive) bytes += 16ull;
         if (survive && !leafpair && dBc == V.dR) claim_root(A, V, q, ib);
         // remaining depth of the entries pushed to the next front
         unsigned rem = (survive && !leafpair) ? (unsigned)(remA - kA + remB - kB) : 0u;
         rem = __reduce_max_sync(kFull, rem);
-        if (lane == 0 && rem > 0 && rem > ld_relaxed(out_rem)) atomicMax(out_rem, rem);
+        if (lane == 0 && rem > 0) atomicMax(&cta().rem, rem);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned r = cta().rem;
+        if (r > 0) atomicMax(out_rem, r);
     }
 }
 
@@ -769,9 +932,10 @@ __device__ void leaf_phase(const KArgs& A, unsigned nleaf, unsigned& tripairs, u
     const int lane = threadIdx.x & 31;
     unsigned* cand_cnt = A.ctr + kCtrCand;
     QView V;
-    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
-         base < total; base += gstride) {
-        unsigned long long vt = base + lane;
+    int iter = 0;
+    for (unsigned long long cbase = (unsigned long long)blockIdx.x * blockDim.x; cbase < total;
+         cbase += gstride, ++iter) {
+        unsigned long long vt = cbase + threadIdx.x;
         bool valid = vt < total;
         Item it = {1u, 1u, 0.f, 0u};
         if (valid) {
@@ -796,7 +960,7 @@ __device__ void leaf_phase(const KArgs& A, unsigned nleaf, unsigned& tripairs, u
         unsigned ta = a0 + (sub >> 1), tb = b0 + (sub & 1);
         valid = valid && ta < a1 && tb < b1;
         bool stop;
-        float Ucur = load_U(A.qs[q], &stop);
+        float Ucur = load_Uq(A, q, &stop);
         valid = valid && !stop;
         if (KIND == 0) valid = valid && it.bound <= min_keep_threshold(Ucur, V.E_box);
         else valid = valid && it.bound >= max_keep_threshold(Ucur, V.E_box);
@@ -814,7 +978,7 @@ __device__ void leaf_phase(const KArgs& A, unsigned nleaf, unsigned& tripairs, u
         if (valid) {
             ++tripairs;
             float lo, up;
-            tri_pair_bounds_tight<KIND>(A.qs[q], V, TA, TB, &lo, &up);
+            tri_pair_bounds_tight<KIND>(A, q, V, TA, TB, &lo, &up);
             have = true;
             if (KIND == 0) {
                 newU = __float_as_uint(up);
@@ -826,9 +990,10 @@ __device__ void leaf_phase(const KArgs& A, unsigned nleaf, unsigned& tripairs, u
                 emit = up >= fmaxf(Ucur, lo);
             }
         }
-        warp_bound_update<KIND>(have, q, newU, A.qs);
+        warp_bound_update<KIND>(A, have, q, newU);
         Cand c = {ta, tb, cb, q};
-        if (!warp_push(emit, c, A.cand, cand_cnt, A.cap_cand)) mark_overflow(A, q);
+        if (!cta_push2(iter, c, emit, A.cand, cand_cnt, A.cap_cand, false, (Cand*)nullptr, (unsigned*)nullptr, 0u))
+            mark_overflow(A, q);
         if (emit) bytes += 16ull;
         if (KIND == 0) {
             // a pair that may touch: try to prove D_min = 0 with it
@@ -979,7 +1144,7 @@ __device__ void refine_phase(const KArgs& A, unsigned ncand, unsigned& refined, 
         }
         QState& s = A.qs[c.q];
         bool stop;
-        const float U = load_U(s, &stop);
+        const float U = load_Uq(A, c.q, &stop);
         const unsigned st = ld_relaxed(&s.status);
         // once D_min = 0 is proven only the proving pair (bound -1) is refined;
         // an evicted query is answered by its own launch later
@@ -1045,8 +1210,8 @@ __device__ void finalize_phase(const KArgs& A, unsigned ncand, unsigned long lon
 __device__ void status_phase(const KArgs& A, unsigned long long first, unsigned long long gstride) {
     for (unsigned long long q = first; q < (unsigned)A.nq; q += gstride) {
         QState& s = A.qs[q];
-        unsigned st = s.status;
-        if (s.best_key == 0xffffffffffffffffull) st |= kStatNoResult;
+        unsigned st = ld_relaxed(&s.status);
+        if (ld_relaxed64(&s.best_key) == 0xffffffffffffffffull) st |= kStatNoResult;
         gd_result& r = A.out[q];
         unsigned code = GD_OK;
         // a proven D_min = 0 stands even if some entries were lost to full
@@ -1070,7 +1235,7 @@ __device__ void status_phase(const KArgs& A, unsigned long long first, unsigned 
 // returns false if the grid barrier after them failed; *ran tells whether
 // there were any.
 __device__ bool refit_jobs(const KArgs& A, bool lead, unsigned& refits, bool* ran) {
-    unsigned jobs = ld_relaxed(A.ctr + kCtrJobs), done = ld_relaxed(A.ctr + kCtrJobsDone);
+    unsigned jobs = cta().ctr[kCtrJobs], done = cta().ctr[kCtrJobsDone];
     if (jobs > A.cap_slots) jobs = A.cap_slots;
     *ran = jobs > done;
     if (jobs <= done) return true;
@@ -1084,7 +1249,7 @@ __device__ bool refit_jobs(const KArgs& A, bool lead, unsigned& refits, bool* ra
         if (ok) refit_subtree(A, job.x, job.y, j);
         else if (threadIdx.x == 0) flag_bad(A, kBadJob);
     }
-    if (!grid_sync(A)) return false;
+    if (!sync(A)) return false;
     if (lead) {
         A.ctr[kCtrJobsDone] = jobs;
         refits = jobs;
@@ -1113,6 +1278,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
     };
 
     // phase 0
+    if (threadIdx.x == 0) cta().ready = 0;
     if (blockIdx.x == 0)
         for (int i = threadIdx.x; i < kCtrReset; i += blockDim.x) A.ctr[i] = 0u;
     for (int q = (int)gfirst; q < A.nq; q += (int)gstride) setup_query(A, q, KIND);
@@ -1129,7 +1295,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
         for (int i = 0; i < 12; ++i) S->phase_ns[i] = 0;
         for (int i = 0; i < 32; ++i) { S->level_ns[i] = 0; S->u_level[i] = 0.f; }
     }
-    if (!grid_sync(A)) goto done;
+    if (!sync(A)) goto done;
 
     // phase 1: root pairs
     for (int q = (int)gfirst; q < A.nq; q += (int)gstride) {
@@ -1150,12 +1316,12 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
             }
         }
     }
-    if (!grid_sync(A)) goto done;
+    if (!sync(A)) goto done;
     lap(0);
 
     // phase 2: BVTT levels
     for (int level = 0;; ++level) {
-        unsigned n = ld_relaxed(A.ctr + kCtrCnt + level % 3);
+        unsigned n = cta().ctr[kCtrCnt + level % 3];
         if (n > A.cap_front) n = A.cap_front;
         if (n == 0) break;
         if (level >= kMaxLevels) {
@@ -1196,11 +1362,11 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
                 probe<KIND>(A, it, V);
             }
             if (lead) A.stats->probes += P;
-            if (!grid_sync(A)) goto done;
+            if (!sync(A)) goto done;
             if (lead && !reprobe) A.stats->u_probe = __uint_as_float(ld_relaxed(&A.qs[0].U));
             lap(2);
         }
-        unsigned rmax = ld_relaxed(A.ctr + kCtrRem + level % 3);
+        unsigned rmax = cta().ctr[kCtrRem + level % 3];
         int k = adaptive_k(n, A.work_target, A.k_max);
         int s = min(2 * k, (int)rmax);
         if (s < 1) s = 1;
@@ -1217,7 +1383,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
         if (A.q_budget)  // the counters of this level's pushes are those of level + 2
             for (int q = (int)gfirst; q < A.nq; q += (int)gstride) A.qs[q].pushed[level & 1] = 0u;
         expand_level<KIND>(A, level, n, s, pairs, bytes);
-        if (!grid_sync(A)) goto done;
+        if (!sync(A)) goto done;
         if (lead) {
             unsigned long long now = globaltimer();
             if (level < 32) A.stats->level_ns[level] = (unsigned)(now - t_mark);
@@ -1228,16 +1394,16 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
         // now (every CTA reads the same count: no push happens between the
         // barrier above and the next level), so that the queue never has to
         // hold the leaf pairs of all levels at once
-        unsigned nl = ld_relaxed(A.ctr + kCtrLeaf);
+        unsigned nl = cta().ctr[kCtrLeaf];
         if (nl >= A.cap_leaf / 2) {
             if (nl > A.cap_leaf) nl = A.cap_leaf;
             leaf_phase<KIND>(A, nl, tripairs, bytes);
-            if (!grid_sync(A)) goto done;
+            if (!sync(A)) goto done;
             if (lead) {
                 A.ctr[kCtrLeaf] = 0u;
                 leaf_flushed += nl;
             }
-            if (!grid_sync(A)) goto done;
+            if (!sync(A)) goto done;
             lap(4);
         }
     }
@@ -1245,15 +1411,15 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
 
     // phase 3
     {
-        unsigned nleaf = ld_relaxed(A.ctr + kCtrLeaf);
+        unsigned nleaf = cta().ctr[kCtrLeaf];
         if (nleaf > A.cap_leaf) nleaf = A.cap_leaf;
         if (lead) A.stats->leaf_pairs = leaf_flushed + nleaf;
         leaf_phase<KIND>(A, nleaf, tripairs, bytes);
     }
-    if (!grid_sync(A)) goto done;
+    if (!sync(A)) goto done;
     lap(4);
     {
-        unsigned nc = ld_relaxed(A.ctr + kCtrCand);
+        unsigned nc = cta().ctr[kCtrCand];
         if (nc > A.cap_cand) nc = A.cap_cand;
         if (lead) A.stats->candidates = nc;
         if (nc <= gridDim.x) {
@@ -1300,13 +1466,13 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
             goto done;
         }
         refine_phase<KIND>(A, nc, refined, bytes, gfirst >> 5, gstride >> 5);
-        if (!grid_sync(A)) goto done;
+        if (!sync(A)) goto done;
         lap(5);
         select_phase(A, nc, gfirst, gstride);
-        if (!grid_sync(A)) goto done;
+        if (!sync(A)) goto done;
         lap(7);
         finalize_phase(A, nc, gfirst, gstride);
-        if (!grid_sync(A)) goto done;
+        if (!sync(A)) goto done;
         status_phase(A, gfirst, gstride);
         lap(8);
     }
