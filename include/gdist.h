@@ -95,25 +95,32 @@ typedef struct {
 /* Traversal tunables of a context.  Zero fields keep the current value. */
 typedef struct {
     int64_t work_target;   /* C of Section 6: a level expands n front entries by
-                              k levels per side with n * 4^k < C (default 2^19) */
-    int32_t k_max;         /* cap on k (default 5) */
+                              k levels per side with n * 4^k < C (default 2^18) */
+    int32_t k_max;         /* cap on k (default 6) */
     int32_t blocks_per_sm; /* persistent CTAs per SM (default: occupancy limit) */
     int64_t front_capacity;/* BVTT entries per front buffer (default 2^24) */
     int64_t leaf_capacity; /* leaf-pair queue entries (default 2^24) */
     int64_t cand_capacity; /* float64 candidate slots (default 2^22) */
-    int64_t max_capacity;  /* growth limit for the three above (default 2^28) */
+    int64_t max_capacity;  /* growth limit for the three above (default 2^30) */
     int64_t timeout_ns;    /* bound on every device-side wait (default 2e9) */
     int32_t refit_mode;    /* 1: refit B's low subtrees (2^8 leaves) into A's
                               frame when the front first reaches them (default);
                               2: never, bound B's local boxes under the map */
     int32_t refit_slots;   /* subtrees refit per launch (default 2^13) */
-    int32_t probes;        /* greedy probes per launch that seed the running
-                              bound (default 256; at least one per query) */
-    int64_t batch_budget;  /* batches of >= 2 queries: the queues are sized for
-                              this many entries per query and level (up to
-                              max_capacity); a query that pushes more than its
-                              share in one level leaves the batch and runs
-                              alone afterwards (default 2^16) */
+    int32_t probes;        /* greedy probes that seed the running bound
+                              (default 64).  Single queries: they start at the
+                              root in up to grid/8 extra CTAs (8 probes each)
+                              that run beside the traversal; batches: after
+                              the first refit, at least one per query.  A min
+                              query's repeated probes on fronts beyond 4 C use
+                              at least 256 */
+    int64_t batch_budget;  /* batches: entries one query may push per level in
+                              the first round (default 2^18); a launch takes
+                              max_capacity / (2 x share) queries; a query that
+                              pushes more than its share in one level leaves
+                              the launch and goes to the next round, whose
+                              share is 16x larger (chunks 16x smaller); a
+                              chunk of one runs alone */
 } gd_tunables;
 
 /* Counters of the last query (or batch) run on a context. */
@@ -214,9 +221,13 @@ GD_API gd_status gd_query_device(gd_ctx *ctx, const gd_mesh *A, const gd_mesh *B
  * serialise them.  Asynchronous; returns argument and launch errors only. */
 GD_API gd_status gd_query_device_noalloc(const gd_mesh *A, const gd_mesh *B, gd_kind kind, const double *d_xa,
                                          const double *d_xb, gd_result *d_out, void *stream);
-/* n independent queries (any mix of meshes and kinds) in persistent
- * launches (one per kind present), results in out[0..n).  Synchronous.
- * A query whose work exceeds the buffers is retried alone with grown buffers. */
+/* n independent queries (any mix of meshes and kinds), results in
+ * out[0..n).  Synchronous.  Each kind runs in persistent launches of chunks
+ * of queries whose fronts share the work queues (sizes: see batch_budget in
+ * gd_tunables); a query whose fronts outgrow its share leaves its launch and
+ * runs again in a later, smaller chunk, finally alone with grown buffers.
+ * Results equal those of single queries (the d = 0 witness may differ, see
+ * gd_result). */
 GD_API gd_status gd_batch_query(gd_ctx *ctx, const gd_query *q, int64_t n, gd_result *out);
 
 /* ---- serving ----------------------------------------------------------- */

@@ -189,12 +189,12 @@ unsigned batch_share(long long cap_front, long long cap_leaf, long long m) {
     return (unsigned)std::max(1ll, std::min(b, 0xffffffffll));
 }
 
-// Queues of a batch of m queries: room for batch_budget entries per query and
+// Queues of a batch of m queries: room for share entries per query and
 // level, within max_capacity (they only grow).
-gd_status size_for_batch(gd_ctx* c, long long m) {
+gd_status size_for_batch(gd_ctx* c, long long m, long long share) {
     if (m < 2) return GD_OK;
     const long long lim = std::min<long long>(c->tun.max_capacity, 0xffffffffll);
-    long long want = std::min(lim, 2 * m * std::max<long long>(1, c->tun.batch_budget));
+    long long want = std::min(lim, 2 * m * std::max<long long>(1, share));
     long long p = 1;
     while (p < want) p <<= 1;
     want = std::min(lim, p);
@@ -208,6 +208,14 @@ gd_status size_for_batch(gd_ctx* c, long long m) {
         return ensure_ws(c, m);
     }
     return GD_OK;
+}
+
+// CTAs of a single-query launch that run the traversal: the others (one per
+// 8 probes, at most 1/8 of the grid) run the greedy probes in the background.
+unsigned single_work_ctas(const gd_ctx* c, int grid) {
+    if (c->tun.probes <= 1 || grid < 16) return (unsigned)grid;
+    const int bg = std::min(grid / 8, (c->tun.probes + 7) / 8);
+    return (unsigned)(grid - bg);
 }
 
 int grid_blocks(gd_ctx* c, int kind) {
@@ -298,6 +306,7 @@ gd_status run_single(gd_ctx* ctx, const gd_mesh* A, const gd_mesh* B, int kind, 
         a.n_slot_of = (unsigned long long)tab;
         a.out = &ctx->mb_dev->out;
         int grid = grid_blocks(ctx, kind);
+        a.work_ctas = single_work_ctas(ctx, grid);
         GD_CUDA(ctx, launch_query(kind, a, grid, ctx->stream));
         GD_CUDA(ctx, cudaMemcpyAsync(ctx->mb_host, ctx->mb_dev, sizeof(Mailbox), cudaMemcpyDeviceToHost, ctx->stream));
         GD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -322,11 +331,11 @@ gd_status run_single(gd_ctx* ctx, const gd_mesh* A, const gd_mesh* B, int kind, 
 // queries that ran out of queue space to *redo, the launch's counters add to
 // *agg.
 gd_status batch_pass(gd_ctx* ctx, const gd_query* q, const std::vector<int64_t>& ids, int kind, gd_result* out,
-                     gd_stats* agg, std::vector<int64_t>* redo) {
+                     gd_stats* agg, std::vector<int64_t>* redo, long long share) {
     const long long m = (long long)ids.size();
     gd_status s = ensure_ws(ctx, m);
     if (s != GD_OK) return s;
-    s = size_for_batch(ctx, m);
+    s = size_for_batch(ctx, m, share);
     if (s != GD_OK) return s;
     long long tab = 0;
     for (long long j = 0; j < m; ++j) {
@@ -403,18 +412,18 @@ GD_API gd_status gd_ctx_create(int device, gd_ctx** out) {
         delete c;
         return GD_ERR_CUDA;
     }
-    c->tun.work_target = 1ll << 19;
-    c->tun.k_max = 5;
+    c->tun.work_target = 1ll << 18;
+    c->tun.k_max = 6;
     c->tun.blocks_per_sm = 0;
     c->tun.front_capacity = 1ll << 24;
     c->tun.leaf_capacity = 1ll << 24;
     c->tun.cand_capacity = 1ll << 22;
-    c->tun.max_capacity = 1ll << 28;
+    c->tun.max_capacity = 1ll << 30;
     c->tun.timeout_ns = 2000000000ll;
     c->tun.refit_mode = 1;
     c->tun.refit_slots = 1 << 13;
-    c->tun.probes = 256;
-    c->tun.batch_budget = 1ll << 16;
+    c->tun.probes = 64;
+    c->tun.batch_budget = 1ll << 18;
     *out = c;
     return GD_OK;
 }
@@ -637,6 +646,7 @@ GD_API gd_status gd_query_device(gd_ctx* ctx, const gd_mesh* A, const gd_mesh* B
     a.out = d_out;
     cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
     int grid = grid_blocks(ctx, (int)kind);
+    a.work_ctas = single_work_ctas(ctx, grid);
     GD_CUDA(ctx, launch_query((int)kind, a, grid, st));
     ctx->stats_pending = true;
     ctx->last_grid = grid;
@@ -662,15 +672,34 @@ GD_API gd_status gd_batch_query(gd_ctx* ctx, const gd_query* q, int64_t n, gd_re
         for (int64_t i = 0; i < n; ++i)
             if ((int)q[i].kind == kind) idx.push_back(i);
         if (idx.empty()) continue;
-        // queries evicted from the batch (or short of queue space) run alone,
-        // where the queues grow as far as one query needs
-        std::vector<int64_t> redo;
-        gd_status s = batch_pass(ctx, q, idx, kind, out, &agg, &redo);
-        if (s != GD_OK) return s;
-        for (int64_t i : redo) {
-            gd_status r = run_single(ctx, q[i].a, q[i].b, kind, q[i].xa, q[i].xb, &out[i]);
-            total_retries += 1 + ctx->last.retries;
-            if (r != GD_OK && r != GD_ERR_OVERFLOW) return r;
+        // Rounds: in round r every query may push share_r = batch_budget x
+        // 16^r entries per level, so one launch takes a chunk of
+        // max_capacity / (2 share_r) queries (the front and the leaf queue
+        // then never overflow).  Queries evicted in a round, the few with
+        // larger fronts, go to the next round in smaller chunks; a chunk of
+        // one runs alone, where the queues grow as far as that query needs.
+        const long long lim = std::min<long long>(ctx->tun.max_capacity, 0xffffffffll);
+        long long share = std::max<long long>(1, ctx->tun.batch_budget);
+        std::vector<int64_t> cur = std::move(idx);
+        while (!cur.empty()) {
+            const long long chunk = std::max<long long>(1, lim / (2 * share));
+            std::vector<int64_t> next;
+            for (size_t b = 0; b < cur.size(); b += (size_t)chunk) {
+                const size_t e = std::min(cur.size(), b + (size_t)chunk);
+                if (e - b == 1) {
+                    const int64_t i = cur[b];
+                    gd_status r = run_single(ctx, q[i].a, q[i].b, kind, q[i].xa, q[i].xb, &out[i]);
+                    total_retries += ctx->last.retries;
+                    if (r != GD_OK && r != GD_ERR_OVERFLOW) return r;
+                    continue;
+                }
+                std::vector<int64_t> part(cur.begin() + b, cur.begin() + e);
+                gd_status s = batch_pass(ctx, q, part, kind, out, &agg, &next, share);
+                if (s != GD_OK) return s;
+            }
+            total_retries += (unsigned)next.size();
+            cur = std::move(next);
+            share *= 16;
         }
     }
     agg.retries = total_retries;

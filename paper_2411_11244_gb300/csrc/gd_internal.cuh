@@ -102,6 +102,7 @@ enum : int {
     kCtrAbort = 20,   // a wait gave up: every CTA leaves at its next barrier
     kCtrLastAbort = 21, // the abort flag of the last finished launch
     kCtrExit = 22,    // CTAs that left the kernel (the last one resets the barrier)
+    kCtrSetupDone = 23, // query setup published (background probe CTAs wait for it)
     kCtrBarCount = 32,// grid-barrier arrivals of this launch (top bit: abort)
     kCtrWords = 64,
 };
@@ -154,6 +155,8 @@ struct KArgs {
     int k_max;
     long long timeout_ns;
     unsigned q_budget;          // batch: entries one query may push per level (0: no limit)
+    unsigned work_ctas;         // CTAs [0, work_ctas) run the traversal and meet at the
+                                // grid barriers; the rest run background probes (0: all)
 };
 
 // ------------------------------------------------------------------ memory
@@ -220,7 +223,7 @@ __device__ __forceinline__ bool grid_sync(const KArgs& A, F&& post) {
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned* count = A.ctr + kCtrBarCount;
-        const unsigned G = gridDim.x;
+        const unsigned G = A.work_ctas ? A.work_ctas : gridDim.x;
         const unsigned old = atom_add_release(count, 1u);
         int ok = (old & kBarAbort) == 0u;
         if (ok) {

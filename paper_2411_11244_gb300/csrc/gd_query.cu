@@ -35,6 +35,7 @@ constexpr float kU = 5.9604645e-08f;    // 2^-24, unit roundoff of float32
 constexpr float kRelW = 9.5367432e-07f; // 2^-20: world vs working-frame slack
 constexpr unsigned kFltMaxBits = 0x7f7fffffu;
 constexpr unsigned kNoSlot = 0xffffffffu, kClaimed = 0xfffffffeu;
+constexpr unsigned kReprobes = 256;
 
 // ------------------------------------------------------------- thresholds
 // All float32 bounds are made rigorous for float64 world distances:
@@ -220,6 +221,28 @@ __device__ __forceinline__ void view(const KArgs& A, unsigned q, QView& V) {
     V.q = q;
 }
 
+// CTAs that run the traversal; any others run background probes
+__device__ __forceinline__ unsigned work_ctas(const KArgs& A) { return A.work_ctas ? A.work_ctas : gridDim.x; }
+
+// Thread 0: the single query's running bound and status, and (once) its
+// constants, into the CTA state.
+__device__ __forceinline__ void cta_load_query(const KArgs& A) {
+    CtaState& c = cta();
+    const unsigned long long w = ld_relaxed64(reinterpret_cast<const unsigned long long*>(&A.qs[0].U));
+    c.U = (unsigned)w;
+    c.stat = (unsigned)(w >> 32);
+    if (!c.ready) {
+        const QState& s = A.qs[0];
+        load_qconst(s, c.v);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) c.Rl[i] = s.Rl[i];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) c.tl[i] = s.tl[i];
+        c.E_df = s.E_df;
+        c.ready = 1;
+    }
+}
+
 // Thread 0's refresh of the CTA state after a barrier.
 __device__ __forceinline__ void cta_refresh(const KArgs& A) {
     CtaState& c = cta();
@@ -228,21 +251,7 @@ __device__ __forceinline__ void cta_refresh(const KArgs& A) {
     for (int i = 0; i < kCtrReset; ++i) v[i] = ld_relaxed(A.ctr + i);
 #pragma unroll
     for (int i = 0; i < kCtrReset; ++i) c.ctr[i] = v[i];
-    if (A.nq == 1) {
-        const unsigned long long w = ld_relaxed64(reinterpret_cast<const unsigned long long*>(&A.qs[0].U));
-        c.U = (unsigned)w;
-        c.stat = (unsigned)(w >> 32);
-        if (!c.ready) {
-            const QState& s = A.qs[0];
-            load_qconst(s, c.v);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) c.Rl[i] = s.Rl[i];
-#pragma unroll
-            for (int i = 0; i < 3; ++i) c.tl[i] = s.tl[i];
-            c.E_df = s.E_df;
-            c.ready = 1;
-        }
-    }
+    if (A.nq == 1) cta_load_query(A);
     c.cnt[0][0] = c.cnt[0][1] = c.cnt[1][0] = c.cnt[1][1] = 0u;
     c.rem = 0u;
 }
@@ -657,9 +666,13 @@ __device__ void refit_subtree(const KArgs& A, unsigned q, unsigned root, unsigne
 
 // ------------------------------------------------------------- probes
 
+// One compiled copy (not inlined): every caller (the refinement's grid and
+// tail paths, the D = 0 proof) gets bit-identical float64 results for a pair,
+// whatever multiply-adds the compiler would contract into FMAs in an inlined
+// copy.
 template <int KIND>
-__device__ __forceinline__ double refine_pair_warp(const QState& s, unsigned ta, unsigned tb, V3<double>* P,
-                                                   V3<double>* Q, int* ida, int* idb);
+__device__ __noinline__ double refine_pair_warp(const QState& s, unsigned ta, unsigned tb, V3<double>* P,
+                                                V3<double>* Q, int* ida, int* idb);
 
 // Proof of D_min = 0 (min kind), run by a whole warp on one pair (ta, tb) of
 // query q whose float32 lower bound is 0: the float64 distance of the pair,
@@ -668,7 +681,7 @@ __device__ __forceinline__ double refine_pair_warp(const QState& s, unsigned ta,
 // enters the candidates with bound -1, the only mark the refinement keeps once
 // kStatZero is set.  A query starts at most kCertMax checks per launch, so
 // touching but disjoint pairs cannot make the proof attempts dominate.
-__device__ void certify_zero(const KArgs& A, unsigned q, unsigned ta, unsigned tb) {
+__device__ __noinline__ void certify_zero(const KArgs& A, unsigned q, unsigned ta, unsigned tb) {
     QState& s = A.qs[q];
     const int lane = threadIdx.x & 31;
     unsigned go = 0;
@@ -711,7 +724,8 @@ __device__ void probe(const KArgs& A, Item it, const QView& V) {
         const unsigned ia = (a << kA) | ((unsigned)lane >> kB);
         const unsigned ib = (b << kB) | ((unsigned)lane & ((1u << kB) - 1u));
         bool stop;
-        const float Ucur = load_Uq(A, q, &stop);
+        // a background probe CTA meets no barrier: it reads the global bound
+        const float Ucur = blockIdx.x >= work_ctas(A) ? load_U(A.qs[q], &stop) : load_Uq(A, q, &stop);
         if (__any_sync(kFull, stop)) return;
         bool ok = false;
         unsigned newU = KIND == 0 ? 0xffffffffu : 0u, key = 0xffffffffu;
@@ -739,6 +753,85 @@ __device__ void probe(const KArgs& A, Item it, const QView& V) {
             certify_zero(A, q, __shfl_sync(kFull, ta, src), __shfl_sync(kFull, tb, src));
         }
     }
+}
+
+// A probe that starts at the root pair.  Its first two steps take the
+// descendant pair of rank w mod 32 and then (w / 32) mod 32 among the
+// survivors (ordered by their enhanced bound), so that the walks of different
+// warps start in different subtree pairs; then it walks greedily as probe().
+template <int KIND>
+__device__ void probe_root(const KArgs& A, unsigned w, const QView& V) {
+    const int lane = threadIdx.x & 31;
+    unsigned a = 1u, b = 1u;
+    for (int step = 0; step < 2; ++step) {
+        const int remA = V.LA - depth_of(a), remB = V.LB - depth_of(b);
+        if (remA == 0 && remB == 0) break;
+        int kA = min(remA, 3);
+        const int kB = min(remB, 5 - kA);
+        kA = min(remA, 5 - kB);
+        const bool valid = lane < (1 << (kA + kB));
+        const unsigned ia = (a << kA) | ((unsigned)lane >> kB);
+        const unsigned ib = (b << kB) | ((unsigned)lane & ((1u << kB) - 1u));
+        bool stop;
+        const float Ucur = load_U(A.qs[0], &stop);
+        if (__any_sync(kFull, stop)) return;
+        bool ok = false;
+        unsigned newU = KIND == 0 ? 0xffffffffu : 0u, key = 0xffffffffu;
+        if (valid) pair_bounds<KIND>(A, V, ia, ib, depth_of(b) + kB, Ucur, &ok, &newU, &key);
+        warp_bound_update<KIND>(A, ok, 0u, newU);
+        const unsigned okm = __ballot_sync(kFull, ok);
+        const unsigned nsurv = __popc(okm);
+        if (nsurv == 0) return;
+        unsigned rank = 0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const unsigned kj = __shfl_sync(kFull, key, j);
+            rank += ((okm >> j) & 1u) && (kj < key || (kj == key && j < lane));
+        }
+        const unsigned want = (step == 0 ? w : w / 32u) % nsurv;
+        const unsigned m = __ballot_sync(kFull, ok && rank == want);
+        const int src = m ? __ffs(m) - 1 : __ffs(okm) - 1;
+        a = __shfl_sync(kFull, ia, src);
+        b = __shfl_sync(kFull, ib, src);
+    }
+    probe<KIND>(A, Item{a, b, 0.f, 0u}, V);
+}
+
+// A background probe CTA of a single-query launch: it waits (bounded) until
+// the query's setup is published, then every warp walks one probe_root from
+// the root while the traversal CTAs run their levels; the probes only lower
+// the global running bound (and may prove D_min = 0), which the traversal
+// reads at its next barrier.  The probes do not use refit boxes: those are
+// being written while the probes run.
+template <int KIND>
+__device__ void bg_probe_cta(const KArgs& A) {
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned long long t0 = globaltimer();
+        while (!ld_acquire(A.ctr + kCtrSetupDone)) {
+            if (ld_relaxed(A.ctr + kCtrAbort)) { ok = 0; break; }
+            if ((long long)(globaltimer() - t0) > A.timeout_ns) {
+                raise_abort(A);
+                ok = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+        if (ok) {
+            cta().ready = 0;
+            cta_load_query(A);
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    QView V;
+    view(A, 0u, V);
+    V.dR = -1;
+    const unsigned w = (blockIdx.x - work_ctas(A)) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    probe_root<KIND>(A, w, V);
+    if (threadIdx.x == 0) atomicAdd(&A.stats->probes, blockDim.x >> 5);
 }
 
 // ------------------------------------------------------------- phase 0
@@ -833,7 +926,7 @@ __device__ void expand_level(const KArgs& A, int level, unsigned n, int s, unsig
     unsigned* out_rem = A.ctr + kCtrRem + (level + 1) % 3;
     unsigned* leaf_cnt = A.ctr + kCtrLeaf;
     const unsigned long long total = (unsigned long long)n << s;
-    const unsigned long long gstride = (unsigned long long)gridDim.x * blockDim.x;
+    const unsigned long long gstride = (unsigned long long)work_ctas(A) * blockDim.x;
     const unsigned long long mask = (1ull << s) - 1;
     const int lane = threadIdx.x & 31;
     QView V;
@@ -928,8 +1021,7 @@ __device__ void expand_level(const KArgs& A, int level, unsigned n, int s, unsig
 template <int KIND>
 __device__ void leaf_phase(const KArgs& A, unsigned nleaf, unsigned& tripairs, unsigned long long& bytes) {
     const unsigned long long total = (unsigned long long)nleaf * 4ull;
-    const unsigned long long gstride = (unsigned long long)gridDim.x * blockDim.x;
-    const int lane = threadIdx.x & 31;
+    const unsigned long long gstride = (unsigned long long)work_ctas(A) * blockDim.x;
     unsigned* cand_cnt = A.ctr + kCtrCand;
     QView V;
     int iter = 0;
@@ -1019,8 +1111,8 @@ __device__ void leaf_phase(const KArgs& A, unsigned nleaf, unsigned& tripairs, u
 // vertex pair.  Every lane returns the warp's result; P, Q are a closest
 // (farthest) pair, *ida, *idb the original triangle indices.
 template <int KIND>
-__device__ __forceinline__ double refine_pair_warp(const QState& s, unsigned ta, unsigned tb, V3<double>* P,
-                                                   V3<double>* Q, int* ida, int* idb) {
+__device__ __noinline__ double refine_pair_warp(const QState& s, unsigned ta, unsigned tb, V3<double>* P,
+                                                V3<double>* Q, int* ida, int* idb) {
     const int lane = threadIdx.x & 31;
     Tri32 TA = load_tri(s.A->tri, ta), TB = load_tri(s.B->tri, tb);
     *ida = TA.id;
@@ -1239,7 +1331,7 @@ __device__ bool refit_jobs(const KArgs& A, bool lead, unsigned& refits, bool* ra
     if (jobs > A.cap_slots) jobs = A.cap_slots;
     *ran = jobs > done;
     if (jobs <= done) return true;
-    for (unsigned j = done + blockIdx.x; j < jobs; j += gridDim.x) {
+    for (unsigned j = done + blockIdx.x; j < jobs; j += work_ctas(A)) {
         uint2 job = __ldcg(A.jobs + j);
         bool ok = job.x < (unsigned)A.nq && job.y >= 1u;
         if (ok) {
@@ -1264,10 +1356,11 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
     unsigned long long pairs = 0, bytes = 0;
     unsigned tripairs = 0, refined = 0, refits = 0;
     unsigned leaf_flushed = 0;
-    bool probed = false;
+    bool probed = false;  // set below once the first probes ran (or run in the background)
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
     const unsigned long long gfirst = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const unsigned long long gstride = (unsigned long long)gridDim.x * blockDim.x;
+    const unsigned W = work_ctas(A);
+    const unsigned long long gstride = (unsigned long long)W * blockDim.x;
     unsigned long long t_start = globaltimer(), t_mark = t_start, t_levels = 0;
     auto lap = [&](int slot) {
         if (lead) {
@@ -1276,6 +1369,11 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
             t_mark = now;
         }
     };
+
+    if (blockIdx.x >= W) {
+        bg_probe_cta<KIND>(A);
+        goto done;
+    }
 
     // phase 0
     if (threadIdx.x == 0) cta().ready = 0;
@@ -1294,6 +1392,14 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
         S->u_probe = 0.f;
         for (int i = 0; i < 12; ++i) S->phase_ns[i] = 0;
         for (int i = 0; i < 32; ++i) { S->level_ns[i] = 0; S->u_level[i] = 0.f; }
+    }
+    if (W < gridDim.x && blockIdx.x == 0) {
+        // publish the (single) query's setup to the background probe CTAs
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicExch(A.ctr + kCtrSetupDone, 1u);
+        }
     }
     if (!sync(A)) goto done;
 
@@ -1320,6 +1426,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
     lap(0);
 
     // phase 2: BVTT levels
+    if (W < gridDim.x) probed = true;
     for (int level = 0;; ++level) {
         unsigned n = cta().ctr[kCtrCnt + level % 3];
         if (n > A.cap_front) n = A.cap_front;
@@ -1341,9 +1448,12 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
             probed = true;
             // greedy probes from entries spread evenly over the front: every
             // warp takes one (at least one per query when the grid allows)
-            const unsigned nwarps = gridDim.x * (blockDim.x >> 5);
+            const unsigned nwarps = W * (blockDim.x >> 5);
             const unsigned wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-            const unsigned P = min(n, min(nwarps, max((unsigned)A.nq, (unsigned)A.probes)));
+            // (a min query's repeated probes on large fronts use at least
+            // kReprobes walks, enough to meet an intersection if there is one)
+            const unsigned want = max((unsigned)A.nq, reprobe ? max((unsigned)A.probes, kReprobes) : (unsigned)A.probes);
+            const unsigned P = min(n, min(nwarps, want));
             const Item* in = (level & 1) ? A.front1 : A.front0;
             QView V;
             for (unsigned p = wid; p < P; p += nwarps) {
@@ -1422,11 +1532,11 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
         unsigned nc = cta().ctr[kCtrCand];
         if (nc > A.cap_cand) nc = A.cap_cand;
         if (lead) A.stats->candidates = nc;
-        if (nc <= gridDim.x) {
+        if (nc <= W) {
             // few candidates: one per CTA (its warp 0), spread over the SMs'
             // float64 pipes; CTA 0 waits for the others (bounded) and then
             // selects the witness alone, so no grid-wide barrier is needed
-            if (threadIdx.x < 32) refine_phase<KIND>(A, nc, refined, bytes, blockIdx.x, gridDim.x);
+            if (threadIdx.x < 32) refine_phase<KIND>(A, nc, refined, bytes, blockIdx.x, W);
             __syncthreads();
             lap(5);
             if (threadIdx.x == 0 && blockIdx.x < nc) {
@@ -1506,6 +1616,7 @@ done:
                 unsigned ab = atomicExch(A.ctr + kCtrAbort, 0u);
                 atomicExch(A.ctr + kCtrLastAbort, ab);
                 atomicExch(A.ctr + kCtrBarCount, 0u);
+                atomicExch(A.ctr + kCtrSetupDone, 0u);
                 atomicExch(A.ctr + kCtrExit, 0u);
                 __threadfence();
             }

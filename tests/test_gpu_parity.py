@@ -384,7 +384,8 @@ def test_zero_proof_stops_traversal(G, oracle_mod):
         A = synth.torus(1.0, 0.25, 64, 32)
         x = _rigid(rng, 0.5)
         ma, mb = _mesh(G, c, A), _mesh(G, c, A)
-        G.gd_ctx_set_tunables(c, front_capacity=64, leaf_capacity=64, cand_capacity=16, max_capacity=128)
+        G.gd_ctx_set_tunables(c, front_capacity=64, leaf_capacity=64, cand_capacity=16, max_capacity=128,
+                              probes=64)
         r = G.gd_min_distance(c, ma, mb, x, x)
         assert r.status == 0 and r.d == 0.0 and r.flags == 3, (r.status, r.d, r.flags)
         dw, _, _ = oracle_mod.witness_distance(A, x, A, x, r.tri_a, r.tri_b, "min")
