@@ -19,25 +19,41 @@ template <class T>
 __device__ __forceinline__ V3<T> mk3(T x, T y, T z) {
     return V3<T>{x, y, z};
 }
+
+// Scalar arithmetic of the geometry.  float32: plain operators (the compiler
+// may contract them into FMAs; every float32 result is only used inside
+// bounds widened for such rounding).  float64: explicitly rounded
+// intrinsics, never contracted, so that the float64 value of a feature is
+// the same bits in every inlined copy and on every code path.
+template <class T> __device__ __forceinline__ T sadd(T a, T b) { return a + b; }
+template <class T> __device__ __forceinline__ T ssub(T a, T b) { return a - b; }
+template <class T> __device__ __forceinline__ T smul(T a, T b) { return a * b; }
+template <class T> __device__ __forceinline__ T sdiv(T a, T b) { return a / b; }
+template <> __device__ __forceinline__ double sadd(double a, double b) { return __dadd_rn(a, b); }
+template <> __device__ __forceinline__ double ssub(double a, double b) { return __dsub_rn(a, b); }
+template <> __device__ __forceinline__ double smul(double a, double b) { return __dmul_rn(a, b); }
+template <> __device__ __forceinline__ double sdiv(double a, double b) { return __ddiv_rn(a, b); }
+
 template <class T>
 __device__ __forceinline__ V3<T> operator+(V3<T> a, V3<T> b) {
-    return mk3(a.x + b.x, a.y + b.y, a.z + b.z);
+    return mk3(sadd(a.x, b.x), sadd(a.y, b.y), sadd(a.z, b.z));
 }
 template <class T>
 __device__ __forceinline__ V3<T> operator-(V3<T> a, V3<T> b) {
-    return mk3(a.x - b.x, a.y - b.y, a.z - b.z);
+    return mk3(ssub(a.x, b.x), ssub(a.y, b.y), ssub(a.z, b.z));
 }
 template <class T>
 __device__ __forceinline__ V3<T> operator*(V3<T> a, T s) {
-    return mk3(a.x * s, a.y * s, a.z * s);
+    return mk3(smul(a.x, s), smul(a.y, s), smul(a.z, s));
 }
 template <class T>
 __device__ __forceinline__ T dot(V3<T> a, V3<T> b) {
-    return a.x * b.x + a.y * b.y + a.z * b.z;
+    return sadd(sadd(smul(a.x, b.x), smul(a.y, b.y)), smul(a.z, b.z));
 }
 template <class T>
 __device__ __forceinline__ V3<T> cross(V3<T> a, V3<T> b) {
-    return mk3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+    return mk3(ssub(smul(a.y, b.z), smul(a.z, b.y)), ssub(smul(a.z, b.x), smul(a.x, b.z)),
+               ssub(smul(a.x, b.y), smul(a.y, b.x)));
 }
 template <class T>
 __device__ __forceinline__ T clamp01(T s) {
@@ -49,7 +65,7 @@ template <class T>
 __device__ __forceinline__ V3<T> closest_on_segment(V3<T> p, V3<T> a, V3<T> d) {
     T dd = dot(d, d);
     T s = T(0);
-    if (dd > T(0)) s = clamp01(dot(p - a, d) / dd);
+    if (dd > T(0)) s = clamp01(sdiv(dot(p - a, d), dd));
     return a + d * s;
 }
 
@@ -73,12 +89,12 @@ template <class T>
 __device__ __forceinline__ V3<T> closest_on_triangle(V3<T> p, V3<T> a, V3<T> b, V3<T> c, bool* inside) {
     V3<T> e0 = b - a, e1 = c - a, w = p - a;
     T g00 = dot(e0, e0), g01 = dot(e0, e1), g11 = dot(e1, e1);
-    T det = g00 * g11 - g01 * g01;
-    if (det > Tiny<T>::rel_det * g00 * g11 && det > T(0)) {
+    T det = ssub(smul(g00, g11), smul(g01, g01));
+    if (det > smul(smul(Tiny<T>::rel_det, g00), g11) && det > T(0)) {
         T r0 = dot(w, e0), r1 = dot(w, e1);
-        T u = (g11 * r0 - g01 * r1) / det;
-        T v = (g00 * r1 - g01 * r0) / det;
-        if (u >= T(0) && v >= T(0) && u + v <= T(1)) {
+        T u = sdiv(ssub(smul(g11, r0), smul(g01, r1)), det);
+        T v = sdiv(ssub(smul(g00, r1), smul(g01, r0)), det);
+        if (u >= T(0) && v >= T(0) && sadd(u, v) <= T(1)) {
             *inside = true;
             return a + e0 * u + e1 * v;
         }
@@ -110,25 +126,25 @@ __device__ __forceinline__ void closest_segment_segment(V3<T> p0, V3<T> d1, V3<T
         s = t = T(0);
     } else if (!(a > T(0))) {
         s = T(0);
-        t = clamp01(f / e);
+        t = clamp01(sdiv(f, e));
     } else {
         T c = dot(d1, r);
         if (!(e > T(0))) {
             t = T(0);
-            s = clamp01(-c / a);
+            s = clamp01(sdiv(-c, a));
         } else {
             T b = dot(d1, d2);
-            T den = a * e - b * b;
-            s = den > T(0) ? clamp01((b * f - c * e) / den) : T(0);
-            T tn = b * s + f;
+            T den = ssub(smul(a, e), smul(b, b));
+            s = den > T(0) ? clamp01(sdiv(ssub(smul(b, f), smul(c, e)), den)) : T(0);
+            T tn = sadd(smul(b, s), f);
             if (tn < T(0)) {
                 t = T(0);
-                s = clamp01(-c / a);
+                s = clamp01(sdiv(-c, a));
             } else if (tn > e) {
                 t = T(1);
-                s = clamp01((b - c) / a);
+                s = clamp01(sdiv(ssub(b, c), a));
             } else {
-                t = tn / e;
+                t = sdiv(tn, e);
             }
         }
     }
@@ -244,9 +260,9 @@ __device__ __forceinline__ void tri_feature(int f, const V3<T>* A, const V3<T>* 
         const V3<T> f0 = ea ? B[0] : A[0], f1 = ea ? B[1] : A[1], f2 = ea ? B[2] : A[2];
         V3<T> n = cross(f1 - f0, f2 - f0);
         T si = dot(n, e0 - f0), sj = dot(n, e1 - f0);
-        have = ((si <= T(0) && sj >= T(0)) || (si >= T(0) && sj <= T(0))) && (si - sj) != T(0);
+        have = ((si <= T(0) && sj >= T(0)) || (si >= T(0) && sj <= T(0))) && ssub(si, sj) != T(0);
         if (have) {
-            V3<T> X = e0 + (e1 - e0) * clamp01(si / (si - sj));
+            V3<T> X = e0 + (e1 - e0) * clamp01(sdiv(si, ssub(si, sj)));
             V3<T> Y = closest_on_triangle(X, f0, f1, f2, &in);
             if (ea) { *P = X; *Q = Y; } else { *P = Y; *Q = X; }
             if (in) { *hit = true; *P = X; *Q = X; }

@@ -98,6 +98,7 @@ enum : int {
     kCtrJobsDone = 11,// refit jobs already run
     kCtrTailDone = 12,// CTAs done with their candidate in the one-per-CTA tail
     kCtrBadIndex = 13,// an index check failed (bit per site); the access was skipped
+    kCtrRefined = 14, // candidates refined in float64 (their indices are listed)
     kCtrReset = 16,   // counters [0, kCtrReset) are cleared at kernel start
     kCtrAbort = 20,   // a wait gave up: every CTA leaves at its next barrier
     kCtrLastAbort = 21, // the abort flag of the last finished launch

@@ -1219,50 +1219,175 @@ __device__ __noinline__ double refine_pair_warp(const QState& s, unsigned ta, un
 }
 
 // float64 refinement, one warp per candidate (warps first_warp, +wstride, ...)
+// float64 distance of one triangle pair computed by three warps of a CTA, one
+// per kind of feature pair: warp 0 the 9 edge-edge pairs, warp 1 the 6
+// vertex-face pairs, warp 2 the 6 edge-plane crossings (max kind: warp 0, the
+// 9 vertex pairs).  All features run in float64 at once, so the three kinds
+// do not wait for one another as they do in one warp, and no float32 pass is
+// needed.  The per-feature arithmetic is the explicitly rounded float64 of
+// tri_feature and the winner is the same (hit first, else the smallest
+// (d2, feature)), so the result equals refine_pair_warp's bit for bit.  Every
+// thread of the CTA calls it; the result is valid on every thread.
 template <int KIND>
-__device__ void refine_phase(const KArgs& A, unsigned ncand, unsigned& refined, unsigned long long& bytes,
-                             unsigned long long first_warp, unsigned long long wstride) {
-    const int lane = threadIdx.x & 31;
-    for (unsigned long long i = first_warp; i < ncand; i += wstride) {
-        float4 raw = __ldcg(reinterpret_cast<const float4*>(A.cand + i));
-        Cand c = *reinterpret_cast<Cand*>(&raw);
-        if (c.q >= (unsigned)A.nq || c.ta >= (unsigned)A.qs[c.q < (unsigned)A.nq ? c.q : 0].A->T ||
-            c.tb >= (unsigned)A.qs[c.q < (unsigned)A.nq ? c.q : 0].B->T) {
-            if (lane == 0) {
-                flag_bad(A, kBadCand);
-                A.cand_d[i] = __longlong_as_double(-1ll);
-            }
-            continue;
+__device__ double refine_pair_cta(const QState& s, unsigned ta, unsigned tb, V3<double>* P, V3<double>* Q, int* ida,
+                                  int* idb) {
+    __shared__ double s_d2[3];
+    __shared__ int s_f[3];
+    __shared__ double s_pq[3][6];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    Tri32 TA = load_tri(s.A->tri, ta), TB = load_tri(s.B->tri, tb);
+    *ida = TA.id;
+    *idb = TB.id;
+    __syncthreads();  // the shared results of a previous pair have been read
+    if (warp < 3) {
+        V3<double> w = mk3(0.0, 0.0, 0.0);
+        if (lane < 3) w = map64(s.xa, (double)TA.v[lane].x, (double)TA.v[lane].y, (double)TA.v[lane].z);
+        else if (lane < 6)
+            w = map64(s.xb, (double)TB.v[lane - 3].x, (double)TB.v[lane - 3].y, (double)TB.v[lane - 3].z);
+        V3<double> Aw[3], Bw[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            Aw[k] = mk3(__shfl_sync(kFull, w.x, k), __shfl_sync(kFull, w.y, k), __shfl_sync(kFull, w.z, k));
+            Bw[k] = mk3(__shfl_sync(kFull, w.x, 3 + k), __shfl_sync(kFull, w.y, 3 + k),
+                        __shfl_sync(kFull, w.z, 3 + k));
         }
-        QState& s = A.qs[c.q];
-        bool stop;
-        const float U = load_Uq(A, c.q, &stop);
-        const unsigned st = ld_relaxed(&s.status);
-        // once D_min = 0 is proven only the proving pair (bound -1) is refined;
-        // an evicted query is answered by its own launch later
-        bool keep = KIND == 0 ? (stop ? (st & kStatZero) && c.bound < 0.f : c.bound <= U)
-                              : (!stop && c.bound >= U);
-        double d = __longlong_as_double(-1ll);  // NaN: never selected
-        if (keep) {
+        V3<double> p = Aw[0], qq = Bw[0];
+        double d2 = INFINITY;
+        bool hit = false;
+        int f = 99;
+        if (KIND == 0) {
+            const bool on = warp == 0 ? lane < 9 : lane < 6;
+            f = warp == 0 ? lane : (warp == 1 ? 9 + lane : 15 + lane);
+            if (on) tri_feature(f, Aw, Bw, &p, &qq, &d2, &hit);
+            else f = 99;
+        } else if (warp == 0 && lane < 9) {
+            p = Aw[lane / 3];
+            qq = Bw[lane % 3];
+            const V3<double> d = p - qq;
+            d2 = -dot(d, d);  // reduce with min
+            f = lane;
+        }
+        const unsigned hits = __ballot_sync(kFull, hit);
+        double best;
+        int win;
+        if (hits) {
+            win = __ffs(hits) - 1;
+            best = -1.0;  // marks a hit
+        } else {
+            best = d2;
+            win = lane;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_xor_sync(kFull, best, o);
+                const int ow = __shfl_xor_sync(kFull, win, o);
+                if (ob < best || (ob == best && ow < win)) { best = ob; win = ow; }
+            }
+        }
+        const double px = __shfl_sync(kFull, p.x, win), py = __shfl_sync(kFull, p.y, win),
+                     pz = __shfl_sync(kFull, p.z, win), qx = __shfl_sync(kFull, qq.x, win),
+                     qy = __shfl_sync(kFull, qq.y, win), qz = __shfl_sync(kFull, qq.z, win);
+        const int fw = __shfl_sync(kFull, f, win);
+        if (lane == 0) {
+            s_d2[warp] = (KIND == 0 && hits) ? -1.0 : best;
+            s_f[warp] = fw;
+            s_pq[warp][0] = px; s_pq[warp][1] = py; s_pq[warp][2] = pz;
+            s_pq[warp][3] = qx; s_pq[warp][4] = qy; s_pq[warp][5] = qz;
+        }
+    }
+    __syncthreads();
+    // min kind: a hit (-1) wins, the smallest feature index first; otherwise
+    // the smallest (d2, feature).  Max kind: the values are -d2.
+    int bw = 0;
+    for (int k = 1; k < 3; ++k) {
+        const bool better = s_d2[k] < s_d2[bw] || (s_d2[k] == s_d2[bw] && s_f[k] < s_f[bw]);
+        if (better) bw = k;
+    }
+    const double best = s_d2[bw];
+    P->x = s_pq[bw][0]; P->y = s_pq[bw][1]; P->z = s_pq[bw][2];
+    Q->x = s_pq[bw][3]; Q->y = s_pq[bw][4]; Q->z = s_pq[bw][5];
+    if (KIND == 0) return best < 0.0 ? 0.0 : sqrt(best);
+    return sqrt(-best);
+}
+
+// The refinement by CTAs: thread t of CTA c tests candidate c + t W (+ 256 W
+// per round) against the running bound, the kept ones are listed in shared
+// memory, and the CTA refines them one after another with refine_pair_cta.
+// Every candidate's float64 distance (NaN when not kept) and points are
+// stored, the per-query extreme is raised or lowered, and the refined
+// candidates are listed for the selection.
+template <int KIND>
+__device__ void refine_phase_cta(const KArgs& A, unsigned ncand, unsigned& refined, unsigned long long& bytes) {
+    __shared__ unsigned s_list[kBlock];
+    __shared__ unsigned s_n;
+    const unsigned long long W = work_ctas(A);
+    for (unsigned long long base = blockIdx.x; base < ncand; base += W * blockDim.x) {
+        if (threadIdx.x == 0) s_n = 0u;
+        __syncthreads();
+        const unsigned long long i = base + (unsigned long long)threadIdx.x * W;
+        if (i < ncand) {
+            float4 raw = __ldcg(reinterpret_cast<const float4*>(A.cand + i));
+            const Cand c = *reinterpret_cast<Cand*>(&raw);
+            bool keep = false;
+            if (c.q >= (unsigned)A.nq || c.ta >= (unsigned)A.qs[c.q < (unsigned)A.nq ? c.q : 0].A->T ||
+                c.tb >= (unsigned)A.qs[c.q < (unsigned)A.nq ? c.q : 0].B->T) {
+                flag_bad(A, kBadCand);
+            } else {
+                bool stop;
+                const float U = load_Uq(A, c.q, &stop);
+                const unsigned st = ld_relaxed(&A.qs[c.q].status);
+                // once D_min = 0 is proven only the proving pair (bound -1) is
+                // refined; an evicted query is answered by its own launch later
+                keep = KIND == 0 ? (stop ? (st & kStatZero) && c.bound < 0.f : c.bound <= U)
+                                 : (!stop && c.bound >= U);
+            }
+            if (keep) s_list[atomicAdd(&s_n, 1u)] = (unsigned)i;
+            else A.cand_d[i] = __longlong_as_double(-1ll);  // NaN: never selected
+        }
+        __syncthreads();
+        const unsigned n = s_n;
+        for (unsigned k = 0; k < n; ++k) {
+            const unsigned ci = s_list[k];
+            float4 raw = __ldcg(reinterpret_cast<const float4*>(A.cand + ci));
+            const Cand c = *reinterpret_cast<Cand*>(&raw);
+            QState& s = A.qs[c.q];
             V3<double> P, Q;
             int ia, ib;
-            d = refine_pair_warp<KIND>(s, c.ta, c.tb, &P, &Q, &ia, &ib);
-            if (lane == 0) {
-                double* w = A.cand_pts + 6ull * i;
+            const double d = refine_pair_cta<KIND>(s, c.ta, c.tb, &P, &Q, &ia, &ib);
+            if (threadIdx.x == 0) {
+                double* w = A.cand_pts + 6ull * ci;
                 w[0] = P.x; w[1] = P.y; w[2] = P.z; w[3] = Q.x; w[4] = Q.y; w[5] = Q.z;
-                unsigned long long bits = (unsigned long long)__double_as_longlong(d);
+                const unsigned r = atomicAdd(A.ctr + kCtrRefined, 1u);
+                if (r < 4ull * A.cap_leaf) reinterpret_cast<unsigned*>(A.leafq)[r] = ci;
+                const unsigned long long bits = (unsigned long long)__double_as_longlong(d);
                 if (KIND == 0) atomicMin(&s.best_d, bits);
                 else atomicMax(&s.best_d, bits);
+                A.cand_d[ci] = d;
                 ++refined;
                 bytes += 16ull + 72ull;
             }
         }
-        if (lane == 0) A.cand_d[i] = d;
+        __syncthreads();
     }
 }
 
-__device__ void select_phase(const KArgs& A, unsigned ncand, unsigned long long first, unsigned long long gstride) {
-    for (unsigned long long i = first; i < ncand; i += gstride) {
+// The candidates to scan after the refinement: the list of refined ones when
+// it is complete, else all ncand.
+struct RefinedSet {
+    const unsigned* list;
+    unsigned n;
+    __device__ __forceinline__ unsigned at(unsigned k) const { return list ? __ldcg(list + k) : k; }
+};
+
+__device__ __forceinline__ RefinedSet refined_set(const KArgs& A, unsigned nrefined, unsigned ncand) {
+    if ((unsigned long long)nrefined <= 4ull * A.cap_leaf)
+        return RefinedSet{reinterpret_cast<const unsigned*>(A.leafq), nrefined};
+    return RefinedSet{nullptr, ncand};
+}
+
+__device__ void select_phase(const KArgs& A, RefinedSet R, unsigned long long first, unsigned long long gstride) {
+    for (unsigned long long k = first; k < R.n; k += gstride) {
+        const unsigned i = R.at((unsigned)k);
+        if (i >= A.cap_cand) continue;
         double d = __ldcg(A.cand_d + i);
         float4 raw = __ldcg(reinterpret_cast<const float4*>(A.cand + i));
         Cand c = *reinterpret_cast<Cand*>(&raw);
@@ -1278,8 +1403,10 @@ __device__ void select_phase(const KArgs& A, unsigned ncand, unsigned long long 
 
 // the witness record of each query: the candidate at the extreme with the
 // smallest original (tri_a, tri_b); its points were stored by the refinement
-__device__ void finalize_phase(const KArgs& A, unsigned ncand, unsigned long long first, unsigned long long gstride) {
-    for (unsigned long long i = first; i < ncand; i += gstride) {
+__device__ void finalize_phase(const KArgs& A, RefinedSet R, unsigned long long first, unsigned long long gstride) {
+    for (unsigned long long k = first; k < R.n; k += gstride) {
+        const unsigned i = R.at((unsigned)k);
+        if (i >= A.cap_cand) continue;
         double d = __ldcg(A.cand_d + i);
         float4 raw = __ldcg(reinterpret_cast<const float4*>(A.cand + i));
         Cand c = *reinterpret_cast<Cand*>(&raw);
@@ -1536,7 +1663,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
             // few candidates: one per CTA (its warp 0), spread over the SMs'
             // float64 pipes; CTA 0 waits for the others (bounded) and then
             // selects the witness alone, so no grid-wide barrier is needed
-            if (threadIdx.x < 32) refine_phase<KIND>(A, nc, refined, bytes, blockIdx.x, W);
+            refine_phase_cta<KIND>(A, nc, refined, bytes);
             __syncthreads();
             lap(5);
             if (threadIdx.x == 0 && blockIdx.x < nc) {
@@ -1563,10 +1690,11 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
                 __syncthreads();
                 if (s_go) {
                     lap(6);
-                    select_phase(A, nc, threadIdx.x, blockDim.x);
+                    const RefinedSet R{nullptr, nc};
+                    select_phase(A, R, threadIdx.x, blockDim.x);
                     __syncthreads();
                     lap(7);
-                    finalize_phase(A, nc, threadIdx.x, blockDim.x);
+                    finalize_phase(A, R, threadIdx.x, blockDim.x);
                     __syncthreads();
                     status_phase(A, threadIdx.x, blockDim.x);
                     __syncthreads();
@@ -1575,13 +1703,28 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
             }
             goto done;
         }
-        refine_phase<KIND>(A, nc, refined, bytes, gfirst >> 5, gstride >> 5);
+        refine_phase_cta<KIND>(A, nc, refined, bytes);
         if (!sync(A)) goto done;
         lap(5);
-        select_phase(A, nc, gfirst, gstride);
+        const RefinedSet R = refined_set(A, cta().ctr[kCtrRefined], nc);
+        if (A.nq == 1) {
+            // one query: CTA 0 selects and writes the witness alone (the refined
+            // candidates are few), no further grid barrier
+            if (blockIdx.x == 0) {
+                select_phase(A, R, threadIdx.x, blockDim.x);
+                __syncthreads();
+                lap(7);
+                finalize_phase(A, R, threadIdx.x, blockDim.x);
+                __syncthreads();
+                status_phase(A, threadIdx.x, blockDim.x);
+                lap(8);
+            }
+            goto done;
+        }
+        select_phase(A, R, gfirst, gstride);
         if (!sync(A)) goto done;
         lap(7);
-        finalize_phase(A, nc, gfirst, gstride);
+        finalize_phase(A, R, gfirst, gstride);
         if (!sync(A)) goto done;
         status_phase(A, gfirst, gstride);
         lap(8);
