@@ -41,6 +41,25 @@ METRIC = "ms/query at 2x7.5M tris; batched queries/s + p50/p99 vs plain path"
 WORKLOAD = "rings: 2 tori R=1 r=0.05, 2500x1500 quads = 7.5M tris each, gap 1e-3, B spun per frame"
 
 
+KERNEL_SOURCES = ("paper_2411_11244_gb300/csrc/gd_query.cu", "paper_2411_11244_gb300/csrc/gd_geom.cuh",
+                  "paper_2411_11244_gb300/csrc/gd_internal.cuh")
+
+
+def _traffic():
+    """DRAM bytes per query launch from the committed ncu summary, or None when
+    the query kernel's sources changed since that capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_query_min_rings_traffic.json")
+    try:
+        rec = json.load(open(path))
+        h = hashlib.sha256()
+        for f in KERNEL_SOURCES:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+    except (OSError, ValueError):
+        return None
+    return rec["dram_bytes_per_launch"] if h.hexdigest() == rec.get("source_sha256") else None
+
+
 def _dist():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -168,12 +187,13 @@ def bench_batched(G, ctx, n=4096, reps=3):
     }
 
 
-def bench_served(G, ctx, rates=(1000, 3000, 10000, 30000), n_req=1500, seed=0):
+def bench_served(G, ctx, rates=(1000, 3000, 10000, 30000, 100000), n_req=1500, seed=0):
     """A pool of 64 meshes (tori, geodesic spheres, gears; 1e3..4e6 triangles,
     BVHs resident) and a stream of random mesh pairs and transforms arriving
     as a Poisson process of rate lambda.  Served: gd_serve_submit/poll
     (continuous batching over stream slots).  Plain: one gd_min_distance per
-    request in arrival order.  Latency = completion - arrival."""
+    request in arrival order.  Latency = completion - arrival (completion: when
+    the result is collected, by gd_serve_drain or on return of the call)."""
     import numpy as np
     from paper_2411_11244_gb300 import synth
     pool = synth.mesh_pool(64, seed=seed)
@@ -202,30 +222,25 @@ def bench_served(G, ctx, rates=(1000, 3000, 10000, 30000), n_req=1500, seed=0):
         # served
         srv = G.gd_serve_start(ctx, slots=4, max_batch=256)
         lat = [None] * n_req
-        tick = [0] * n_req
+        slot_of = {}
         serr = 0
         t0 = time.perf_counter()
         nxt = 0
-        pending = []
-        while nxt < n_req or pending:
+        left = n_req
+        while left > 0:
             now = time.perf_counter() - t0
             while nxt < n_req and arrivals[nxt] <= now:
                 rc, t = G.gd_serve_submit(srv, arr[nxt])
                 if rc != 0:
                     break
-                tick[nxt] = t
-                pending.append(nxt)
+                slot_of[t] = nxt
                 nxt += 1
-            still = []
-            for i in pending:
-                rc, r = G.gd_serve_poll(srv, tick[i])
-                if rc == G.GD_ERR_NOT_READY:
-                    still.append(i)
-                    continue
+            for t, r in G.gd_serve_drain(srv):
+                i = slot_of.pop(t)
                 lat[i] = 1000.0 * ((time.perf_counter() - t0) - arrivals[i])
-                if rc != 0 or r.status != 0:
+                left -= 1
+                if r.status != 0:
                     serr += 1
-            pending = still
         wall = time.perf_counter() - t0
         G.gd_serve_stop(srv)
         sl = sorted(lat)
@@ -406,7 +421,7 @@ def main():
                 "d2h_bytes_per_step": 632, "p50_ms": sorted(e2e_ms)[len(e2e_ms) // 2]},
         "gpu_launches": args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                     "frac": achieved / peak, "traffic": _traffic(), "peak_source": peak_kind,
                      "kernel": "k_query<min>", "alg_bytes_per_launch": alg},
         "traversal": {k: stats[-1][k] for k in ("levels", "front", "slots", "pairs_tested", "leaf_pairs",
                                                   "tri_pairs", "candidates", "refined", "blocks", "probes",

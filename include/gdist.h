@@ -121,6 +121,12 @@ typedef struct {
                               the launch and goes to the next round, whose
                               share is 16x larger (chunks 16x smaller); a
                               chunk of one runs alone */
+    int32_t bounds_mode;   /* 1: enhanced bounds, Eq. 10 (upper bound of the
+                              min) and Eq. 11 (lower bound of the max), the
+                              default; 2: conventional bounds only, Eq. 9 (the
+                              farthest-point bound) for the min and the box gap
+                              for the max: the ablation of Section 9, same
+                              results, more node pairs */
 } gd_tunables;
 
 /* Counters of the last query (or batch) run on a context. */
@@ -159,6 +165,16 @@ GD_API void gd_ctx_destroy(gd_ctx *ctx);
 /* Message of the last failing call on ctx ("" if none).  Owned by ctx. */
 GD_API const char *gd_last_error(gd_ctx *ctx);
 GD_API gd_status gd_ctx_set_tunables(gd_ctx *ctx, const gd_tunables *t);
+/* Autotuner (no counterpart in the paper): times the caller's sample (one
+ * query, or a batch of n, run as gd_min/max_distance or gd_batch_query) under
+ * settings of work_target, k_max, probes, blocks_per_sm and, for n > 1,
+ * batch_budget, one coordinate-descent pass (median of reps timed runs after
+ * one untimed run per setting; a value is kept when >= 1% faster), and leaves
+ * the fastest setting in ctx (also copied to *best unless NULL).  Tunables
+ * change the speed only, never a result.  Synchronous; errors of the sample's
+ * queries are returned (the tunables then stay as they were before the
+ * failing setting). */
+GD_API gd_status gd_autotune(gd_ctx *ctx, const gd_query *sample, int64_t n, int32_t reps, gd_tunables *best);
 GD_API gd_status gd_ctx_get_tunables(gd_ctx *ctx, gd_tunables *t);
 GD_API gd_status gd_get_stats(gd_ctx *ctx, gd_stats *out);
 /* The CUDA stream (cudaStream_t) the context runs on. */
@@ -249,6 +265,10 @@ GD_API gd_status gd_serve_submit(gd_server *srv, const gd_query *q, uint64_t *ti
 /* GD_OK and *out filled if the ticket is done (the ticket is then released);
  * GD_ERR_NOT_READY otherwise. */
 GD_API gd_status gd_serve_poll(gd_server *srv, uint64_t ticket, gd_result *out);
+/* Up to max finished requests (any tickets): their tickets in tickets[0..*n)
+ * and results in out[0..*n); those tickets are released.  GD_OK with *n = 0
+ * when none is finished. */
+GD_API gd_status gd_serve_drain(gd_server *srv, uint64_t *tickets, gd_result *out, int64_t max, int64_t *n);
 /* Drain in-flight work, stop the loop and free the server. */
 GD_API gd_status gd_serve_stop(gd_server *srv);
 

@@ -3,6 +3,7 @@
 // buffers and launches; every step of the computation runs in the kernels of
 // gd_build.cu and gd_query.cu.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -246,6 +247,7 @@ void fill_common(gd_ctx* c, KArgs& a, unsigned* ctr, StatsDev* stats) {
     a.cap_slots = (unsigned)c->cap_slots;
     a.slot_of = c->slot_of;
     a.refit = c->tun.refit_mode == 2 ? 0 : 1;
+    a.conventional = c->tun.bounds_mode == 2 ? 1 : 0;
     a.probes = c->tun.probes;
     a.n_slot_of = 0;
 }
@@ -424,6 +426,7 @@ GD_API gd_status gd_ctx_create(int device, gd_ctx** out) {
     c->tun.refit_slots = 1 << 13;
     c->tun.probes = 64;
     c->tun.batch_budget = 1ll << 18;
+    c->tun.bounds_mode = 1;
     *out = c;
     return GD_OK;
 }
@@ -461,10 +464,77 @@ GD_API gd_status gd_ctx_set_tunables(gd_ctx* c, const gd_tunables* t) {
     if (t->refit_slots > 0) { c->tun.refit_slots = t->refit_slots; realloc = true; }
     if (t->probes > 0) c->tun.probes = t->probes;
     if (t->batch_budget > 0) c->tun.batch_budget = t->batch_budget;
+    if (t->bounds_mode == 1 || t->bounds_mode == 2) c->tun.bounds_mode = t->bounds_mode;
     if (realloc && c->ready) {
         cudaStreamSynchronize(c->stream);
         free_ws(c);
     }
+    return GD_OK;
+}
+
+// Autotuner: one coordinate-descent pass over the traversal tunables, each
+// setting timed (wall clock of the synchronous call, median of reps after one
+// untimed run) on the caller's sample; a value is kept when it is at least 1%
+// faster.  The tunables change only the speed, never the results.
+GD_API gd_status gd_autotune(gd_ctx* c, const gd_query* sample, int64_t n, int32_t reps, gd_tunables* best) {
+    if (!c) return GD_ERR_INVALID_ARG;
+    if (!sample || n < 1 || n > (1ll << 20)) return fail(c, GD_ERR_INVALID_ARG, "autotune needs 1..2^20 sample queries");
+    reps = reps > 0 ? std::min(reps, 50) : 3;
+    std::vector<gd_result> out((size_t)n);
+    auto timed = [&](double* ms) -> gd_status {
+        std::vector<double> t;
+        for (int r = -1; r < reps; ++r) {
+            const auto t0 = std::chrono::steady_clock::now();
+            gd_status s;
+            if (n == 1) {
+                const gd_query& q = sample[0];
+                s = run_single(c, q.a, q.b, (int)q.kind, q.xa, q.xb, out.data());
+            } else {
+                s = gd_batch_query(c, sample, n, out.data());
+            }
+            const auto t1 = std::chrono::steady_clock::now();
+            if (s != GD_OK) return s;
+            if (r >= 0) t.push_back(std::chrono::duration<double, std::milli>(t1 - t0).count());
+        }
+        std::sort(t.begin(), t.end());
+        *ms = t[t.size() / 2];
+        return GD_OK;
+    };
+    double best_ms = 0.0;
+    gd_status s = timed(&best_ms);
+    if (s != GD_OK) return s;
+    struct Axis {
+        int64_t* f64;
+        int32_t* f32;
+        std::vector<int64_t> values;
+    };
+    std::vector<Axis> axes = {
+        {&c->tun.work_target, nullptr, {1ll << 16, 1ll << 17, 1ll << 18, 1ll << 19, 1ll << 20}},
+        {nullptr, &c->tun.k_max, {4, 5, 6, 7}},
+        {nullptr, &c->tun.probes, {1, 16, 64, 128}},
+        {nullptr, &c->tun.blocks_per_sm, {1, 2}},
+    };
+    if (n > 1) axes.push_back({&c->tun.batch_budget, nullptr, {1ll << 16, 1ll << 18, 1ll << 20}});
+    for (Axis& ax : axes) {
+        const int64_t keep = ax.f64 ? *ax.f64 : *ax.f32;
+        int64_t chosen = keep;
+        for (int64_t v : ax.values) {
+            if (v == keep) continue;
+            if (ax.f64) *ax.f64 = v; else *ax.f32 = (int32_t)v;
+            double ms = 0.0;
+            s = timed(&ms);
+            if (s != GD_OK) {
+                if (ax.f64) *ax.f64 = keep; else *ax.f32 = (int32_t)keep;
+                return s;
+            }
+            if (ms < 0.99 * best_ms) {
+                best_ms = ms;
+                chosen = v;
+            }
+        }
+        if (ax.f64) *ax.f64 = chosen; else *ax.f32 = (int32_t)chosen;
+    }
+    if (best) *best = c->tun;
     return GD_OK;
 }
 
@@ -713,7 +783,7 @@ GD_API gd_status gd_batch_query(gd_ctx* ctx, const gd_query* q, int64_t n, gd_re
 // ---- hooks for the serving loop (gd_serve.cu)
 namespace gd {
 
-gd_status serve_launch_batch(gd_ctx* ctx, SlotBuffers& sb, const gd_query* qs, long long m, int kind) {
+gd_status serve_launch_batch(gd_ctx* ctx, SlotBuffers& sb, const gd_query* qs, long long m, int kind, int grid) {
     long long tab = 0;
     for (long long j = 0; j < m; ++j) {
         QIn& in = sb.qin_host[j];
@@ -751,10 +821,12 @@ gd_status serve_launch_batch(gd_ctx* ctx, SlotBuffers& sb, const gd_query* qs, l
     a.cap_slots = (unsigned)sb.cap_slots;
     a.slot_of = sb.slot_of;
     a.refit = refit ? 1 : 0;
+    a.conventional = ctx->tun.bounds_mode == 2 ? 1 : 0;
     a.probes = ctx->tun.probes;
     a.n_slot_of = refit ? (unsigned long long)tab : 0ull;
     a.q_budget = batch_share(sb.cap_front, sb.cap_leaf, m);
-    GD_CUDA(ctx, launch_query(kind, a, sb.grid, sb.stream));
+    a.work_ctas = m == 1 ? single_work_ctas(ctx, grid) : (unsigned)grid;
+    GD_CUDA(ctx, launch_query(kind, a, grid, sb.stream));
     GD_CUDA(ctx, cudaMemcpyAsync(sb.out_host, sb.out_dev, sizeof(gd_result) * m, cudaMemcpyDeviceToHost, sb.stream));
     GD_CUDA(ctx, cudaMemcpyAsync(sb.ctr_host, sb.mb_dev_ctr, sizeof(unsigned) * kCtrWords, cudaMemcpyDeviceToHost,
                                  sb.stream));

@@ -116,26 +116,69 @@ __global__ void k_rs_hist(const unsigned long long* keys, long long n, int shift
     hist[(long long)threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
 }
 
-// exclusive scan of m words in place, one CTA of 1024 threads
-__global__ void k_rs_scan(unsigned* hist, long long m) {
-    __shared__ unsigned part[1024];
-    long long per = (m + 1023) / 1024;
-    long long b = threadIdx.x * per, e = b + per < m ? b + per : m;
-    unsigned s = 0;
-    for (long long i = b; i < e; ++i) s += hist[i];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        unsigned v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
+// Exclusive scan of m words in place, in three launches: every CTA of
+// kScanCtas sums its contiguous chunk (k_scan_sums), one CTA scans those sums
+// (k_scan_top), and every CTA scans its chunk tile by tile from its offset
+// (k_scan_chunks).  Loads and stores are coalesced.
+constexpr int kScanCtas = 256;
+constexpr int kScanThreads = 256;
+static_assert(kScanCtas == kScanThreads, "k_scan_top scans one sum per thread");
+
+__device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned* total) {
+    __shared__ unsigned warp_sum[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
     }
-    unsigned run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
-    for (long long i = b; i < e; ++i) {
-        unsigned v = hist[i];
-        hist[i] = run;
-        run += v;
+    if (lane == 31) warp_sum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned w = lane < kScanThreads / 32 ? warp_sum[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(kFull, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < kScanThreads / 32) warp_sum[lane] = w;
+    }
+    __syncthreads();
+    const unsigned before = warp ? warp_sum[warp - 1] : 0u;
+    *total = warp_sum[kScanThreads / 32 - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void k_scan_sums(const unsigned* a, long long m, unsigned* sums) {
+    const long long chunk = (m + kScanCtas - 1) / kScanCtas;
+    const long long b = blockIdx.x * chunk, e = b + chunk < m ? b + chunk : m;
+    unsigned s = 0;
+    for (long long i = b + threadIdx.x; i < e; i += kScanThreads) s += a[i];
+    unsigned total;
+    block_excl_scan(s, &total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void k_scan_top(unsigned* sums) {
+    unsigned total;
+    const unsigned v = sums[threadIdx.x];
+    const unsigned x = block_excl_scan(v, &total);
+    sums[threadIdx.x] = x;
+}
+
+__global__ void k_scan_chunks(unsigned* a, long long m, const unsigned* sums) {
+    const long long chunk = (m + kScanCtas - 1) / kScanCtas;
+    const long long b = blockIdx.x * chunk, e = b + chunk < m ? b + chunk : m;
+    unsigned run = sums[blockIdx.x];
+    for (long long t = b; t < e; t += kScanThreads) {
+        const long long i = t + threadIdx.x;
+        const unsigned v = i < e ? a[i] : 0u;
+        unsigned total;
+        const unsigned x = block_excl_scan(v, &total);
+        if (i < e) a[i] = run + x;
+        run += total;
     }
 }
 
@@ -237,10 +280,11 @@ int grid_for(long long n, int threads) {
 
 }  // namespace
 
+// the histogram (256 digits x tiles) followed by the scan's per-CTA sums
 size_t build_hist_words(long long nt) {
     long long nb = (nt + kSortTile - 1) / kSortTile;
     if (nb < 1) nb = 1;
-    return (size_t)nb * 256;
+    return (size_t)nb * 256 + kScanCtas;
 }
 
 cudaError_t build_validate(const BuildBuffers& b, cudaStream_t st) {
@@ -257,7 +301,10 @@ cudaError_t build_tree(const BuildBuffers& b, cudaStream_t st) {
     int cur = 0;
     for (int p = 0; p < passes; ++p) {
         k_rs_hist<<<(unsigned)nb, kSortThreads, 0, st>>>(b.keys[cur], b.nt, 8 * p, b.hist);
-        k_rs_scan<<<1, 1024, 0, st>>>(b.hist, nb * 256);
+        unsigned* sums = b.hist + nb * 256;
+        k_scan_sums<<<kScanCtas, kScanThreads, 0, st>>>(b.hist, nb * 256, sums);
+        k_scan_top<<<1, kScanThreads, 0, st>>>(sums);
+        k_scan_chunks<<<kScanCtas, kScanThreads, 0, st>>>(b.hist, nb * 256, sums);
         k_rs_scatter<<<(unsigned)nb, kSortThreads, 0, st>>>(b.keys[cur], b.vals[cur], b.keys[cur ^ 1],
                                                              b.vals[cur ^ 1], b.nt, 8 * p, b.hist);
         cur ^= 1;

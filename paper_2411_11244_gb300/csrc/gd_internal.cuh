@@ -151,6 +151,8 @@ struct KArgs {
     unsigned long long n_slot_of;
     uint2* jobs;                // (query, root) of every refit slot
     int refit;                  // 0: map B's local boxes only; 1: lazy refit
+    int conventional;           // 1: conventional bounds only (Eq. 9 for the min, the
+                                // box gap for the max) instead of Eqs. 10-11
     int probes;                 // greedy probes per launch (at least one per query)
     long long work_target;
     int k_max;

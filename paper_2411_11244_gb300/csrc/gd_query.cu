@@ -576,7 +576,7 @@ __device__ __forceinline__ float pair_bounds(const KArgs& A, const QView& V, uns
             bound = lower_min_sq(ba, bb.lo, bb.hi);
             *survive = bound <= min_keep_threshold(Ucur, V.E_box);
             if (*survive) {
-                float u2 = upper_min_sq_enhanced<true>(V.X, ba, bb);
+                float u2 = A.conventional ? upper_max_sq(ba, bb.lo, bb.hi) : upper_min_sq_enhanced<true>(V.X, ba, bb);
                 *newU = __float_as_uint(upper_from_sq(u2, V.E_box));
                 *key = __float_as_uint(u2);
             }
@@ -584,7 +584,7 @@ __device__ __forceinline__ float pair_bounds(const KArgs& A, const QView& V, uns
             bound = upper_max_sq(ba, bb.lo, bb.hi);
             *survive = bound >= max_keep_threshold(Ucur, V.E_box);
             if (*survive) {
-                float l2 = lower_max_sq_enhanced<true>(V.X, ba, bb);
+                float l2 = A.conventional ? lower_min_sq(ba, bb.lo, bb.hi) : lower_max_sq_enhanced<true>(V.X, ba, bb);
                 *newU = __float_as_uint(lower_from_sq(l2, V.E_box));
                 *key = ~__float_as_uint(l2);
             }
@@ -597,7 +597,7 @@ __device__ __forceinline__ float pair_bounds(const KArgs& A, const QView& V, uns
             bound = lower_min_sq(ba, elo, ehi);
             *survive = bound <= min_keep_threshold(Ucur, V.E_box);
             if (*survive) {
-                float u2 = upper_min_sq_enhanced<false>(V.X, ba, bb);
+                float u2 = A.conventional ? upper_max_sq(ba, elo, ehi) : upper_min_sq_enhanced<false>(V.X, ba, bb);
                 *newU = __float_as_uint(upper_from_sq(u2, V.E_box));
                 *key = __float_as_uint(u2);
             }
@@ -605,7 +605,7 @@ __device__ __forceinline__ float pair_bounds(const KArgs& A, const QView& V, uns
             bound = upper_max_sq(ba, elo, ehi);
             *survive = bound >= max_keep_threshold(Ucur, V.E_box);
             if (*survive) {
-                float l2 = lower_max_sq_enhanced<false>(V.X, ba, bb);
+                float l2 = A.conventional ? lower_min_sq(ba, elo, ehi) : lower_max_sq_enhanced<false>(V.X, ba, bb);
                 *newU = __float_as_uint(lower_from_sq(l2, V.E_box));
                 *key = ~__float_as_uint(l2);
             }

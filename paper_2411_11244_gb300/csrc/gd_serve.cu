@@ -31,6 +31,7 @@ struct Request {
 struct Slot {
     SlotBuffers b;
     bool busy = false;
+    bool whole = false;  // launched on the whole GPU: no other slot starts meanwhile
     int kind = 0;
     std::vector<Request> reqs;
 };
@@ -58,6 +59,7 @@ struct gd_server {
     long long queued_foot = 0;
     long long slot_budget = 0;
     uint64_t next_ticket = 1;
+    int whole_grid = 0;  // co-resident CTAs of the whole GPU
     std::atomic<bool> stop{false};
     std::thread loop;
     gd_status loop_error = GD_OK;
@@ -174,8 +176,12 @@ void run_loop(gd_server* S) {
                 worked = true;
             }
         }
-        // admit queued requests into free slots
+        // admit queued requests into free slots (none while a slot holds the
+        // whole GPU)
+        bool whole_busy = false;
+        for (Slot& s : S->slots) whole_busy = whole_busy || (s.busy && s.whole);
         for (Slot& s : S->slots) {
+            if (whole_busy) break;
             if (s.busy) continue;
             std::vector<Request> take;
             {
@@ -201,7 +207,18 @@ void run_loop(gd_server* S) {
             std::vector<gd_query> qs(take.size());
             for (size_t j = 0; j < take.size(); ++j) qs[j] = take[j].q;
             int kind = (int)qs[0].kind;
-            gd_status st = serve_launch_batch(S->ctx, s.b, qs.data(), (long long)qs.size(), kind);
+            // a batch that finds the GPU idle and the queue empty gets the whole
+            // GPU (the latency of a lone request is that of a plain query);
+            // otherwise the slot's share, so that slots run side by side
+            bool idle = true;
+            for (Slot& o : S->slots) idle = idle && !o.busy;
+            bool solo = false;
+            if (idle) {
+                std::lock_guard<std::mutex> g(S->mu);
+                solo = S->queue.empty();
+            }
+            const int grid = solo ? S->whole_grid : s.b.grid;
+            gd_status st = serve_launch_batch(S->ctx, s.b, qs.data(), (long long)qs.size(), kind, grid);
             if (st != GD_OK) {
                 std::lock_guard<std::mutex> g(S->mu);
                 for (auto& r : take) {
@@ -213,9 +230,11 @@ void run_loop(gd_server* S) {
                 continue;
             }
             s.kind = kind;
+            s.whole = solo;
             s.reqs = std::move(take);
             s.busy = true;
             worked = true;
+            if (solo) break;
         }
         if (S->stop.load()) {
             bool idle = true;
@@ -273,6 +292,7 @@ GD_API gd_status gd_serve_start(gd_ctx* ctx, const gd_serve_opts* opts, gd_serve
         per -= per % 16;
         if (per < 16) per = std::min(16, cap);
     }
+    S->whole_grid = cap;
     S->slots.resize(o.slots);
     for (Slot& s : S->slots) {
         if (!alloc_slot(s, S->slot_budget, o.max_batch, per)) {
@@ -321,6 +341,20 @@ GD_API gd_status gd_serve_poll(gd_server* S, uint64_t ticket, gd_result* out) {
     }
     if (S->pending.count(ticket)) return GD_ERR_NOT_READY;
     return GD_ERR_INVALID_ARG;
+}
+
+GD_API gd_status gd_serve_drain(gd_server* S, uint64_t* tickets, gd_result* out, int64_t max, int64_t* n) {
+    if (!S || !n || max < 0 || (max > 0 && (!tickets || !out))) return GD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(S->mu);
+    int64_t k = 0;
+    for (auto it = S->done.begin(); it != S->done.end() && k < max;) {
+        tickets[k] = it->first;
+        out[k] = it->second;
+        ++k;
+        it = S->done.erase(it);
+    }
+    *n = k;
+    return GD_OK;
 }
 
 GD_API gd_status gd_serve_stop(gd_server* S) {

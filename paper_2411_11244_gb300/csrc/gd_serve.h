@@ -33,7 +33,7 @@ struct SlotBuffers {
     int grid = 0;
 };
 
-gd_status serve_launch_batch(gd_ctx* ctx, SlotBuffers& sb, const gd_query* qs, long long m, int kind);
+gd_status serve_launch_batch(gd_ctx* ctx, SlotBuffers& sb, const gd_query* qs, long long m, int kind, int grid);
 gd_status serve_single(gd_ctx* ctx, const gd_query& q, gd_result* out);
 int serve_device(gd_ctx* ctx);
 int serve_sms(gd_ctx* ctx);

@@ -29,8 +29,8 @@ EXPORTS = [
     "gd_ctx_create", "gd_ctx_destroy", "gd_last_error", "gd_ctx_set_tunables", "gd_ctx_get_tunables",
     "gd_get_stats", "gd_ctx_stream", "gd_mesh_create", "gd_bvh_build", "gd_mesh_destroy", "gd_mesh_info",
     "gd_mesh_download", "gd_min_distance", "gd_max_distance", "gd_query_device", "gd_query_device_noalloc",
-    "gd_batch_query",
-    "gd_serve_start", "gd_serve_submit", "gd_serve_poll", "gd_serve_stop",
+    "gd_batch_query", "gd_autotune",
+    "gd_serve_start", "gd_serve_submit", "gd_serve_poll", "gd_serve_drain", "gd_serve_stop",
 ]
 
 
@@ -56,7 +56,8 @@ class gd_tunables(C.Structure):
     _fields_ = [("work_target", C.c_int64), ("k_max", C.c_int32), ("blocks_per_sm", C.c_int32),
                 ("front_capacity", C.c_int64), ("leaf_capacity", C.c_int64), ("cand_capacity", C.c_int64),
                 ("max_capacity", C.c_int64), ("timeout_ns", C.c_int64), ("refit_mode", C.c_int32),
-                ("refit_slots", C.c_int32), ("probes", C.c_int32), ("batch_budget", C.c_int64)]
+                ("refit_slots", C.c_int32), ("probes", C.c_int32), ("batch_budget", C.c_int64),
+                ("bounds_mode", C.c_int32)]
 
 
 class gd_stats(C.Structure):
@@ -118,9 +119,12 @@ def load(path: str = LIB_PATH):
         "gd_query_device": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp, _vp, _vp, _vp]),
         "gd_query_device_noalloc": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _vp, _vp]),
         "gd_batch_query": (C.c_int, [_vp, C.POINTER(gd_query), C.c_int64, C.POINTER(gd_result)]),
+        "gd_autotune": (C.c_int, [_vp, C.POINTER(gd_query), C.c_int64, C.c_int32, C.POINTER(gd_tunables)]),
         "gd_serve_start": (C.c_int, [_vp, C.POINTER(gd_serve_opts), C.POINTER(_vp)]),
         "gd_serve_submit": (C.c_int, [_vp, C.POINTER(gd_query), C.POINTER(C.c_uint64)]),
         "gd_serve_poll": (C.c_int, [_vp, C.c_uint64, C.POINTER(gd_result)]),
+        "gd_serve_drain": (C.c_int, [_vp, C.POINTER(C.c_uint64), C.POINTER(gd_result), C.c_int64,
+                                     C.POINTER(C.c_int64)]),
         "gd_serve_stop": (C.c_int, [_vp]),
     }
     for name, (res, args) in sig.items():
@@ -266,6 +270,15 @@ def make_queries(items):
     return arr
 
 
+def gd_autotune(ctx, sample, reps=3) -> dict:
+    """Tune ctx's traversal tunables on a sample of queries; returns them."""
+    if not isinstance(sample, C.Array):
+        sample = make_queries(sample)
+    t = gd_tunables()
+    _check(load().gd_autotune(ctx, sample, len(sample), int(reps), C.byref(t)), ctx)
+    return {f: getattr(t, f) for f, _ in gd_tunables._fields_}
+
+
 def gd_batch_query(ctx, queries):
     if not isinstance(queries, C.Array):
         queries = make_queries(queries)
@@ -292,6 +305,21 @@ def gd_serve_poll(srv, ticket):
     r = gd_result()
     rc = load().gd_serve_poll(srv, C.c_uint64(ticket), C.byref(r))
     return rc, r
+
+
+_drain_bufs = {}
+
+
+def gd_serve_drain(srv, max_n=256):
+    """Finished requests as a list of (ticket, gd_result), at most max_n."""
+    if max_n not in _drain_bufs:
+        _drain_bufs[max_n] = ((C.c_uint64 * max_n)(), (gd_result * max_n)())
+    tk, rs = _drain_bufs[max_n]
+    n = C.c_int64()
+    rc = load().gd_serve_drain(srv, tk, rs, max_n, C.byref(n))
+    if rc != GD_OK:
+        raise GdError(rc, "gd_serve_drain")
+    return [(tk[i], gd_result.from_buffer_copy(rs[i])) for i in range(n.value)]
 
 
 def gd_serve_stop(srv):

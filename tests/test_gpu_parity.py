@@ -328,6 +328,63 @@ def test_refit_modes_agree(G, oracle_mod):
         G.gd_ctx_destroy(c)
 
 
+def test_conventional_bounds_ablation(G, oracle_mod):
+    """Section 9's ablation: with conventional bounds only (Eq. 9 for the min,
+    the box gap for the max) the answers are the same and the traversal tests
+    at least as many node pairs; the enhanced bounds cull more."""
+    c = G.gd_ctx_create(0)
+    try:
+        rng = np.random.default_rng(19)
+        A = synth.torus(1.0, 0.1, 96, 40)
+        B = synth.geosphere(20, 0.5, 1e-3, 3)
+        ma, mb = _mesh(G, c, A), _mesh(G, c, B)
+        more = 0
+        for i in range(4):
+            xa, xb = _rigid(rng, 0.3), _rigid(rng, 1.5)
+            for kind, fn in (("min", G.gd_min_distance), ("max", G.gd_max_distance)):
+                G.gd_ctx_set_tunables(c, bounds_mode=1)
+                r1 = fn(c, ma, mb, xa, xb)
+                p1 = G.gd_get_stats(c)["pairs_tested"]
+                G.gd_ctx_set_tunables(c, bounds_mode=2)
+                r2 = fn(c, ma, mb, xa, xb)
+                p2 = G.gd_get_stats(c)["pairs_tested"]
+                same_answer(r1, r2, oracle_mod, A, xa, B, xb, kind)
+                more += p2 > p1
+        assert more > 0
+        G.gd_ctx_set_tunables(c, bounds_mode=1)
+        G.gd_mesh_destroy(ma)
+        G.gd_mesh_destroy(mb)
+    finally:
+        G.gd_ctx_destroy(c)
+
+
+def test_autotune_keeps_answers(G, oracle_mod):
+    """gd_autotune picks tunables by timing and never changes an answer: the
+    answers before and after tuning are the same (single query and batch)."""
+    c = G.gd_ctx_create(0)
+    try:
+        rng = np.random.default_rng(23)
+        A = synth.torus(1.0, 0.1, 96, 40)
+        B = synth.geosphere(12, 0.5, 1e-3, 3)
+        ma, mb = _mesh(G, c, A), _mesh(G, c, B)
+        items = [(ma, mb, _rigid(rng, 0.3), _rigid(rng, 1.5), i % 2) for i in range(8)]
+        before = G.gd_batch_query(c, items)
+        one = G.gd_min_distance(c, ma, mb, items[0][2], items[0][3])
+        t1 = G.gd_autotune(c, items[:1], reps=2)
+        assert t1["k_max"] in (4, 5, 6, 7) and t1["work_target"] >= 1 << 16
+        t2 = G.gd_autotune(c, items, reps=2)
+        assert t2["batch_budget"] in (1 << 16, 1 << 18, 1 << 20)
+        after = G.gd_batch_query(c, items)
+        for i, (a, b, xa, xb, kind) in enumerate(items):
+            same_answer(before[i], after[i], oracle_mod, A, xa, B, xb, "min" if kind == 0 else "max")
+        same_answer(one, G.gd_min_distance(c, ma, mb, items[0][2], items[0][3]), oracle_mod, A, items[0][2], B,
+                    items[0][3], "min")
+        G.gd_mesh_destroy(ma)
+        G.gd_mesh_destroy(mb)
+    finally:
+        G.gd_ctx_destroy(c)
+
+
 def test_device_resident_query(G, ctx, oracle_mod):
     torch = pytest.importorskip("torch")
     A, B, xa, xb = synth.config_tori(1)
@@ -472,6 +529,41 @@ def test_serve_alone_equals_in_mix(G, ctx, oracle_mod):
         a, b = ids[i]
         same_answer(got[t], alone[i], oracle_mod, meshes[a], qs[i][2], meshes[b], qs[i][3],
                     "min" if qs[i][4] == 0 else "max")
+    for h in hs:
+        G.gd_mesh_destroy(h)
+
+
+def test_serve_drain_collects_every_ticket(G, ctx, oracle_mod):
+    """gd_serve_drain hands back every finished request once, with the same
+    answer as the request alone."""
+    import time
+    rng = np.random.default_rng(8)
+    meshes = [synth.torus(1.0, 0.25, 40, 20), synth.geosphere(12, 0.6, 1e-3, 1)]
+    hs = [_mesh(G, ctx, m) for m in meshes]
+    qs = [(hs[i % 2], hs[(i + 1) % 2], _rigid(rng, 0.3), _rigid(rng, 1.5), G.GD_MIN) for i in range(40)]
+    alone = [G.gd_min_distance(ctx, q[0], q[1], q[2], q[3]) for q in qs]
+    arr = G.make_queries(qs)
+    srv = G.gd_serve_start(ctx, slots=2, max_batch=8)
+    try:
+        idx = {}
+        for i in range(len(qs)):
+            rc, t = G.gd_serve_submit(srv, arr[i])
+            assert rc == 0
+            idx[t] = i
+        got = {}
+        deadline = time.time() + 120
+        while len(got) < len(qs) and time.time() < deadline:
+            for t, r in G.gd_serve_drain(srv, 16):
+                assert t in idx and t not in got
+                got[t] = r
+            time.sleep(0.001)
+    finally:
+        G.gd_serve_stop(srv)
+    assert len(got) == len(qs)
+    for t, r in got.items():
+        i = idx[t]
+        a = 0 if i % 2 == 0 else 1
+        same_answer(r, alone[i], oracle_mod, meshes[a], qs[i][2], meshes[1 - a], qs[i][3], "min")
     for h in hs:
         G.gd_mesh_destroy(h)
 
