@@ -187,6 +187,41 @@ def bench_batched(G, ctx, n=4096, reps=3):
     }
 
 
+def bench_ablation(G, ctx, ma, mb, xa, xbs, frames=4):
+    """Section 9's ablations on the rings frames, same engine: the enhanced
+    bounds (Eqs. 10-11) against the conventional ones only (Eq. 9), and the
+    adaptive depth k (Section 6) against a fixed k = 5; node pairs tested and
+    ms per query (synchronous calls, means over the frames)."""
+    base = G.gd_ctx_get_tunables(ctx)
+
+    def run(**tun):
+        G.gd_ctx_set_tunables(ctx, **tun)
+        G.gd_min_distance(ctx, ma, mb, xa, xbs[0])
+        pairs, ms, d = [], [], []
+        for xb in xbs[1:frames + 1]:
+            t0 = time.perf_counter()
+            r = G.gd_min_distance(ctx, ma, mb, xa, xb)
+            ms.append(1000.0 * (time.perf_counter() - t0))
+            pairs.append(G.gd_get_stats(ctx)["pairs_tested"])
+            d.append(r.d)
+        return statistics.mean(pairs), statistics.mean(ms), d
+
+    p_enh, t_enh, d_enh = run(bounds_mode=1)
+    p_conv, t_conv, d_conv = run(bounds_mode=2)
+    p_fix, t_fix, d_fix = run(bounds_mode=1, k_max=5, work_target=1 << 40)
+    G.gd_ctx_set_tunables(ctx, bounds_mode=1, k_max=base["k_max"], work_target=base["work_target"])
+    return {
+        "frames": frames,
+        "enhanced": {"pairs_tested": p_enh, "ms": t_enh},
+        "conventional": {"pairs_tested": p_conv, "ms": t_conv},
+        "fixed_k5": {"pairs_tested": p_fix, "ms": t_fix},
+        "pairs_ratio_enhanced_over_conventional": p_enh / p_conv,
+        "slowdown_conventional": t_conv / t_enh,
+        "slowdown_fixed_k5": t_fix / t_enh,
+        "same_answers": d_enh == d_conv == d_fix,
+    }
+
+
 def bench_served(G, ctx, rates=(1000, 3000, 10000, 30000, 100000), n_req=1500, seed=0):
     """A pool of 64 meshes (tori, geodesic spheres, gears; 1e3..4e6 triangles,
     BVHs resident) and a stream of random mesh pairs and transforms arriving
@@ -310,6 +345,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-ablation", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -429,6 +465,8 @@ def main():
         "clocks": clk.summary(),
         "wall_s": wall,
     }
+    if not args.no_ablation:
+        line["ablation"] = bench_ablation(G, ctx, ma, mb, xa, xbs)
     G.gd_mesh_destroy(ma)
     G.gd_mesh_destroy(mb)
     if not args.no_batched:

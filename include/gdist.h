@@ -237,6 +237,22 @@ GD_API gd_status gd_query_device(gd_ctx *ctx, const gd_mesh *A, const gd_mesh *B
  * serialise them.  Asynchronous; returns argument and launch errors only. */
 GD_API gd_status gd_query_device_noalloc(const gd_mesh *A, const gd_mesh *B, gd_kind kind, const double *d_xa,
                                          const double *d_xb, gd_result *d_out, void *stream);
+/* A captured CUDA graph of one device-resident query (the launch of
+ * gd_query_device with these arguments), for loops that ask the same
+ * question every frame: update *d_xa / *d_xb in place (device memory), then
+ * gd_graph_launch; the result lands in *d_out as for gd_query_device
+ * (status GD_ERR_OVERFLOW when the work outgrew the buffers: run one
+ * synchronous query to grow them).  The graph holds one cooperative kernel
+ * node; it is rebuilt by gd_graph_launch when the context's work buffers or
+ * tunables changed.  Meshes, transforms and result must outlive the graph.
+ * No counterpart in the paper. */
+typedef struct gd_graph gd_graph;
+GD_API gd_status gd_graph_create(gd_ctx *ctx, const gd_mesh *A, const gd_mesh *B, gd_kind kind, const double *d_xa,
+                                 const double *d_xb, gd_result *d_out, gd_graph **out);
+/* Asynchronous on stream (NULL: the context's stream). */
+GD_API gd_status gd_graph_launch(gd_graph *g, void *stream);
+GD_API gd_status gd_graph_destroy(gd_graph *g);
+
 /* n independent queries (any mix of meshes and kinds), results in
  * out[0..n).  Synchronous.  Each kind runs in persistent launches of chunks
  * of queries whose fronts share the work queues (sizes: see batch_budget in

@@ -64,6 +64,7 @@ struct gd_ctx {
     long long cap_table = 0;
     gd_stats last{};
     bool stats_pending = false;  // last run was device-resident: stats still on the device
+    unsigned ws_gen = 0;         // bumped whenever the work buffers or tunables change
     int last_grid = 0;
 };
 
@@ -139,6 +140,7 @@ gd_status alloc_queues(gd_ctx* c) {
     GD_CUDA(c, cudaMalloc(&c->rbox, sizeof(float) * 6 * kRefitBoxes * (size_t)c->cap_slots));
     GD_CUDA(c, cudaMalloc(&c->jobs, sizeof(uint2) * (size_t)c->cap_slots));
     c->ready = true;
+    ++c->ws_gen;
     return GD_OK;
 }
 
@@ -465,6 +467,7 @@ GD_API gd_status gd_ctx_set_tunables(gd_ctx* c, const gd_tunables* t) {
     if (t->probes > 0) c->tun.probes = t->probes;
     if (t->batch_budget > 0) c->tun.batch_budget = t->batch_budget;
     if (t->bounds_mode == 1 || t->bounds_mode == 2) c->tun.bounds_mode = t->bounds_mode;
+    ++c->ws_gen;
     if (realloc && c->ready) {
         cudaStreamSynchronize(c->stream);
         free_ws(c);
@@ -720,6 +723,96 @@ GD_API gd_status gd_query_device(gd_ctx* ctx, const gd_mesh* A, const gd_mesh* B
     GD_CUDA(ctx, launch_query((int)kind, a, grid, st));
     ctx->stats_pending = true;
     ctx->last_grid = grid;
+    return GD_OK;
+}
+
+struct gd_graph {
+    gd_ctx* ctx = nullptr;
+    const gd_mesh* A = nullptr;
+    const gd_mesh* B = nullptr;
+    gd_kind kind = GD_MIN;
+    const double* d_xa = nullptr;
+    const double* d_xb = nullptr;
+    gd_result* d_out = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned gen = 0;  // work-buffer generation the graph was built for
+};
+
+namespace {
+gd_status graph_build(gd_graph* g) {
+    gd_ctx* ctx = g->ctx;
+    KArgs a{};
+    a.nq = 1;
+    a.mA = g->A->d_desc;
+    a.mB = g->B->d_desc;
+    a.xa_src = g->d_xa;
+    a.xb_src = g->d_xb;
+    const long long tab = table_entries(ctx, g->B);
+    gd_status s = ensure_table(ctx, tab);
+    if (s != GD_OK) return s;
+    fill_common(ctx, a, ctx->mb_dev->ctr, &ctx->mb_dev->stats);
+    a.slot_of = ctx->slot_of;
+    a.n_slot_of = (unsigned long long)tab;
+    a.out = g->d_out;
+    const int grid = grid_blocks(ctx, (int)g->kind);
+    a.work_ctas = single_work_ctas(ctx, grid);
+    if (g->exec) {
+        cudaGraphExecDestroy(g->exec);
+        g->exec = nullptr;
+    }
+    GD_CUDA(ctx, build_query_graph((int)g->kind, a, grid, &g->exec));
+    g->gen = ctx->ws_gen;
+    ctx->last_grid = grid;
+    return GD_OK;
+}
+}  // namespace
+
+GD_API gd_status gd_graph_create(gd_ctx* ctx, const gd_mesh* A, const gd_mesh* B, gd_kind kind, const double* d_xa,
+                                 const double* d_xb, gd_result* d_out, gd_graph** out) {
+    if (!ctx || !out) return GD_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!d_xa || !d_xb || !d_out || (kind != GD_MIN && kind != GD_MAX))
+        return fail(ctx, GD_ERR_INVALID_ARG, "NULL argument or bad kind");
+    gd_status s = check_pair(ctx, A, B);
+    if (s != GD_OK) return s;
+    if (!ctx->ready || !ctx->mb_dev || ctx->cap_q < 1)
+        return fail(ctx, GD_ERR_INVALID_ARG, "work buffers not sized: run one synchronous query first");
+    gd_graph* g = new gd_graph();
+    g->ctx = ctx;
+    g->A = A;
+    g->B = B;
+    g->kind = kind;
+    g->d_xa = d_xa;
+    g->d_xb = d_xb;
+    g->d_out = d_out;
+    s = graph_build(g);
+    if (s != GD_OK) {
+        delete g;
+        return s;
+    }
+    *out = g;
+    return GD_OK;
+}
+
+GD_API gd_status gd_graph_launch(gd_graph* g, void* stream) {
+    if (!g) return GD_ERR_INVALID_ARG;
+    gd_ctx* ctx = g->ctx;
+    if (!ctx->ready) return fail(ctx, GD_ERR_INVALID_ARG, "work buffers not sized: run one synchronous query first");
+    if (g->gen != ctx->ws_gen) {
+        // the context's work buffers moved (grown queues, new tunables): the
+        // node's arguments are rebuilt
+        gd_status s = graph_build(g);
+        if (s != GD_OK) return s;
+    }
+    GD_CUDA(ctx, cudaGraphLaunch(g->exec, stream ? (cudaStream_t)stream : ctx->stream));
+    ctx->stats_pending = true;
+    return GD_OK;
+}
+
+GD_API gd_status gd_graph_destroy(gd_graph* g) {
+    if (!g) return GD_ERR_INVALID_ARG;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    delete g;
     return GD_OK;
 }
 

@@ -32,5 +32,6 @@ cudaError_t build_tree(const BuildBuffers& b, cudaStream_t stream);
 // ---- query (gd_query.cu)
 int query_max_blocks_per_sm(int kind);
 cudaError_t launch_query(int kind, const KArgs& args, int grid, cudaStream_t stream);
+cudaError_t build_query_graph(int kind, const KArgs& args, int grid, cudaGraphExec_t* exec);
 
 }  // namespace gd

@@ -1791,4 +1791,29 @@ cudaError_t launch_query(int kind, const KArgs& args, int grid, cudaStream_t str
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), params, 0, stream);
 }
 
+// A graph with the query kernel as its one cooperative kernel node (the
+// arguments are copied into the node).
+cudaError_t build_query_graph(int kind, const KArgs& args, int grid, cudaGraphExec_t* exec) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return e;
+    void* params[] = {const_cast<KArgs*>(&args)};
+    cudaKernelNodeParams p{};
+    p.func = kind == 0 ? (void*)k_query<0> : (void*)k_query<1>;
+    p.gridDim = dim3(grid);
+    p.blockDim = dim3(kBlock);
+    p.sharedMemBytes = 0;
+    p.kernelParams = params;
+    cudaGraphNode_t node = nullptr;
+    e = cudaGraphAddKernelNode(&node, g, nullptr, 0, &p);
+    if (e == cudaSuccess) {
+        cudaLaunchAttributeValue v{};
+        v.cooperative = 1;
+        e = cudaGraphKernelNodeSetAttribute(node, cudaLaunchAttributeCooperative, &v);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    return e;
+}
+
 }  // namespace gd

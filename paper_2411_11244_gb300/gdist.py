@@ -29,7 +29,7 @@ EXPORTS = [
     "gd_ctx_create", "gd_ctx_destroy", "gd_last_error", "gd_ctx_set_tunables", "gd_ctx_get_tunables",
     "gd_get_stats", "gd_ctx_stream", "gd_mesh_create", "gd_bvh_build", "gd_mesh_destroy", "gd_mesh_info",
     "gd_mesh_download", "gd_min_distance", "gd_max_distance", "gd_query_device", "gd_query_device_noalloc",
-    "gd_batch_query", "gd_autotune",
+    "gd_batch_query", "gd_autotune", "gd_graph_create", "gd_graph_launch", "gd_graph_destroy",
     "gd_serve_start", "gd_serve_submit", "gd_serve_poll", "gd_serve_drain", "gd_serve_stop",
 ]
 
@@ -120,6 +120,9 @@ def load(path: str = LIB_PATH):
         "gd_query_device_noalloc": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _vp, _vp]),
         "gd_batch_query": (C.c_int, [_vp, C.POINTER(gd_query), C.c_int64, C.POINTER(gd_result)]),
         "gd_autotune": (C.c_int, [_vp, C.POINTER(gd_query), C.c_int64, C.c_int32, C.POINTER(gd_tunables)]),
+        "gd_graph_create": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp, _vp, _vp, C.POINTER(_vp)]),
+        "gd_graph_launch": (C.c_int, [_vp, _vp]),
+        "gd_graph_destroy": (C.c_int, [_vp]),
         "gd_serve_start": (C.c_int, [_vp, C.POINTER(gd_serve_opts), C.POINTER(_vp)]),
         "gd_serve_submit": (C.c_int, [_vp, C.POINTER(gd_query), C.POINTER(C.c_uint64)]),
         "gd_serve_poll": (C.c_int, [_vp, C.c_uint64, C.POINTER(gd_result)]),
@@ -268,6 +271,21 @@ def make_queries(items):
         arr[i].kind = int(kind)
         arr[i].user_tag = int(it[5]) if len(it) > 5 else i
     return arr
+
+
+def gd_graph_create(ctx, A, B, kind, d_xa, d_xb, d_out):
+    """Graph of one device-resident query (device pointers as ints)."""
+    g = _vp()
+    _check(load().gd_graph_create(ctx, A, B, int(kind), d_xa, d_xb, d_out, C.byref(g)), ctx)
+    return g.value
+
+
+def gd_graph_launch(graph, stream=None, ctx=None):
+    _check(load().gd_graph_launch(graph, stream or None), ctx)
+
+
+def gd_graph_destroy(graph):
+    _check(load().gd_graph_destroy(graph))
 
 
 def gd_autotune(ctx, sample, reps=3) -> dict:

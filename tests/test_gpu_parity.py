@@ -403,6 +403,41 @@ def test_device_resident_query(G, ctx, oracle_mod):
     G.gd_mesh_destroy(mb)
 
 
+def test_graph_replays_match_calls(G, ctx, oracle_mod):
+    """A captured graph of one device-resident query, replayed after the
+    transforms are updated in place, gives the answers of the synchronous
+    calls; it is rebuilt when the tunables change."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(41)
+    A = synth.torus(1.0, 0.2, 64, 24)
+    B = synth.geosphere(10, 0.5, 1e-3, 4)
+    ma, mb = _mesh(G, ctx, A), _mesh(G, ctx, B)
+    xa = _rigid(rng, 0.2)
+    G.gd_min_distance(ctx, ma, mb, xa, _rigid(rng, 1.5))
+    dxa = torch.tensor(np.asarray(xa), dtype=torch.float64, device="cuda")
+    dxb = torch.zeros(12, dtype=torch.float64, device="cuda")
+    out = torch.zeros(10, dtype=torch.float64, device="cuda")
+    g = G.gd_graph_create(ctx, ma, mb, G.GD_MIN, dxa.data_ptr(), dxb.data_ptr(), out.data_ptr())
+    stream = torch.cuda.current_stream().cuda_stream
+    try:
+        for i in range(6):
+            xb = _rigid(rng, 1.5)
+            dxb.copy_(torch.tensor(np.asarray(xb), dtype=torch.float64))
+            torch.cuda.synchronize()
+            if i == 3:
+                G.gd_ctx_set_tunables(ctx, probes=16)
+            G.gd_graph_launch(g, stream, ctx)
+            torch.cuda.synchronize()
+            r = G.gd_result.from_buffer_copy(out.cpu().numpy().tobytes())
+            ref = G.gd_min_distance(ctx, ma, mb, xa, xb)
+            same_answer(r, ref, oracle_mod, A, xa, B, xb, "min")
+    finally:
+        G.gd_graph_destroy(g)
+        G.gd_ctx_set_tunables(ctx, probes=64)
+        G.gd_mesh_destroy(ma)
+        G.gd_mesh_destroy(mb)
+
+
 def test_overflow_grows_then_reports(G, oracle_mod):
     """Capacity faults are injected on the host: tiny queues must grow and
     still give the oracle's answer; a growth limit below the need reports
