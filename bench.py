@@ -455,7 +455,7 @@ def main():
                    "p50_ms": p50, "p99_ms": p99, "bvh_build_ms_per_mesh": build_ms,
                    "paper_context_ms": 0.38, "paper_context_gpu": "RTX 4090 (FP32 only)"},
         "e2e": {"value": statistics.mean(e2e_ms), "unit": "ms/query", "h2d_bytes_per_step": 192,
-                "d2h_bytes_per_step": 632, "p50_ms": sorted(e2e_ms)[len(e2e_ms) // 2]},
+                "d2h_bytes_per_step": 336, "p50_ms": sorted(e2e_ms)[len(e2e_ms) // 2]},
         "gpu_launches": args.steps * world,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": _traffic(), "peak_source": peak_kind,

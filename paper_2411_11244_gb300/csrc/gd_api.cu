@@ -6,6 +6,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstddef>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -16,11 +17,14 @@
 
 using namespace gd;
 
+// A single query's result and counters come back after every query (the
+// first kResultBytes); its statistics only when gd_get_stats asks.
 struct Mailbox {
     gd_result out;
-    StatsDev stats;
     unsigned ctr[kCtrWords];
+    StatsDev stats;
 };
+constexpr size_t kResultBytes = offsetof(Mailbox, stats);
 
 struct gd_mesh {
     gd_ctx* ctx = nullptr;
@@ -65,6 +69,7 @@ struct gd_ctx {
     gd_stats last{};
     bool stats_pending = false;  // last run was device-resident: stats still on the device
     unsigned ws_gen = 0;         // bumped whenever the work buffers or tunables change
+    unsigned pending_retries = 0;  // growth retries of the query whose stats are pending
     int last_grid = 0;
 };
 
@@ -258,12 +263,18 @@ void to_stats(const StatsDev& s, unsigned blocks, unsigned retries, gd_stats* o)
     std::memset(o, 0, sizeof(*o));
     o->levels = s.levels;
     for (int i = 0; i < 32; ++i) { o->front[i] = s.front[i]; o->slots[i] = s.slots[i]; }
-    o->pairs_tested = s.pairs_tested;
+    o->pairs_tested = 0;
+    o->alg_bytes = 0;
+    o->tri_pairs = 0;
+    o->refined = 0;
+    for (int i = 0; i < kAccWays; ++i) {
+        o->pairs_tested += s.acc_pairs[i];
+        o->alg_bytes += s.acc_bytes[i];
+        o->tri_pairs += s.acc_tri[i];
+        o->refined += s.acc_ref[i];
+    }
     o->leaf_pairs = s.leaf_pairs;
-    o->tri_pairs = s.tri_pairs;
     o->candidates = s.candidates;
-    o->refined = s.refined;
-    o->alg_bytes = s.alg_bytes;
     o->retries = retries;
     o->blocks = blocks;
     for (int i = 0; i < 32; ++i) o->level_ns[i] = s.level_ns[i];
@@ -312,11 +323,12 @@ gd_status run_single(gd_ctx* ctx, const gd_mesh* A, const gd_mesh* B, int kind, 
         int grid = grid_blocks(ctx, kind);
         a.work_ctas = single_work_ctas(ctx, grid);
         GD_CUDA(ctx, launch_query(kind, a, grid, ctx->stream));
-        GD_CUDA(ctx, cudaMemcpyAsync(ctx->mb_host, ctx->mb_dev, sizeof(Mailbox), cudaMemcpyDeviceToHost, ctx->stream));
+        GD_CUDA(ctx, cudaMemcpyAsync(ctx->mb_host, ctx->mb_dev, kResultBytes, cudaMemcpyDeviceToHost, ctx->stream));
         GD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         const Mailbox& m = *ctx->mb_host;
-        to_stats(m.stats, (unsigned)grid, retries, &ctx->last);
-        ctx->stats_pending = false;
+        ctx->stats_pending = true;
+        ctx->last_grid = grid;
+        ctx->pending_retries = retries;
         if (m.ctr[kCtrLastAbort]) return fail(ctx, GD_ERR_TIMEOUT, "a device-side wait timed out");
         if (m.ctr[kCtrBadIndex])
             return fail(ctx, GD_ERR_CUDA, "internal index check failed (sites " + std::to_string(m.ctr[kCtrBadIndex]) + ")");
@@ -554,7 +566,7 @@ GD_API gd_status gd_get_stats(gd_ctx* c, gd_stats* o) {
         cudaSetDevice(c->device);
         GD_CUDA(c, cudaDeviceSynchronize());
         GD_CUDA(c, cudaMemcpy(&c->mb_host->stats, &c->mb_dev->stats, sizeof(StatsDev), cudaMemcpyDeviceToHost));
-        to_stats(c->mb_host->stats, (unsigned)c->last_grid, 0, &c->last);
+        to_stats(c->mb_host->stats, (unsigned)c->last_grid, c->pending_retries, &c->last);
         c->stats_pending = false;
     }
     *o = c->last;
@@ -723,6 +735,7 @@ GD_API gd_status gd_query_device(gd_ctx* ctx, const gd_mesh* A, const gd_mesh* B
     GD_CUDA(ctx, launch_query((int)kind, a, grid, st));
     ctx->stats_pending = true;
     ctx->last_grid = grid;
+    ctx->pending_retries = 0;
     return GD_OK;
 }
 
@@ -852,7 +865,7 @@ GD_API gd_status gd_batch_query(gd_ctx* ctx, const gd_query* q, int64_t n, gd_re
                 if (e - b == 1) {
                     const int64_t i = cur[b];
                     gd_status r = run_single(ctx, q[i].a, q[i].b, kind, q[i].xa, q[i].xb, &out[i]);
-                    total_retries += ctx->last.retries;
+                    total_retries += ctx->pending_retries;
                     if (r != GD_OK && r != GD_ERR_OVERFLOW) return r;
                     continue;
                 }

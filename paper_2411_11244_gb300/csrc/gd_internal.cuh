@@ -108,13 +108,21 @@ enum : int {
     kCtrWords = 64,
 };
 
+// CTA totals of a launch are added to copy (CTA index mod kAccWays) of each
+// counter: one copy would queue the final atomics of 300 CTAs on one L2 word
+// (measured: the last CTA then left 12-17 us after the rest); the host sums
+// the copies
+constexpr int kAccWays = 16;
+
 struct StatsDev {
     unsigned levels;
     unsigned front[32];
     unsigned slots[32];
-    unsigned long long pairs_tested;
-    unsigned leaf_pairs, tri_pairs, candidates, refined;
-    unsigned long long alg_bytes;
+    unsigned long long acc_pairs[kAccWays];  // node pairs tested
+    unsigned long long acc_bytes[kAccWays];  // algorithmic bytes
+    unsigned acc_tri[kAccWays];              // float32 triangle pairs
+    unsigned acc_ref[kAccWays];              // float64 refinements
+    unsigned leaf_pairs, candidates;
     unsigned level_ns[32];  // device time of each level (CTA 0's view, barrier to barrier)
     unsigned phase_ns[12];  // setup, refit, probe, levels, leaf, refine, tail wait, select,
                             // finalize, total, -, -

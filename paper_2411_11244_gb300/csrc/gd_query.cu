@@ -1511,9 +1511,13 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
     if (lead) {
         StatsDev* S = A.stats;
         S->levels = 0;
-        S->pairs_tested = 0;
-        S->leaf_pairs = S->tri_pairs = S->candidates = S->refined = 0;
-        S->alg_bytes = 0;
+        for (int i = 0; i < kAccWays; ++i) {
+            S->acc_pairs[i] = 0;
+            S->acc_bytes[i] = 0;
+            S->acc_tri[i] = 0;
+            S->acc_ref[i] = 0;
+        }
+        S->leaf_pairs = S->candidates = 0;
         S->probes = 0;
         S->refits = 0;
         S->u_probe = 0.f;
@@ -1741,16 +1745,27 @@ done:
         __shared__ unsigned s_tri, s_ref;
         if (threadIdx.x == 0) { s_pairs = 0; s_bytes = 0; s_tri = 0; s_ref = 0; }
         __syncthreads();
-        atomicAdd(&s_pairs, pairs);
-        atomicAdd(&s_bytes, bytes);
-        atomicAdd(&s_tri, tripairs);
-        atomicAdd(&s_ref, refined);
+        // warp sums first, then one shared atomic per warp
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            pairs += __shfl_xor_sync(kFull, pairs, o);
+            bytes += __shfl_xor_sync(kFull, bytes, o);
+        }
+        tripairs = __reduce_add_sync(kFull, tripairs);
+        refined = __reduce_add_sync(kFull, refined);
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&s_pairs, pairs);
+            atomicAdd(&s_bytes, bytes);
+            atomicAdd(&s_tri, tripairs);
+            atomicAdd(&s_ref, refined);
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
-            atomicAdd(&A.stats->pairs_tested, s_pairs);
-            atomicAdd(&A.stats->alg_bytes, s_bytes);
-            atomicAdd(&A.stats->tri_pairs, s_tri);
-            atomicAdd(&A.stats->refined, s_ref);
+            const int w = blockIdx.x % kAccWays;
+            if (s_pairs) atomicAdd(&A.stats->acc_pairs[w], s_pairs);
+            if (s_bytes) atomicAdd(&A.stats->acc_bytes[w], s_bytes);
+            if (s_tri) atomicAdd(&A.stats->acc_tri[w], s_tri);
+            if (s_ref) atomicAdd(&A.stats->acc_ref[w], s_ref);
             // the last CTA out leaves the barrier and abort words clean for the
             // next launch and publishes this launch's abort flag
             __threadfence();
