@@ -218,6 +218,12 @@ gd_status size_for_batch(gd_ctx* c, long long m, long long share) {
     return GD_OK;
 }
 
+// Whether phase 0 of a single query may push its root pair itself: only when
+// the root needs no refit claim (refit off, or B deeper than one refit tree).
+int single_fuse_root(const gd_ctx* c, const gd_mesh* B) {
+    return (c->tun.refit_mode == 2 || B->L > kRefitH) ? 1 : 0;
+}
+
 // CTAs of a single-query launch that run the traversal: the others (one per
 // 8 probes, at most 1/8 of the grid) run the greedy probes in the background.
 unsigned single_work_ctas(const gd_ctx* c, int grid) {
@@ -322,6 +328,7 @@ gd_status run_single(gd_ctx* ctx, const gd_mesh* A, const gd_mesh* B, int kind, 
         a.out = &ctx->mb_dev->out;
         int grid = grid_blocks(ctx, kind);
         a.work_ctas = single_work_ctas(ctx, grid);
+        a.fuse_root = single_fuse_root(ctx, B);
         GD_CUDA(ctx, launch_query(kind, a, grid, ctx->stream));
         GD_CUDA(ctx, cudaMemcpyAsync(ctx->mb_host, ctx->mb_dev, kResultBytes, cudaMemcpyDeviceToHost, ctx->stream));
         GD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -732,6 +739,7 @@ GD_API gd_status gd_query_device(gd_ctx* ctx, const gd_mesh* A, const gd_mesh* B
     cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
     int grid = grid_blocks(ctx, (int)kind);
     a.work_ctas = single_work_ctas(ctx, grid);
+    a.fuse_root = single_fuse_root(ctx, B);
     GD_CUDA(ctx, launch_query((int)kind, a, grid, st));
     ctx->stats_pending = true;
     ctx->last_grid = grid;
@@ -769,6 +777,7 @@ gd_status graph_build(gd_graph* g) {
     a.out = g->d_out;
     const int grid = grid_blocks(ctx, (int)g->kind);
     a.work_ctas = single_work_ctas(ctx, grid);
+    a.fuse_root = single_fuse_root(ctx, g->B);
     if (g->exec) {
         cudaGraphExecDestroy(g->exec);
         g->exec = nullptr;

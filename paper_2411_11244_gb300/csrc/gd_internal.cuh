@@ -166,6 +166,8 @@ struct KArgs {
     int k_max;
     long long timeout_ns;
     unsigned q_budget;          // batch: entries one query may push per level (0: no limit)
+    int fuse_root;              // single query, no refit claim at the root: phase 0 pushes
+                                // the root pair (phase 1 and its barrier are skipped)
     unsigned work_ctas;         // CTAs [0, work_ctas) run the traversal and meet at the
                                 // grid barriers; the rest run background probes (0: all)
 };

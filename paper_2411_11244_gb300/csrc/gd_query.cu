@@ -1504,9 +1504,26 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
 
     // phase 0
     if (threadIdx.x == 0) cta().ready = 0;
-    if (blockIdx.x == 0)
+    if (blockIdx.x == 0) {
         for (int i = threadIdx.x; i < kCtrReset; i += blockDim.x) A.ctr[i] = 0u;
+        if (A.fuse_root) __syncthreads();  // cleared before the root is pushed below
+    }
     for (int q = (int)gfirst; q < A.nq; q += (int)gstride) setup_query(A, q, KIND);
+    if (A.fuse_root && gfirst == 0) {
+        // one query whose root needs no refit claim: the thread that set it up
+        // pushes its root pair now, and phase 1 with its barrier is skipped
+        const QState& s = A.qs[0];
+        const int LA = s.A->L, LB = s.B->L;
+        const Item it = {1u, 1u, KIND == 0 ? 0.f : FLT_MAX, 0u};
+        if (LA == 0 && LB == 0) {
+            A.leafq[0] = it;
+            A.ctr[kCtrLeaf] = 1u;
+        } else {
+            A.front0[0] = it;
+            A.ctr[kCtrCnt] = 1u;
+            A.ctr[kCtrRem] = (unsigned)(LA + LB);
+        }
+    }
     for (unsigned long long i = gfirst; i < A.n_slot_of; i += gstride) A.slot_of[i] = kNoSlot;
     if (lead) {
         StatsDev* S = A.stats;
@@ -1535,6 +1552,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
     if (!sync(A)) goto done;
 
     // phase 1: root pairs
+    if (A.fuse_root) goto levels;
     for (int q = (int)gfirst; q < A.nq; q += (int)gstride) {
         const QState& s = A.qs[q];
         int LA = s.A->L, LB = s.B->L;
@@ -1554,6 +1572,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
         }
     }
     if (!sync(A)) goto done;
+levels:
     lap(0);
 
     // phase 2: BVTT levels
@@ -1604,7 +1623,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
             }
             if (lead) A.stats->probes += P;
             if (!sync(A)) goto done;
-            if (lead && !reprobe) A.stats->u_probe = __uint_as_float(ld_relaxed(&A.qs[0].U));
+            if (lead && !reprobe) A.stats->u_probe = A.nq == 1 ? __uint_as_float(cta().U) : 0.f;
             lap(2);
         }
         unsigned rmax = cta().ctr[kCtrRem + level % 3];
@@ -1617,7 +1636,9 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
             if (level < 32) {
                 A.stats->front[level] = n;
                 A.stats->slots[level] = (unsigned)s;
-                A.stats->u_level[level] = __uint_as_float(ld_relaxed(&A.qs[0].U));
+                // query 0's bound as this CTA knows it (no global round trip
+                // on the lead's way into the level)
+                A.stats->u_level[level] = A.nq == 1 ? __uint_as_float(cta().U) : 0.f;
             }
             A.stats->levels = level + 1;
         }
