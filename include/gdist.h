@@ -95,7 +95,7 @@ typedef struct {
 /* Traversal tunables of a context.  Zero fields keep the current value. */
 typedef struct {
     int64_t work_target;   /* C of Section 6: a level expands n front entries by
-                              k levels per side with n * 4^k < C (default 2^18) */
+                              k levels per side with n * 4^k < C (default 2^17) */
     int32_t k_max;         /* cap on k (default 6) */
     int32_t blocks_per_sm; /* persistent CTAs per SM (default: occupancy limit) */
     int64_t front_capacity;/* BVTT entries per front buffer (default 2^24) */

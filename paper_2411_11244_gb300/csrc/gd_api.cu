@@ -435,7 +435,7 @@ GD_API gd_status gd_ctx_create(int device, gd_ctx** out) {
         delete c;
         return GD_ERR_CUDA;
     }
-    c->tun.work_target = 1ll << 18;
+    c->tun.work_target = 1ll << 17;
     c->tun.k_max = 6;
     c->tun.blocks_per_sm = 0;
     c->tun.front_capacity = 1ll << 24;
