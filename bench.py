@@ -222,6 +222,78 @@ def bench_ablation(G, ctx, ma, mb, xa, xbs, frames=4):
     }
 
 
+def bench_deformable(G, ctx, ma, frames=8):
+    """The rings with a deforming B (Section 8's Deformable scene): per frame,
+    gd_mesh_update uploads B's warped vertices and refits its BVH on the
+    device, then one min-distance query runs.  Vertices come from device
+    memory (a simulation on the GPU) or from pinned host memory; ms per
+    frame are means over the frames (synchronous calls, wall clock)."""
+    import torch
+    from paper_2411_11244_gb300 import synth
+    A, tb, xa, xbs, frame_verts = synth.config_deforming_rings(frames=frames)
+    mb = G.gd_mesh_create(ctx, A[0], tb)
+    G.gd_bvh_build(mb, ctx=ctx)
+    host = [torch.from_numpy(frame_verts(i)).pin_memory() for i in range(frames)]
+    dev = [h.cuda() for h in host]
+    torch.cuda.synchronize()
+    G.gd_mesh_update(mb, dev[0], ctx=ctx)
+    G.gd_min_distance(ctx, ma, mb, xa, xbs[0])
+
+    def run(src):
+        upd, qry, d = [], [], []
+        for i in range(frames):
+            t0 = time.perf_counter()
+            G.gd_mesh_update(mb, src[i], ctx=ctx)
+            t1 = time.perf_counter()
+            r = G.gd_min_distance(ctx, ma, mb, xa, xbs[i])
+            t2 = time.perf_counter()
+            assert r.status == 0
+            upd.append(1000.0 * (t1 - t0))
+            qry.append(1000.0 * (t2 - t1))
+            d.append(r.d)
+        return statistics.mean(upd), statistics.mean(qry), d
+
+    u_dev, q_dev, d_dev = run(dev)
+    u_host, q_host, d_host = run([h.numpy() for h in host])
+    G.gd_mesh_destroy(mb)
+    return {
+        "workload": f"rings: 2 x {len(tb)} tris, B warped per frame (amplitude 0.01, surfaces apart)",
+        "frames": frames,
+        "update_ms_device_src": u_dev, "update_ms_host_src": u_host,
+        "query_ms": statistics.mean([q_dev, q_host]),
+        "frame_ms_device_src": u_dev + q_dev, "frame_ms_host_src": u_host + q_host,
+        "h2d_bytes_per_frame_host_src": int(host[0].numel() * 4),
+        "same_answers": d_dev == d_host, "min_d": min(d_dev),
+    }
+
+
+def bench_naive(G, ctx, ma, mb, xa, xbs, frames=2, timeout_s=10.0):
+    """Section 8's naive GPU comparator on the rings frames: one thread per
+    triangle of A, depth-first walk of B's BVH, one global atomic bound.
+    Against the front traversal on the same frames: ms per query, BVTT nodes
+    visited (node box tests against node pairs tested) and the walk length
+    of the busiest thread.  Each naive launch stops at timeout_s."""
+    out = []
+    for xb in xbs[1:frames + 1]:
+        t0 = time.perf_counter()
+        r = G.gd_min_distance(ctx, ma, mb, xa, xb)
+        t_front = 1000.0 * (time.perf_counter() - t0)
+        pairs = G.gd_get_stats(ctx)["pairs_tested"]
+        t0 = time.perf_counter()
+        n = G.gd_naive_query(ctx, ma, mb, G.GD_MIN, xa, xb, timeout_ns=int(timeout_s * 1e9))
+        t_naive = 1000.0 * (time.perf_counter() - t0)
+        out.append({"front_ms": t_front, "naive_ms": t_naive, "naive_status": n["status"],
+                    "front_pairs_tested": pairs, "naive_node_tests": n["node_tests"],
+                    "naive_leaf_tests": n["leaf_tests"], "naive_max_thread_tests": n["max_thread_tests"],
+                    "d_front": r.d, "d_naive": n["d"]})
+    return {
+        "frames": out,
+        "speedup_front_over_naive": statistics.mean(f["naive_ms"] / f["front_ms"] for f in out),
+        "nodes_ratio_naive_over_front": statistics.mean(f["naive_node_tests"] / f["front_pairs_tested"] for f in out),
+        "timeouts": sum(1 for f in out if f["naive_status"] != 0), "timeout_s": timeout_s,
+    }
+
+
 def bench_served(G, ctx, rates=(1000, 3000, 10000, 30000, 100000), n_req=1500, seed=0):
     """A pool of 64 meshes (tori, geodesic spheres, gears; 1e3..4e6 triangles,
     BVHs resident) and a stream of random mesh pairs and transforms arriving
@@ -346,6 +418,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-ablation", action="store_true")
+    ap.add_argument("--no-deformable", action="store_true")
+    ap.add_argument("--no-naive", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -468,6 +542,10 @@ def main():
     }
     if not args.no_ablation:
         line["ablation"] = bench_ablation(G, ctx, ma, mb, xa, xbs)
+    if not args.no_naive:
+        line["naive"] = bench_naive(G, ctx, ma, mb, xa, xbs)
+    if not args.no_deformable:
+        line["deformable"] = bench_deformable(G, ctx, ma)
     G.gd_mesh_destroy(ma)
     G.gd_mesh_destroy(mb)
     if not args.no_batched:

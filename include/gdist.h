@@ -79,6 +79,16 @@ typedef struct {
     uint32_t status, flags;
 } gd_result;
 
+/* Answer of the naive comparator (gd_naive_query). */
+typedef struct {
+    double d;                  /* float32 distance (squared in float32, root taken in float64) */
+    uint64_t node_tests;       /* (triangle of A, node of B) box tests: the BVTT nodes visited */
+    uint64_t leaf_tests;       /* triangle pairs evaluated */
+    uint64_t max_thread_tests; /* most box tests of one thread (load imbalance) */
+    uint32_t status;           /* GD_OK, or GD_ERR_TIMEOUT (d and the counts are partial) */
+    uint32_t pad;
+} gd_naive_result;
+
 /* One query of a batch or of the server. */
 typedef struct {
     const gd_mesh *a, *b;
@@ -194,6 +204,21 @@ GD_API gd_status gd_mesh_create(gd_ctx *ctx, const float *verts, int64_t nv, con
  * boxes up to the root.  Every box is tight (Section 4, tightness lemma).
  * Synchronous.  GD_ERR_INVALID_ARG on bad indices or non-finite vertices. */
 GD_API gd_status gd_bvh_build(gd_mesh *mesh, const gd_build_opts *opts);
+/* Deformable meshes (Section 8: the BVH is refit on the fly when vertices
+ * move).  Replaces the vertex positions of a built mesh (same count nv, same
+ * triangles) and refits its tree on the device: the leaf order of the last
+ * gd_bvh_build is kept, leaf boxes are recomputed as exact bounds of the new
+ * vertices and every inner box as the union of its children, so every box is
+ * tight again and queries stay exact.  Only the culling efficiency depends on
+ * how far the mesh moved since the build (call gd_bvh_build to re-sort).
+ * verts: nv x 3 float32, host or device memory (read before the call
+ * returns).  Synchronous on the context's stream; queries on the context's
+ * stream see the new positions.  The caller must not update a mesh while a
+ * query that uses it is in flight on another stream (a server's, a captured
+ * graph's).  GD_ERR_NOT_BUILT if the mesh has no tree; GD_ERR_INVALID_ARG if
+ * nv differs from the mesh's or a coordinate is not finite (the mesh is then
+ * left unbuilt until the next successful update or build). */
+GD_API gd_status gd_mesh_update(gd_mesh *mesh, const float *verts, int64_t nv);
 GD_API void gd_mesh_destroy(gd_mesh *mesh);
 /* Tree depth L (leaves = 2^L) and triangle count of a built mesh. */
 GD_API gd_status gd_mesh_info(const gd_mesh *mesh, int32_t *levels, int64_t *triangles);
@@ -212,6 +237,19 @@ GD_API gd_status gd_min_distance(gd_ctx *ctx, const gd_mesh *A, const gd_mesh *B
 /* Maximum distance D_max (Eq. 2); same contract as gd_min_distance. */
 GD_API gd_status gd_max_distance(gd_ctx *ctx, const gd_mesh *A, const gd_mesh *B, const double xa[12],
                                  const double xb[12], gd_result *out);
+/* The naive GPU comparator of Section 8 (Performance): one thread per
+ * triangle of A walks B's BVH depth first (nearer child first), pruning with
+ * the conventional box bounds (Eqs. 5-8) against one global running bound
+ * read and updated with atomics; float32 throughout.  Not the product path:
+ * it exists to measure the BVTT nodes such a walk visits and its load
+ * imbalance against the front traversal.  Same meshes and transforms as
+ * gd_min_distance; kind GD_MIN or GD_MAX.  timeout_ns > 0 bounds the launch
+ * (0: the context's timeout): threads stop at the deadline and the call
+ * returns GD_ERR_TIMEOUT with out filled in (partial counts, d an upper
+ * (min) or lower (max) bound).  Synchronous. */
+GD_API gd_status gd_naive_query(gd_ctx *ctx, const gd_mesh *A, const gd_mesh *B, gd_kind kind,
+                                const double xa[12], const double xb[12], int64_t timeout_ns,
+                                gd_naive_result *out);
 /* Device-resident form: d_xa, d_xb are device pointers to 12 doubles each,
  * d_out a device pointer to one gd_result; stream is a cudaStream_t (NULL =
  * the context's stream).  Asynchronous (no host synchronisation); the

@@ -34,9 +34,12 @@ struct gd_mesh {
     int32_t* d_tris = nullptr;
     float* d_box = nullptr;
     float4* d_tri = nullptr;
+    unsigned* d_order = nullptr;  // original index of each sorted triangle (leaf order)
     MeshDev* d_desc = nullptr;
     MeshDev h_desc{};
-    bool built = false;
+    unsigned* d_flags = nullptr;  // validation flags of gd_mesh_update
+    bool tree = false;            // box, tri and L hold a sorted tree (refit may run)
+    bool built = false;           // ... and its boxes bound the current vertices
 };
 
 struct gd_ctx {
@@ -66,6 +69,7 @@ struct gd_ctx {
     long long cap_slots = 0;
     unsigned* slot_of = nullptr;  // refit-root tables
     long long cap_table = 0;
+    unsigned long long* naive_ws = nullptr;  // scratch of the naive comparator
     gd_stats last{};
     bool stats_pending = false;  // last run was device-resident: stats still on the device
     unsigned ws_gen = 0;         // bumped whenever the work buffers or tunables change
@@ -462,6 +466,7 @@ GD_API void gd_ctx_destroy(gd_ctx* c) {
     cudaFree(c->qs); cudaFree(c->qin_dev); cudaFree(c->out_dev);
     cudaFreeHost(c->qin_host); cudaFreeHost(c->out_host);
     cudaFree(c->slot_of);
+    cudaFree(c->naive_ws);
     cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -615,9 +620,10 @@ GD_API gd_status gd_bvh_build(gd_mesh* m, const gd_build_opts* opts) {
     }
     int L = 0;
     while ((2ll << L) <= m->nt) ++L;
-    cudaFree(m->d_box); cudaFree(m->d_tri);
-    m->d_box = nullptr; m->d_tri = nullptr;
+    cudaFree(m->d_box); cudaFree(m->d_tri); cudaFree(m->d_order);
+    m->d_box = nullptr; m->d_tri = nullptr; m->d_order = nullptr;
     m->built = false;
+    m->tree = false;
     BuildBuffers b{};
     b.verts = m->d_verts; b.tris = m->d_tris; b.nv = m->nv; b.nt = m->nt; b.L = L; b.morton_bits = bits;
     std::vector<void*> tmp;
@@ -637,9 +643,11 @@ GD_API gd_status gd_bvh_build(gd_mesh* m, const gd_build_opts* opts) {
 #undef GD_ALLOC
     cudaError_t e = cudaMalloc(&m->d_box, sizeof(float) * 6 * (2ull << L));
     if (e == cudaSuccess) e = cudaMalloc(&m->d_tri, sizeof(float4) * 3 * m->nt);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_order, sizeof(unsigned) * m->nt);
     if (e != cudaSuccess) { cleanup(); return cuda_fail(ctx, e, "gd_bvh_build alloc"); }
     b.box = m->d_box;
     b.tri = m->d_tri;
+    b.order = m->d_order;
     unsigned flags[8] = {0};
     e = build_validate(b, ctx->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(flags, b.flags, sizeof(flags), cudaMemcpyDeviceToHost, ctx->stream);
@@ -665,6 +673,39 @@ GD_API gd_status gd_bvh_build(gd_mesh* m, const gd_build_opts* opts) {
     GD_CUDA(ctx, cudaMemcpyAsync(m->d_desc, &m->h_desc, sizeof(MeshDev), cudaMemcpyHostToDevice, ctx->stream));
     GD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     m->built = true;
+    m->tree = true;
+    return GD_OK;
+}
+
+GD_API gd_status gd_mesh_update(gd_mesh* m, const float* verts, int64_t nv) {
+    if (!m) return GD_ERR_INVALID_ARG;
+    gd_ctx* ctx = m->ctx;
+    if (!verts) return fail(ctx, GD_ERR_INVALID_ARG, "NULL vertices");
+    if (nv != m->nv) return fail(ctx, GD_ERR_INVALID_ARG, "vertex count differs from the mesh's");
+    if (!m->tree) return fail(ctx, GD_ERR_NOT_BUILT, "BVH not built (call gd_bvh_build)");
+    cudaSetDevice(ctx->device);
+    m->built = false;
+    if (!m->d_flags) GD_CUDA(ctx, cudaMalloc(&m->d_flags, 64 * sizeof(unsigned)));
+    // host or device source: with unified addressing the copy kind follows the pointer
+    GD_CUDA(ctx, cudaMemcpyAsync(m->d_verts, verts, sizeof(float) * 3 * nv, cudaMemcpyDefault, ctx->stream));
+    BuildBuffers b{};
+    b.verts = m->d_verts; b.tris = m->d_tris; b.nv = m->nv; b.nt = m->nt; b.L = m->L;
+    b.box = m->d_box; b.tri = m->d_tri; b.order = m->d_order; b.flags = m->d_flags;
+    // the refit writes max |coordinate| straight into the device descriptor
+    float* P_dev = reinterpret_cast<float*>(reinterpret_cast<char*>(m->d_desc) + offsetof(MeshDev, P));
+    GD_CUDA(ctx, build_refit(b, P_dev, ctx->stream));
+    unsigned flags[14];
+    GD_CUDA(ctx, cudaMemcpyAsync(flags, b.flags, sizeof(flags), cudaMemcpyDeviceToHost, ctx->stream));
+    GD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (flags[1]) return fail(ctx, GD_ERR_INVALID_ARG, "non-finite vertex coordinate (mesh left unbuilt)");
+    float P = 0.f;
+    for (int i = 0; i < 6; ++i) {
+        float x;
+        std::memcpy(&x, &flags[8 + i], sizeof(float));
+        P = std::max(P, std::fabs(x));
+    }
+    m->h_desc.P = P;
+    m->built = true;
     return GD_OK;
 }
 
@@ -675,6 +716,7 @@ GD_API void gd_mesh_destroy(gd_mesh* m) {
         cudaStreamSynchronize(m->ctx->stream);
     }
     cudaFree(m->d_verts); cudaFree(m->d_tris); cudaFree(m->d_box); cudaFree(m->d_tri); cudaFree(m->d_desc);
+    cudaFree(m->d_order); cudaFree(m->d_flags);
     delete m;
 }
 
@@ -701,6 +743,55 @@ GD_API gd_status gd_mesh_download(const gd_mesh* m, float* boxes, int32_t* order
             order[j] = id;
         }
     }
+    return GD_OK;
+}
+
+GD_API gd_status gd_naive_query(gd_ctx* ctx, const gd_mesh* A, const gd_mesh* B, gd_kind kind, const double xa[12],
+                                const double xb[12], int64_t timeout_ns, gd_naive_result* out) {
+    if (!ctx) return GD_ERR_INVALID_ARG;
+    if (!out || !xa || !xb) return fail(ctx, GD_ERR_INVALID_ARG, "NULL argument");
+    if (kind != GD_MIN && kind != GD_MAX) return fail(ctx, GD_ERR_INVALID_ARG, "kind must be GD_MIN or GD_MAX");
+    gd_status s = check_pair(ctx, A, B);
+    if (s != GD_OK) return s;
+    std::string why;
+    if (!xform_ok(xa, &why) || !xform_ok(xb, &why)) return fail(ctx, GD_ERR_INVALID_ARG, why);
+    cudaSetDevice(ctx->device);
+    if (!ctx->naive_ws) GD_CUDA(ctx, cudaMalloc(&ctx->naive_ws, sizeof(unsigned long long) * kNaiveWords));
+    NaiveArgs g{};
+    g.triA = A->d_tri; g.TA = A->nt;
+    g.boxB = B->d_box; g.triB = B->d_tri; g.TB = B->nt; g.LB = B->L;
+    // A-local -> B-local: M = R_B^T R_A, c = R_B^T (t_A - t_B), in float64, then rounded
+    double cmax = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) {
+            double m = 0.0;
+            for (int k = 0; k < 3; ++k) m += xb[4 * k + i] * xa[4 * k + j];
+            g.R[3 * i + j] = (float)m;
+        }
+        double c = 0.0;
+        for (int k = 0; k < 3; ++k) c += xb[4 * k + i] * (xa[4 * k + 3] - xb[4 * k + 3]);
+        g.t[i] = (float)c;
+        cmax = std::max(cmax, std::fabs(c));
+    }
+    // the float32 map is off by a few units in the last place of 3 P_A + |c|
+    g.E = (float)std::ldexp(3.0 * (double)A->h_desc.P + cmax, -20);
+    g.ws = ctx->naive_ws;
+    g.timeout_ns = timeout_ns > 0 ? timeout_ns : ctx->tun.timeout_ns;
+    GD_CUDA(ctx, launch_naive(kind, g, ctx->stream));
+    unsigned long long w[kNaiveWords];
+    GD_CUDA(ctx, cudaMemcpyAsync(w, ctx->naive_ws, sizeof(w), cudaMemcpyDeviceToHost, ctx->stream));
+    GD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    float u;
+    const unsigned ub = (unsigned)(w[kNaiveU] & 0xffffffffull);
+    std::memcpy(&u, &ub, sizeof(u));
+    out->d = std::sqrt((double)u);
+    out->node_tests = w[kNaiveTests];
+    out->leaf_tests = w[kNaiveLeaves];
+    out->max_thread_tests = w[kNaiveMaxTests];
+    out->status = w[kNaiveBad] ? GD_ERR_CUDA : w[kNaiveTimeout] ? GD_ERR_TIMEOUT : GD_OK;
+    out->pad = 0;
+    if (w[kNaiveBad]) return fail(ctx, GD_ERR_CUDA, "naive walk outgrew its stack");
+    if (w[kNaiveTimeout]) return fail(ctx, GD_ERR_TIMEOUT, "naive query passed its deadline");
     return GD_OK;
 }
 

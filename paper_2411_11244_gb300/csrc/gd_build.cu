@@ -3,7 +3,8 @@
 // order), 2^L leaves of one or two consecutive sorted triangles, exact leaf
 // boxes, and a level-by-level union up to the root.  Leaf boxes are exact
 // bounds of their vertices, so every box is tight (Section 4: tight leaves
-// make every node tight).
+// make every node tight).  Refit for moved vertices (Section 8, deformable
+// scenes): the same leaf and union kernels over the stored leaf order.
 #include <cfloat>
 #include <cstdint>
 
@@ -228,46 +229,101 @@ __global__ void k_rs_scatter(const unsigned long long* kin, const unsigned* vin,
     }
 }
 
-// leaves: leaf l owns sorted triangles [floor(l T / 2^L), floor((l+1) T / 2^L))
-__global__ void k_leaves(const float* verts, const int32_t* tris, long long nt, int L, const unsigned* order,
-                         float4* tri, float* box) {
-    const long long nleaf = 1ll << L;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x; l < nleaf; l += stride) {
-        long long s = (long long)(((unsigned long long)l * (unsigned long long)nt) >> L);
-        long long e = (long long)(((unsigned long long)(l + 1) * (unsigned long long)nt) >> L);
-        float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
-        for (long long j = s; j < e; ++j) {
-            unsigned id = order[j];
-            float v[9];
-            for (int k = 0; k < 3; ++k)
-                for (int c = 0; c < 3; ++c) {
-                    float x = verts[3ll * tris[3ll * id + k] + c];
-                    v[3 * k + c] = x;
-                    lo[c] = fminf(lo[c], x);
-                    hi[c] = fmaxf(hi[c], x);
-                }
-            tri[3 * j] = make_float4(v[0], v[1], v[2], v[3]);
-            tri[3 * j + 1] = make_float4(v[4], v[5], v[6], v[7]);
-            tri[3 * j + 2] = make_float4(v[8], __int_as_float((int)id), 0.f, 0.f);
+constexpr int kTreeLevels = 8;  // tree levels one CTA reduces (2^8 = 256 nodes in, one out)
+
+// Subtree union shared by the two tree kernels: on entry thread i holds node
+// box (lo, hi) of the CTA's 2^levels consecutive nodes of depth d (heap ids
+// from first = 2^d + CTA offset); each step makes node k of the level above
+// the union of its children 2k, 2k+1 (Section 4: tight children make a tight
+// parent) and stores it.  At the root (depth 0) the root box goes to
+// root_out[0..5] and max |coordinate| to *P_out, when given.
+__device__ __forceinline__ void reduce_subtree(float* box, long long first, int levels, float lo[3], float hi[3],
+                                               float* root_out, float* P_out) {
+    __shared__ float sb[6 << kTreeLevels];
+    const int i = threadIdx.x;
+    for (int s = 1; s <= levels; ++s) {
+        sb[6 * i + 0] = lo[0]; sb[6 * i + 1] = lo[1]; sb[6 * i + 2] = lo[2];
+        sb[6 * i + 3] = hi[0]; sb[6 * i + 4] = hi[1]; sb[6 * i + 5] = hi[2];
+        __syncthreads();
+        const int n = (int)blockDim.x >> s;
+        if (i < n) {
+            const float* l = sb + 12 * i;
+            const float* r = l + 6;
+            lo[0] = fminf(l[0], r[0]); lo[1] = fminf(l[1], r[1]); lo[2] = fminf(l[2], r[2]);
+            hi[0] = fmaxf(l[3], r[3]); hi[1] = fmaxf(l[4], r[4]); hi[2] = fmaxf(l[5], r[5]);
         }
-        float* b = box + 6 * ((1ll << L) + l);
-        b[0] = lo[0]; b[1] = lo[1]; b[2] = lo[2];
-        b[3] = hi[0]; b[4] = hi[1]; b[5] = hi[2];
+        __syncthreads();
+        if (i < n) {
+            float* o = box + 6 * ((first >> s) + i);
+            o[0] = lo[0]; o[1] = lo[1]; o[2] = lo[2];
+            o[3] = hi[0]; o[4] = hi[1]; o[5] = hi[2];
+        }
+    }
+    if ((first >> levels) == 1 && i == 0) {
+        if (root_out)
+            for (int c = 0; c < 3; ++c) { root_out[c] = lo[c]; root_out[3 + c] = hi[c]; }
+        if (P_out) {
+            float P = 0.f;
+            for (int c = 0; c < 3; ++c) P = fmaxf(P, fmaxf(fabsf(lo[c]), fabsf(hi[c])));
+            *P_out = P;
+        }
     }
 }
 
-// one level: node i in [2^d, 2^(d+1)) gets the union of nodes 2i, 2i+1
-__global__ void k_reduce_level(float* box, int d) {
-    const long long n = 1ll << d;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
-        long long i = n + k;
-        const float* l = box + 12 * i;
-        const float* r = l + 6;
-        float* o = box + 6 * i;
-        o[0] = fminf(l[0], r[0]); o[1] = fminf(l[1], r[1]); o[2] = fminf(l[2], r[2]);
-        o[3] = fmaxf(l[3], r[3]); o[4] = fmaxf(l[4], r[4]); o[5] = fmaxf(l[5], r[5]);
+// leaves: leaf l owns sorted triangles [floor(l T / 2^L), floor((l+1) T / 2^L)).
+// One thread per leaf, 2^levels leaves per CTA: gather the leaf's triangles in
+// sorted order (order[j] = original index of sorted triangle j), store them
+// and the exact leaf box, then the CTA's subtree above its leaves.
+// bad != nullptr: a non-finite coordinate sets *bad (the refit's check; the
+// build validated the vertices before sorting).
+__global__ void k_leaves(const float* verts, const int32_t* tris, long long nt, int L, const unsigned* order,
+                         float4* tri, float* box, int levels, unsigned* bad, float* root_out, float* P_out) {
+    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // grid x block = 2^L exactly
+    const long long s = (long long)(((unsigned long long)l * (unsigned long long)nt) >> L);
+    const long long e = (long long)(((unsigned long long)(l + 1) * (unsigned long long)nt) >> L);
+    float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    bool finite = true;
+    for (long long j = s; j < e; ++j) {
+        const unsigned id = order[j];
+        float v[9];
+        for (int k = 0; k < 3; ++k)
+            for (int c = 0; c < 3; ++c) {
+                const float x = verts[3ll * tris[3ll * id + k] + c];
+                finite = finite && isfinite(x);
+                v[3 * k + c] = x;
+                lo[c] = fminf(lo[c], x);
+                hi[c] = fmaxf(hi[c], x);
+            }
+        tri[3 * j] = make_float4(v[0], v[1], v[2], v[3]);
+        tri[3 * j + 1] = make_float4(v[4], v[5], v[6], v[7]);
+        tri[3 * j + 2] = make_float4(v[8], __int_as_float((int)id), 0.f, 0.f);
+    }
+    if (bad && __syncthreads_or(!finite) && threadIdx.x == 0) atomicOr(bad, 1u);
+    float* b = box + 6 * ((1ll << L) + l);
+    b[0] = lo[0]; b[1] = lo[1]; b[2] = lo[2];
+    b[3] = hi[0]; b[4] = hi[1]; b[5] = hi[2];
+    reduce_subtree(box, (1ll << L) + (long long)blockIdx.x * blockDim.x, levels, lo, hi, root_out, P_out);
+}
+
+// levels above depth d: each CTA loads 2^levels consecutive nodes of depth d
+// and reduces them (grid x block = 2^d exactly)
+__global__ void k_reduce_up(float* box, int d, int levels, float* root_out, float* P_out) {
+    const long long first = (1ll << d) + (long long)blockIdx.x * blockDim.x;
+    const float* b = box + 6 * (first + threadIdx.x);
+    float lo[3] = {b[0], b[1], b[2]}, hi[3] = {b[3], b[4], b[5]};
+    reduce_subtree(box, first, levels, lo, hi, root_out, P_out);
+}
+
+// all boxes from the sorted order: leaves plus the lowest levels, then one
+// launch per further kTreeLevels levels (three launches for 2^22 leaves)
+void tree_boxes(const float* verts, const int32_t* tris, long long nt, int L, const unsigned* order, float4* tri,
+                float* box, unsigned* bad, float* root_out, float* P_out, cudaStream_t st) {
+    int lv = L < kTreeLevels ? L : kTreeLevels;
+    k_leaves<<<(unsigned)(1ll << (L - lv)), 1u << lv, 0, st>>>(verts, tris, nt, L, order, tri, box, lv, bad,
+                                                                 root_out, P_out);
+    for (int d = L - lv; d > 0; d -= lv) {
+        lv = d < kTreeLevels ? d : kTreeLevels;
+        k_reduce_up<<<(unsigned)(1ll << (d - lv)), 1u << lv, 0, st>>>(box, d, lv, root_out, P_out);
     }
 }
 
@@ -309,8 +365,17 @@ cudaError_t build_tree(const BuildBuffers& b, cudaStream_t st) {
                                                              b.vals[cur ^ 1], b.nt, 8 * p, b.hist);
         cur ^= 1;
     }
-    k_leaves<<<grid_for(1ll << b.L, 256), 256, 0, st>>>(b.verts, b.tris, b.nt, b.L, b.vals[cur], b.tri, b.box);
-    for (int d = b.L - 1; d >= 0; --d) k_reduce_level<<<grid_for(1ll << d, 256), 256, 0, st>>>(b.box, d);
+    cudaError_t e = cudaMemcpyAsync(b.order, b.vals[cur], sizeof(unsigned) * b.nt, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+    tree_boxes(b.verts, b.tris, b.nt, b.L, b.order, b.tri, b.box, nullptr, nullptr, nullptr, st);
+    return cudaGetLastError();
+}
+
+cudaError_t build_refit(const BuildBuffers& b, float* P_out, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(b.flags, 0, 16 * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    tree_boxes(b.verts, b.tris, b.nt, b.L, b.order, b.tri, b.box, b.flags + 1,
+               reinterpret_cast<float*>(b.flags + 8), P_out, st);
     return cudaGetLastError();
 }
 

@@ -17,6 +17,7 @@ struct BuildBuffers {
     int morton_bits;
     float* box;           // 6 * 2^(L+1) floats, device
     float4* tri;          // 3 * nt float4, device
+    unsigned* order;      // nt, device: original index of each sorted triangle (kept for refits)
     unsigned* flags;      // device: [0] bad index, [1] non-finite vertex, [2..8] bounds scratch
     unsigned long long* keys[2];  // nt each, device
     unsigned* vals[2];            // nt each, device
@@ -28,6 +29,40 @@ size_t build_hist_words(long long nt);
 cudaError_t build_validate(const BuildBuffers& b, cudaStream_t stream);
 // the rest of the build; only after build_validate reported clean flags
 cudaError_t build_tree(const BuildBuffers& b, cudaStream_t stream);
+// refit of a built tree after its vertices moved (verts, tris, L, order, tri,
+// box, flags): stored triangles and leaf boxes from the new vertices, then the
+// unions up to the root.  flags[1] != 0 afterwards: a referenced coordinate is
+// not finite; flags[8..13]: the root box (float bits); *P_out (device, may be
+// null): max |coordinate| of the root box.
+cudaError_t build_refit(const BuildBuffers& b, float* P_out, cudaStream_t stream);
+
+// ---- naive comparator (gd_naive.cu)
+// words of its device scratch (uint64 each)
+enum : int {
+    kNaiveU = 0,         // running bound: float bits of a squared distance (low 32 bits)
+    kNaiveTests = 1,     // node boxes tested
+    kNaiveLeaves = 2,    // triangle pairs evaluated
+    kNaiveMaxTests = 3,  // most boxes tested by one thread
+    kNaiveT0 = 4,        // globaltimer stamp of the first thread to start
+    kNaiveTimeout = 5,   // some thread passed the deadline and stopped
+    kNaiveBad = 6,       // a walk outgrew its stack (never, for at most 31 levels)
+    kNaiveWords = 8,
+};
+
+struct NaiveArgs {
+    const float4* triA;   // A's triangles in leaf order
+    long long TA;
+    const float* boxB;    // B's tree
+    const float4* triB;
+    long long TB;
+    int LB;
+    float R[9], t[3];     // A-local -> B-local, float32
+    float E;              // widening of each mapped triangle's box
+    unsigned long long* ws;
+    long long timeout_ns;
+};
+
+cudaError_t launch_naive(int kind, const NaiveArgs& g, cudaStream_t stream);
 
 // ---- query (gd_query.cu)
 int query_max_blocks_per_sm(int kind);

@@ -27,11 +27,19 @@ STATUS_NAMES = {
 # every symbol include/gdist.h declares
 EXPORTS = [
     "gd_ctx_create", "gd_ctx_destroy", "gd_last_error", "gd_ctx_set_tunables", "gd_ctx_get_tunables",
-    "gd_get_stats", "gd_ctx_stream", "gd_mesh_create", "gd_bvh_build", "gd_mesh_destroy", "gd_mesh_info",
-    "gd_mesh_download", "gd_min_distance", "gd_max_distance", "gd_query_device", "gd_query_device_noalloc",
+    "gd_get_stats", "gd_ctx_stream", "gd_mesh_create", "gd_bvh_build", "gd_mesh_update", "gd_mesh_destroy", "gd_mesh_info",
+    "gd_mesh_download", "gd_min_distance", "gd_max_distance", "gd_naive_query", "gd_query_device", "gd_query_device_noalloc",
     "gd_batch_query", "gd_autotune", "gd_graph_create", "gd_graph_launch", "gd_graph_destroy",
     "gd_serve_start", "gd_serve_submit", "gd_serve_poll", "gd_serve_drain", "gd_serve_stop",
 ]
+
+
+class gd_naive_result(C.Structure):
+    _fields_ = [("d", C.c_double), ("node_tests", C.c_uint64), ("leaf_tests", C.c_uint64),
+                ("max_thread_tests", C.c_uint64), ("status", C.c_uint32), ("pad", C.c_uint32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
 
 
 class gd_result(C.Structure):
@@ -111,11 +119,13 @@ def load(path: str = LIB_PATH):
         "gd_mesh_create": (C.c_int, [_vp, C.POINTER(C.c_float), C.c_int64, C.POINTER(C.c_int32), C.c_int64,
                                      C.POINTER(_vp)]),
         "gd_bvh_build": (C.c_int, [_vp, C.POINTER(gd_build_opts)]),
+        "gd_mesh_update": (C.c_int, [_vp, _vp, C.c_int64]),
         "gd_mesh_destroy": (None, [_vp]),
         "gd_mesh_info": (C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
         "gd_mesh_download": (C.c_int, [_vp, C.POINTER(C.c_float), C.POINTER(C.c_int32)]),
         "gd_min_distance": (C.c_int, [_vp, _vp, _vp, _dp, _dp, C.POINTER(gd_result)]),
         "gd_max_distance": (C.c_int, [_vp, _vp, _vp, _dp, _dp, C.POINTER(gd_result)]),
+        "gd_naive_query": (C.c_int, [_vp, _vp, _vp, C.c_int, _dp, _dp, C.c_int64, C.POINTER(gd_naive_result)]),
         "gd_query_device": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp, _vp, _vp, _vp]),
         "gd_query_device_noalloc": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _vp, _vp]),
         "gd_batch_query": (C.c_int, [_vp, C.POINTER(gd_query), C.c_int64, C.POINTER(gd_result)]),
@@ -211,6 +221,19 @@ def gd_bvh_build(mesh, morton_bits: int | None = None, ctx=None):
     _check(load().gd_bvh_build(mesh, o), ctx)
 
 
+def gd_mesh_update(mesh, verts, ctx=None):
+    """New vertex positions for a built mesh, then a device refit of its BVH.
+    verts: an (nv, 3) float32 array on the host, or a contiguous float32 CUDA
+    tensor (its device pointer is passed through)."""
+    if hasattr(verts, "is_cuda") and verts.is_cuda:
+        if str(verts.dtype) != "torch.float32" or not verts.is_contiguous() or verts.numel() % 3:
+            raise ValueError("device vertices must be a contiguous float32 tensor of nv x 3 values")
+        _check(load().gd_mesh_update(mesh, _vp(verts.data_ptr()), verts.numel() // 3), ctx)
+        return
+    v = np.ascontiguousarray(np.asarray(verts, dtype=np.float32).reshape(-1, 3))
+    _check(load().gd_mesh_update(mesh, _vp(v.ctypes.data), len(v)), ctx)
+
+
 def gd_mesh_destroy(mesh):
     load().gd_mesh_destroy(mesh)
 
@@ -245,6 +268,18 @@ def gd_min_distance(ctx, A, B, xa, xb) -> gd_result:
 
 def gd_max_distance(ctx, A, B, xa, xb) -> gd_result:
     return _query(load().gd_max_distance, ctx, A, B, xa, xb)
+
+
+def gd_naive_query(ctx, A, B, kind: int, xa, xb, timeout_ns: int = 0) -> dict:
+    """The naive comparator; a timeout is reported in the result's status
+    (with partial counts) instead of raising."""
+    xa, xb = _x(xa), _x(xb)
+    r = gd_naive_result()
+    rc = load().gd_naive_query(ctx, A, B, int(kind), xa.ctypes.data_as(_dp), xb.ctypes.data_as(_dp),
+                               int(timeout_ns), C.byref(r))
+    if rc not in (GD_OK, GD_ERR_TIMEOUT):
+        _check(rc, ctx)
+    return r.as_dict()
 
 
 def gd_query_device(ctx, A, B, kind: int, d_xa: int, d_xb: int, d_out: int, stream: int = 0):

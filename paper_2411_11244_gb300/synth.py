@@ -25,7 +25,7 @@ __all__ = [
     "torus", "geosphere", "gear", "box", "grid", "random_rotation",
     "xform", "compose", "identity_xform", "rot_axis",
     "config_tori", "config_rings", "config_icospheres", "config_gears",
-    "mesh_pool",
+    "mesh_pool", "warp", "config_deforming_rings",
 ]
 
 
@@ -346,6 +346,44 @@ def config_rings(frames: int = 100, seed: int = 0, nu: int = 2500, nv: int = 150
         Rb = to_xz @ rot_axis((0, 0, 1), ang)
         xbs.append(xform(Rb, (c, 0.0, 0.0)))
     return A, A, identity_xform(), xbs
+
+
+def warp(verts, amp: float, freq: float, phase: float):
+    """Smooth non-rigid deformation of a vertex array (a deforming body for the
+    paper's Deformable scene, Section 8): every vertex x moves by
+    amp * (sin(2 pi f y + p), sin(2 pi f z + 1.3 p), sin(2 pi f x + 0.7 p)),
+    at most amp * sqrt(3).  Connectivity is unchanged.  float64 arithmetic,
+    rounded to float32."""
+    v = np.asarray(verts, dtype=np.float64)
+    w = 2.0 * math.pi * freq
+    d = np.stack([np.sin(w * v[:, 1] + phase), np.sin(w * v[:, 2] + 1.3 * phase),
+                  np.sin(w * v[:, 0] + 0.7 * phase)], axis=1)
+    return _f32(v + amp * d)
+
+
+def config_deforming_rings(frames: int = 8, seed: int = 0, nu: int = 2500, nv: int = 1500,
+                           R: float = 1.0, r: float = 0.05, gap: float = RING_GAP, amp: float = 0.01):
+    """The interlinked rings with a deforming B: each frame warps B's local
+    vertices (warp with amplitude amp, one wave per unit length, a seeded
+    phase) and spins B as in config_rings.  B's centre sits at
+    c = 2 r + gap + 2 amp, so the warped surfaces stay apart (each vertex moves
+    by at most amp * sqrt(3) < 2 amp).  Returns (A, tris_B, xa, [xb...],
+    frame_verts) where frame_verts(i) gives B's float32 vertices of frame i."""
+    A = torus(R, r, nu, nv)
+    c = 2 * r + gap + 2 * amp
+    rng = np.random.default_rng(seed)
+    to_xz = rot_axis((1, 0, 0), math.pi / 2)
+    xbs, phases = [], []
+    for _ in range(frames):
+        Rb = to_xz @ rot_axis((0, 0, 1), rng.uniform(0.0, 2 * math.pi))
+        xbs.append(xform(Rb, (c, 0.0, 0.0)))
+        phases.append(rng.uniform(0.0, 2 * math.pi))
+    base = A[0]
+
+    def frame_verts(i: int):
+        return warp(base, amp, 1.0, phases[i])
+
+    return A, A[1], identity_xform(), xbs, frame_verts
 
 
 def config_icospheres(level: int = 8, seed: int = 0, noise: float = 1e-3, gap_frac: float = 1e-5):

@@ -146,21 +146,26 @@ def test_bvh_build_structure(G, ctx, case):
         # stable Morton order, bit for bit
         keys = _morton_np(v, t)
         assert np.array_equal(order, np.argsort(keys, kind="stable").astype(np.int32))
-        # leaves: exact bounds of their one or two triangles
-        vt = np.asarray(v, dtype=np.float32)[np.asarray(t)[order]]  # (T, 3, 3) in leaf order
-        for leaf in range(1 << L):
-            s, e = (leaf * T) >> L, ((leaf + 1) * T) >> L
-            assert 1 <= e - s <= 2
-            pts = vt[s:e].reshape(-1, 3)
-            b = boxes[(1 << L) + leaf]
-            assert np.array_equal(b[:3], pts.min(0)) and np.array_equal(b[3:], pts.max(0))
-        # internal nodes: unions of their children (hence tight)
-        for i in range(1, 1 << L):
-            l, r = boxes[2 * i], boxes[2 * i + 1]
-            assert np.array_equal(boxes[i][:3], np.minimum(l[:3], r[:3]))
-            assert np.array_equal(boxes[i][3:], np.maximum(l[3:], r[3:]))
+        _check_tree(boxes, order, v, t, L)
     finally:
         G.gd_mesh_destroy(h)
+
+
+def _check_tree(boxes, order, v, t, L):
+    """Leaves are the exact bounds of their one or two triangles (f12 rule,
+    Section 7.3); inner nodes are unions of their children (hence tight)."""
+    T = len(t)
+    vt = np.asarray(v, dtype=np.float32)[np.asarray(t)[order]]  # (T, 3, 3) in leaf order
+    for leaf in range(1 << L):
+        s, e = (leaf * T) >> L, ((leaf + 1) * T) >> L
+        assert 1 <= e - s <= 2
+        pts = vt[s:e].reshape(-1, 3)
+        b = boxes[(1 << L) + leaf]
+        assert np.array_equal(b[:3], pts.min(0)) and np.array_equal(b[3:], pts.max(0))
+    for i in range(1, 1 << L):
+        l, r = boxes[2 * i], boxes[2 * i + 1]
+        assert np.array_equal(boxes[i][:3], np.minimum(l[:3], r[:3]))
+        assert np.array_equal(boxes[i][3:], np.maximum(l[3:], r[3:]))
 
 
 def test_bvh_build_rejects_bad_input(G, ctx):
@@ -601,6 +606,144 @@ def test_serve_drain_collects_every_ticket(G, ctx, oracle_mod):
         same_answer(r, alone[i], oracle_mod, meshes[a], qs[i][2], meshes[1 - a], qs[i][3], "min")
     for h in hs:
         G.gd_mesh_destroy(h)
+
+
+# ------------------------------------------------------------------ deformable meshes
+
+def test_mesh_update_refits_tree(G, ctx):
+    """A refit keeps the build's leaf order and makes every box tight for the
+    new vertices again (bit for bit: min/max of float32 values are exact)."""
+    for v, t in (synth.torus(1.0, 0.3, 32, 32), synth.gear(96, 3, teeth=12, seed=1), _soup(np.random.default_rng(5), 5)):
+        h = _mesh(G, ctx, (v, t))
+        try:
+            L, _ = G.gd_mesh_info(h)
+            _, order0 = G.gd_mesh_download(h)
+            for ph in (0.3, 2.1):
+                w = synth.warp(v, 0.05, 1.0, ph)
+                G.gd_mesh_update(h, w, ctx=ctx)
+                boxes, order = G.gd_mesh_download(h)
+                assert np.array_equal(order, order0)
+                _check_tree(boxes, order, w, t, L)
+        finally:
+            G.gd_mesh_destroy(h)
+
+
+def test_deformable_frames_match_oracle(G, ctx, oracle_mod):
+    """Frames of a deforming torus B next to a rigid torus A (the Deformable
+    scene of Section 8): each frame uploads B's warped vertices (from the host
+    on even frames, from device memory on odd ones) and refits its tree; min
+    and max distances match the oracle on the warped mesh, and equal a query
+    on a mesh built from scratch from the same vertices."""
+    import torch
+    A = synth.torus(1.0, 0.3, 24, 20)
+    vb, tb = synth.torus(0.8, 0.25, 28, 18)
+    xa = synth.identity_xform()
+    rng = np.random.default_rng(31)
+    ma, mb = _mesh(G, ctx, A), _mesh(G, ctx, (vb, tb))
+    try:
+        for f in range(4):
+            w = synth.warp(vb, 0.08, 0.7, rng.uniform(0, 2 * math.pi))
+            if f % 2:
+                G.gd_mesh_update(mb, torch.from_numpy(w).cuda(), ctx=ctx)
+            else:
+                G.gd_mesh_update(mb, w, ctx=ctx)
+            B = (w, tb)
+            xb = synth.xform(synth.random_rotation(rng), rng.normal(size=3) * 0.6 + (1.6, 0, 0))
+            diag = oracle_mod.diag(A, xa, B, xb)
+            fresh = _mesh(G, ctx, B)
+            try:
+                for kind in ("min", "max"):
+                    fn = G.gd_min_distance if kind == "min" else G.gd_max_distance
+                    r = fn(ctx, ma, mb, xa, xb)
+                    check(r, A, xa, B, xb, kind, oracle_mod.brute(A, xa, B, xb, kind), diag, oracle_mod)
+                    same_answer(r, fn(ctx, ma, fresh, xa, xb), oracle_mod, A, xa, B, xb, kind)
+            finally:
+                G.gd_mesh_destroy(fresh)
+    finally:
+        G.gd_mesh_destroy(ma)
+        G.gd_mesh_destroy(mb)
+
+
+def test_mesh_update_rejects_bad_input(G, ctx, oracle_mod):
+    v, t = synth.torus(1.0, 0.3, 12, 10)
+    I = synth.identity_xform()
+    far = synth.xform(np.eye(3), (3.0, 0.0, 0.0))
+    h = _mesh(G, ctx, (v, t))
+    try:
+        with pytest.raises(G.GdError) as e:
+            G.gd_mesh_update(h, v[:-1], ctx=ctx)
+        assert e.value.status == G.GD_ERR_INVALID_ARG
+        r0 = G.gd_min_distance(ctx, h, h, I, far)  # the mesh is untouched
+        bad = v.copy()
+        bad[7, 1] = np.inf
+        with pytest.raises(G.GdError) as e:
+            G.gd_mesh_update(h, bad, ctx=ctx)
+        assert e.value.status == G.GD_ERR_INVALID_ARG
+        with pytest.raises(G.GdError) as e:
+            G.gd_min_distance(ctx, h, h, I, far)
+        assert e.value.status == G.GD_ERR_NOT_BUILT
+        G.gd_mesh_update(h, v, ctx=ctx)  # a valid update makes it usable again
+        r1 = G.gd_min_distance(ctx, h, h, I, far)
+        assert (r1.d, r1.tri_a, r1.tri_b) == (r0.d, r0.tri_a, r0.tri_b)
+        unbuilt = G.gd_mesh_create(ctx, v, t)
+        with pytest.raises(G.GdError) as e:
+            G.gd_mesh_update(unbuilt, v, ctx=ctx)
+        assert e.value.status == G.GD_ERR_NOT_BUILT
+        G.gd_mesh_destroy(unbuilt)
+    finally:
+        G.gd_mesh_destroy(h)
+
+
+# ------------------------------------------------------------------ naive comparator
+
+def test_naive_comparator_matches_oracle(G, ctx, oracle_mod):
+    """The naive per-triangle DFS (Section 8's GPU comparator) finds the same
+    extreme in float32: within a float32 error budget of the oracle's value.
+    A walk tests each node of B at most once."""
+    rng = np.random.default_rng(41)
+    pairs = [
+        (synth.torus(1.0, 0.3, 24, 16), synth.torus(0.9, 0.2, 20, 14)),
+        (synth.geosphere(6, 0.8, 2e-3, 1), synth.gear(96, 3, teeth=12, seed=2)),
+        (_soup(rng, 1), _soup(rng, 5)),
+    ]
+    for A, B in pairs:
+        ma, mb = _mesh(G, ctx, A), _mesh(G, ctx, B)
+        LB, _ = G.gd_mesh_info(mb)
+        try:
+            for k in range(3):
+                xa = _rigid(rng)
+                xb = synth.compose(synth.xform(np.eye(3), rng.normal(size=3) * (0.5 + k)), xa)
+                xb = synth.compose(xb, synth.xform(synth.random_rotation(rng), (0, 0, 0)))
+                diag = oracle_mod.diag(A, xa, B, xb)
+                scale = diag + float(np.abs(np.asarray(xa)[[3, 7, 11]]).max() + np.abs(np.asarray(xb)[[3, 7, 11]]).max())
+                for kind, gk in (("min", G.GD_MIN), ("max", G.GD_MAX)):
+                    ref = oracle_mod.brute(A, xa, B, xb, kind)
+                    r = G.gd_naive_query(ctx, ma, mb, gk, xa, xb)
+                    assert r["status"] == 0
+                    assert abs(r["d"] - ref.d) <= 2e-6 * scale, (kind, r["d"], ref.d)
+                    assert r["leaf_tests"] >= 1
+                    assert 1 <= r["max_thread_tests"] <= min(r["node_tests"], (2 << LB) - 1)
+        finally:
+            G.gd_mesh_destroy(ma)
+            G.gd_mesh_destroy(mb)
+
+
+def test_naive_comparator_deadline(G, ctx, oracle_mod):
+    """A deadline far shorter than the walk stops every thread; the call
+    reports the timeout with partial counts and the context stays usable."""
+    A = synth.torus(1.0, 0.3, 200, 100)
+    ma = _mesh(G, ctx, A)
+    I = synth.identity_xform()
+    near = synth.xform(np.eye(3), (0.2, 0.0, 0.0))
+    try:
+        r = G.gd_naive_query(ctx, ma, ma, G.GD_MIN, I, near, timeout_ns=1)
+        assert r["status"] == G.GD_ERR_TIMEOUT
+        full = G.gd_naive_query(ctx, ma, ma, G.GD_MIN, I, near)
+        assert full["status"] == 0 and full["node_tests"] > r["node_tests"]
+        ok = G.gd_min_distance(ctx, ma, ma, I, near)
+        assert ok.status == 0 and abs(ok.d - full["d"]) <= 1e-5
+    finally:
+        G.gd_mesh_destroy(ma)
 
 
 # ------------------------------------------------------------------ full-size workloads
