@@ -294,6 +294,52 @@ def bench_naive(G, ctx, ma, mb, xa, xbs, frames=2, timeout_s=10.0):
     }
 
 
+def bench_points(G, ctx, ma, n=1 << 20, reps=3):
+    """Point-to-mesh queries against ring A (7.5 M triangles): n world points,
+    half near the surface (vertices moved by N(0, 0.002)), half uniform in the
+    ring's bounding box grown by 10 %.  Points/s with points and results in
+    device memory, and through host arrays (copies included); node tests and
+    float64 distances per point."""
+    import numpy as np
+    import torch
+    from paper_2411_11244_gb300 import synth
+    A = synth.torus(1.0, 0.05, 2500, 1500)
+    rng = np.random.default_rng(7)
+    v = np.asarray(A[0], dtype=np.float64)
+    lo, hi = v.min(0), v.max(0)
+    ext = hi - lo
+    near = v[rng.integers(0, len(v), n // 2)] + rng.normal(size=(n // 2, 3)) * 0.002
+    unif = rng.uniform(lo - 0.05 * ext, hi + 0.05 * ext, (n - n // 2, 3))
+    pts = np.ascontiguousarray(np.concatenate([near, unif]))
+    I = synth.identity_xform()
+    dpts = torch.from_numpy(pts).cuda()
+    try:
+        G.gd_point_distance(ctx, ma, I, dpts)
+    except G.GdError as e:
+        return {"workload": f"{n} points vs ring A", "error": str(e)}
+    dev = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        raw = G.gd_point_distance(ctx, ma, I, dpts)
+        dev.append(time.perf_counter() - t0)
+    st = G.gd_point_stats(ctx)
+    host = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        res = G.gd_point_distance(ctx, ma, I, pts)
+        host.append(time.perf_counter() - t0)
+    ok = int((res["status"] == 0).sum())
+    same = bool(np.array_equal(G.gd_point_records(raw.cpu().numpy())["d"], res["d"]))
+    return {
+        "workload": f"{n} points vs a {len(A[1])}-triangle ring (half near the surface, half uniform)",
+        "points_per_s_device": n / statistics.median(dev), "ms_device": 1000.0 * statistics.median(dev),
+        "points_per_s_host": n / statistics.median(host), "ms_host": 1000.0 * statistics.median(host),
+        "node_tests_per_point": st["node_tests"] / n, "exact_per_point": st["exact_tests"] / n,
+        "ok": ok, "device_equals_host": same,
+    }
+
+
 def bench_served(G, ctx, rates=(1000, 3000, 10000, 30000, 100000), n_req=1500, seed=0):
     """A pool of 64 meshes (tori, geodesic spheres, gears; 1e3..4e6 triangles,
     BVHs resident) and a stream of random mesh pairs and transforms arriving
@@ -420,6 +466,7 @@ def main():
     ap.add_argument("--no-ablation", action="store_true")
     ap.add_argument("--no-deformable", action="store_true")
     ap.add_argument("--no-naive", action="store_true")
+    ap.add_argument("--no-points", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -542,6 +589,8 @@ def main():
     }
     if not args.no_ablation:
         line["ablation"] = bench_ablation(G, ctx, ma, mb, xa, xbs)
+    if not args.no_points:
+        line["points"] = bench_points(G, ctx, ma)
     if not args.no_naive:
         line["naive"] = bench_naive(G, ctx, ma, mb, xa, xbs)
     if not args.no_deformable:

@@ -89,6 +89,15 @@ typedef struct {
     uint32_t pad;
 } gd_naive_result;
 
+/* Answer of a point-to-mesh query (gd_point_distance). */
+typedef struct {
+    double d;        /* float64 distance from the point to the mesh surface */
+    int64_t tri;     /* the caller's index of the closest triangle (smallest among ties) */
+    double p[3];     /* closest point on that triangle, world frame */
+    uint32_t status; /* GD_OK; GD_ERR_INVALID_ARG (non-finite point); GD_ERR_TIMEOUT */
+    uint32_t pad;
+} gd_point_result;
+
 /* One query of a batch or of the server. */
 typedef struct {
     const gd_mesh *a, *b;
@@ -237,6 +246,23 @@ GD_API gd_status gd_min_distance(gd_ctx *ctx, const gd_mesh *A, const gd_mesh *B
 /* Maximum distance D_max (Eq. 2); same contract as gd_min_distance. */
 GD_API gd_status gd_max_distance(gd_ctx *ctx, const gd_mesh *A, const gd_mesh *B, const double xa[12],
                                  const double xb[12], gd_result *out);
+/* Point-to-mesh distances (Eq. 1 with one side a single point; the 1-to-N
+ * direction of Section 10's future work, with N query points): for each of
+ * n world points, the closest point of mesh M placed by x (12 doubles, as
+ * for the mesh queries).  Exact in float64: one thread per point walks M's
+ * tree twice (a float32 walk finds a near triangle whose float64 distance
+ * bounds the answer; a second walk takes the float64 distance of every
+ * triangle whose box is within that bound, boxes widened by the float32
+ * error of the mapped point), so the result is the minimum over all
+ * triangles, the smallest index among ties.  points: n x 3 float64; points
+ * and out may each be host or device memory.  Synchronous.  Per-point
+ * status in out; the call returns GD_ERR_TIMEOUT if some point passed the
+ * context's timeout. */
+GD_API gd_status gd_point_distance(gd_ctx *ctx, const gd_mesh *M, const double x[12], const double *points,
+                                   int64_t n, gd_point_result *out);
+/* Work of the context's last gd_point_distance call: node boxes tested and
+ * float64 point-triangle distances taken, summed over its points. */
+GD_API gd_status gd_point_stats(gd_ctx *ctx, uint64_t *node_tests, uint64_t *exact_tests);
 /* The naive GPU comparator of Section 8 (Performance): one thread per
  * triangle of A walks B's BVH depth first (nearer child first), pruning with
  * the conventional box bounds (Eqs. 5-8) against one global running bound

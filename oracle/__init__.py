@@ -81,6 +81,9 @@ def lib():
         L.or_bvh_query_batch.restype = C.c_int
         L.or_tri_pair_world.argtypes = [_fp, _dp, _fp, _dp, C.c_int, _dp, _dp]
         L.or_tri_pair_world.restype = C.c_double
+        L.or_point_mesh.argtypes = [_fp, C.c_int64, _ip, C.c_int64, _dp, _dp, C.c_int64, C.c_int, _dp,
+                                    C.POINTER(C.c_int64), _dp]
+        L.or_point_mesh.restype = C.c_int
         _lib = L
     return _lib
 
@@ -214,6 +217,24 @@ def bvh_query_batch(A: Bvh, xa, B: Bvh, xbs, kind: str = "min", threads: int | N
     if rc:
         raise RuntimeError(f"oracle batch query failed ({rc})")
     return [_ans(out[i]) for i in range(n)]
+
+
+def point_mesh(mesh, x, points, threads: int | None = None):
+    """Distance from each world point to the mesh placed by x (Eq. 1 with one
+    side a single point), brute force: (d[n], tri[n], closest[n, 3])."""
+    v, t = _mesh(mesh)
+    x = _d(x, 12)
+    P = np.ascontiguousarray(np.asarray(points, dtype=np.float64).reshape(-1, 3))
+    n = len(P)
+    d = np.zeros(n)
+    tri = np.zeros(n, dtype=np.int64)
+    q = np.zeros((n, 3))
+    rc = lib().or_point_mesh(_ptr(v, _fp), len(v), _ptr(t, _ip), len(t), _ptr(x, _dp), _ptr(P, _dp), n,
+                             threads or os.cpu_count() or 1, _ptr(d, _dp),
+                             tri.ctypes.data_as(C.POINTER(C.c_int64)), _ptr(q, _dp))
+    if rc != 0:
+        raise RuntimeError(f"or_point_mesh failed ({rc})")
+    return d, tri, q
 
 
 def world_vertices(mesh, x):

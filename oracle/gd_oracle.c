@@ -315,6 +315,64 @@ OR_API int or_brute(const float *va, int64_t nva, const int32_t *ta, int64_t nta
     return 0;
 }
 
+/* ----------------------------------------------------- point to mesh (N points)
+ *
+ * The distance from a point p to a mesh Q is Eq. 1 with P = {p}: the minimum
+ * over the triangles of Q of the point-triangle distance.  Brute force over
+ * all triangles, threaded over the points; among triangles at the same
+ * float64 distance the smallest index is reported, with its closest point.
+ */
+
+typedef struct {
+    const v3 *w;
+    int64_t nt;
+    const double *pts;
+    int64_t i0, i1;
+    double *d, *q;
+    int64_t *tri;
+} point_job;
+
+static void *point_worker(void *arg) {
+    point_job *J = (point_job *)arg;
+    for (int64_t i = J->i0; i < J->i1; ++i) {
+        const v3 p = ld(J->pts + 3 * i);
+        double best = INFINITY;
+        int64_t bt = -1;
+        v3 bq = p, q;
+        for (int64_t j = 0; j < J->nt; ++j) {
+            const double d = pt_tri(p, J->w[3 * j], J->w[3 * j + 1], J->w[3 * j + 2], &q);
+            if (d < best) { best = d; bt = j; bq = q; }
+        }
+        J->d[i] = best;
+        J->tri[i] = bt;
+        st(J->q + 3 * i, bq);
+    }
+    return NULL;
+}
+
+/* pts: n x 3 world points; out: d[n], tri[n], q[3n] (closest points, world). */
+OR_API int or_point_mesh(const float *v, int64_t nv, const int32_t *t, int64_t nt, const double *X,
+                         const double *pts, int64_t n, int nthreads, double *d, int64_t *tri, double *q) {
+    (void)nv;
+    if (nt <= 0 || n < 0) return 1;
+    if (n == 0) return 0;
+    v3 *w = world_tris(v, t, nt, X);
+    if (!w) return 2;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > n) nthreads = (int)n;
+    point_job *jobs = (point_job *)calloc((size_t)nthreads, sizeof(point_job));
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    for (int k = 0; k < nthreads; ++k) {
+        point_job *J = &jobs[k];
+        J->w = w; J->nt = nt; J->pts = pts; J->d = d; J->q = q; J->tri = tri;
+        J->i0 = n * k / nthreads; J->i1 = n * (k + 1) / nthreads;
+        pthread_create(&th[k], NULL, point_worker, J);
+    }
+    for (int k = 0; k < nthreads; ++k) pthread_join(th[k], NULL);
+    free(jobs); free(th); free(w);
+    return 0;
+}
+
 /* -------------------------------------------------------------- AABB tree */
 
 typedef struct {

@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libgdist.so")
-SOURCES = ["gd_query.cu", "gd_build.cu", "gd_api.cu", "gd_serve.cu", "gd_noalloc.cu", "gd_naive.cu"]
+SOURCES = ["gd_query.cu", "gd_build.cu", "gd_api.cu", "gd_serve.cu", "gd_noalloc.cu", "gd_naive.cu", "gd_point.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-fvisibility=hidden", "-I", os.path.join(ROOT, "include")]
 

@@ -70,6 +70,11 @@ struct gd_ctx {
     unsigned* slot_of = nullptr;  // refit-root tables
     long long cap_table = 0;
     unsigned long long* naive_ws = nullptr;  // scratch of the naive comparator
+    unsigned long long* point_ws = nullptr;  // counters of point queries
+    double* pts_dev = nullptr;               // staged host points and results
+    gd_point_result* pres_dev = nullptr;
+    long long cap_pts = 0;
+    unsigned long long last_point_tests = 0, last_point_exact = 0;  // counters of the last point call
     gd_stats last{};
     bool stats_pending = false;  // last run was device-resident: stats still on the device
     unsigned ws_gen = 0;         // bumped whenever the work buffers or tunables change
@@ -467,6 +472,7 @@ GD_API void gd_ctx_destroy(gd_ctx* c) {
     cudaFreeHost(c->qin_host); cudaFreeHost(c->out_host);
     cudaFree(c->slot_of);
     cudaFree(c->naive_ws);
+    cudaFree(c->point_ws); cudaFree(c->pts_dev); cudaFree(c->pres_dev);
     cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -743,6 +749,66 @@ GD_API gd_status gd_mesh_download(const gd_mesh* m, float* boxes, int32_t* order
             order[j] = id;
         }
     }
+    return GD_OK;
+}
+
+namespace {
+bool on_device(const void* p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+}  // namespace
+
+GD_API gd_status gd_point_distance(gd_ctx* ctx, const gd_mesh* M, const double x[12], const double* points,
+                                   int64_t n, gd_point_result* out) {
+    if (!ctx) return GD_ERR_INVALID_ARG;
+    if (!x || n < 0 || (n > 0 && (!points || !out))) return fail(ctx, GD_ERR_INVALID_ARG, "NULL argument or n < 0");
+    if (!M) return fail(ctx, GD_ERR_INVALID_ARG, "NULL mesh");
+    if (M->ctx != ctx) return fail(ctx, GD_ERR_INVALID_ARG, "mesh belongs to another context");
+    if (!M->built) return fail(ctx, GD_ERR_NOT_BUILT, "BVH not built (call gd_bvh_build)");
+    std::string why;
+    if (!xform_ok(x, &why)) return fail(ctx, GD_ERR_INVALID_ARG, why);
+    if (n == 0) return GD_OK;
+    cudaSetDevice(ctx->device);
+    if (!ctx->point_ws) GD_CUDA(ctx, cudaMalloc(&ctx->point_ws, sizeof(unsigned long long) * kPointWords));
+    const bool dev_in = on_device(points), dev_out = on_device(out);
+    if ((!dev_in || !dev_out) && n > ctx->cap_pts) {
+        cudaFree(ctx->pts_dev); cudaFree(ctx->pres_dev);
+        ctx->pts_dev = nullptr; ctx->pres_dev = nullptr; ctx->cap_pts = 0;
+        GD_CUDA(ctx, cudaMalloc(&ctx->pts_dev, sizeof(double) * 3 * n));
+        GD_CUDA(ctx, cudaMalloc(&ctx->pres_dev, sizeof(gd_point_result) * n));
+        ctx->cap_pts = n;
+    }
+    PointArgs g{};
+    g.box = M->d_box; g.tri = M->d_tri; g.T = M->nt; g.L = M->L;
+    std::memcpy(g.x, x, sizeof(g.x));
+    g.pts = dev_in ? points : ctx->pts_dev;
+    g.n = n;
+    g.out = dev_out ? out : ctx->pres_dev;
+    g.ws = ctx->point_ws;
+    g.timeout_ns = ctx->tun.timeout_ns;
+    if (!dev_in)
+        GD_CUDA(ctx, cudaMemcpyAsync(ctx->pts_dev, points, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, ctx->stream));
+    GD_CUDA(ctx, launch_point(g, ctx->stream));
+    if (!dev_out)
+        GD_CUDA(ctx, cudaMemcpyAsync(out, ctx->pres_dev, sizeof(gd_point_result) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    unsigned long long w[kPointWords];
+    GD_CUDA(ctx, cudaMemcpyAsync(w, ctx->point_ws, sizeof(w), cudaMemcpyDeviceToHost, ctx->stream));
+    GD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->last_point_tests = w[kPointTests];
+    ctx->last_point_exact = w[kPointExact];
+    if (w[kPointTimeout]) return fail(ctx, GD_ERR_TIMEOUT, "a point query passed the timeout");
+    return GD_OK;
+}
+
+GD_API gd_status gd_point_stats(gd_ctx* ctx, uint64_t* node_tests, uint64_t* exact_tests) {
+    if (!ctx) return GD_ERR_INVALID_ARG;
+    if (node_tests) *node_tests = ctx->last_point_tests;
+    if (exact_tests) *exact_tests = ctx->last_point_exact;
     return GD_OK;
 }
 

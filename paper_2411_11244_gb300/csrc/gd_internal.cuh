@@ -9,8 +9,6 @@
 //          original index stored as int bits.
 //   leaf l owns sorted triangles [floor(l T / 2^L), floor((l+1) T / 2^L)):
 //          one or two each, no per-leaf storage (the f12 rule of Section 7.3).
-//   order: uint32[T], the original index of each sorted triangle (read by the
-//          refit of a deformed mesh; the traversal never reads it).
 #pragma once
 #include <cstddef>
 

@@ -64,6 +64,30 @@ struct NaiveArgs {
 
 cudaError_t launch_naive(int kind, const NaiveArgs& g, cudaStream_t stream);
 
+// ---- point-to-mesh queries (gd_point.cu)
+enum : int {
+    kPointTests = 0,     // node boxes tested
+    kPointExact = 1,     // float64 point-triangle distances
+    kPointT0 = 2,        // globaltimer stamp of the first CTA to start
+    kPointTimeout = 3,   // some point passed the deadline
+    kPointWords = 4,
+};
+
+struct PointArgs {
+    const float* box;     // the mesh's tree
+    const float4* tri;
+    long long T;
+    int L;
+    double x[12];         // mesh local -> world
+    const double* pts;    // n x 3 world points, device
+    long long n;
+    gd_point_result* out; // n results, device
+    unsigned long long* ws;
+    long long timeout_ns;
+};
+
+cudaError_t launch_point(const PointArgs& g, cudaStream_t stream);
+
 // ---- query (gd_query.cu)
 int query_max_blocks_per_sm(int kind);
 cudaError_t launch_query(int kind, const KArgs& args, int grid, cudaStream_t stream);

@@ -1018,15 +1018,35 @@ __device__ void expand_level(const KArgs& A, int level, unsigned n, int s, unsig
 
 // ------------------------------------------------------------- phase 3
 
+// Single-query launches: merge the global running bound and status word
+// (read earlier into w by thread 0) into the CTA's copy.  The leaf phase has
+// no grid barrier to refresh that copy, so without this a CTA would not see
+// the other CTAs' bounds, nor a D = 0 proof, until the phase ended.
+template <int KIND>
+__device__ __forceinline__ void cta_merge_bound(unsigned long long w) {
+    CtaState& c = cta();
+    if (KIND == 0) atomicMin(&c.U, (unsigned)w);
+    else atomicMax(&c.U, (unsigned)w);
+    const unsigned st = (unsigned)(w >> 32) & kStatStop;
+    if (st) atomicOr(&c.stat, st);
+}
+
 template <int KIND>
 __device__ void leaf_phase(const KArgs& A, unsigned nleaf, unsigned& tripairs, unsigned long long& bytes) {
     const unsigned long long total = (unsigned long long)nleaf * 4ull;
     const unsigned long long gstride = (unsigned long long)work_ctas(A) * blockDim.x;
     unsigned* cand_cnt = A.ctr + kCtrCand;
+    const bool pull = A.nq == 1 && threadIdx.x == 0;
     QView V;
     int iter = 0;
     for (unsigned long long cbase = (unsigned long long)blockIdx.x * blockDim.x; cbase < total;
          cbase += gstride, ++iter) {
+        // a single query whose traversal stopped (D = 0 proven) skips the rest
+        if (A.nq == 1 && __syncthreads_or((((volatile CtaState&)cta()).stat & kStatStop) != 0u)) break;
+        // issued now, merged at the end of the iteration (the load's latency
+        // hides behind this iteration's work)
+        unsigned long long gw = 0;
+        if (pull) gw = ld_relaxed64(reinterpret_cast<const unsigned long long*>(&A.qs[0].U));
         unsigned long long vt = cbase + threadIdx.x;
         bool valid = vt < total;
         Item it = {1u, 1u, 0.f, 0u};
@@ -1096,6 +1116,7 @@ __device__ void leaf_phase(const KArgs& A, unsigned nleaf, unsigned& tripairs, u
                              __shfl_sync(kFull, tb, src));
             }
         }
+        if (pull) cta_merge_bound<KIND>(gw);
     }
 }
 

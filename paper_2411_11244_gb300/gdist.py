@@ -28,10 +28,15 @@ STATUS_NAMES = {
 EXPORTS = [
     "gd_ctx_create", "gd_ctx_destroy", "gd_last_error", "gd_ctx_set_tunables", "gd_ctx_get_tunables",
     "gd_get_stats", "gd_ctx_stream", "gd_mesh_create", "gd_bvh_build", "gd_mesh_update", "gd_mesh_destroy", "gd_mesh_info",
-    "gd_mesh_download", "gd_min_distance", "gd_max_distance", "gd_naive_query", "gd_query_device", "gd_query_device_noalloc",
+    "gd_mesh_download", "gd_min_distance", "gd_max_distance", "gd_naive_query", "gd_point_distance", "gd_point_stats", "gd_query_device", "gd_query_device_noalloc",
     "gd_batch_query", "gd_autotune", "gd_graph_create", "gd_graph_launch", "gd_graph_destroy",
     "gd_serve_start", "gd_serve_submit", "gd_serve_poll", "gd_serve_drain", "gd_serve_stop",
 ]
+
+
+class gd_point_result(C.Structure):
+    _fields_ = [("d", C.c_double), ("tri", C.c_int64), ("p", C.c_double * 3), ("status", C.c_uint32),
+                ("pad", C.c_uint32)]
 
 
 class gd_naive_result(C.Structure):
@@ -125,6 +130,8 @@ def load(path: str = LIB_PATH):
         "gd_mesh_download": (C.c_int, [_vp, C.POINTER(C.c_float), C.POINTER(C.c_int32)]),
         "gd_min_distance": (C.c_int, [_vp, _vp, _vp, _dp, _dp, C.POINTER(gd_result)]),
         "gd_max_distance": (C.c_int, [_vp, _vp, _vp, _dp, _dp, C.POINTER(gd_result)]),
+        "gd_point_distance": (C.c_int, [_vp, _vp, _dp, _vp, C.c_int64, _vp]),
+        "gd_point_stats": (C.c_int, [_vp, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
         "gd_naive_query": (C.c_int, [_vp, _vp, _vp, C.c_int, _dp, _dp, C.c_int64, C.POINTER(gd_naive_result)]),
         "gd_query_device": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp, _vp, _vp, _vp]),
         "gd_query_device_noalloc": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _vp, _vp]),
@@ -268,6 +275,46 @@ def gd_min_distance(ctx, A, B, xa, xb) -> gd_result:
 
 def gd_max_distance(ctx, A, B, xa, xb) -> gd_result:
     return _query(load().gd_max_distance, ctx, A, B, xa, xb)
+
+
+def gd_point_distance(ctx, M, x, points):
+    """Distances from world points to mesh M placed by x.  points: an (n, 3)
+    float64 array on the host, or a contiguous float64 CUDA tensor.  Returns a
+    structured numpy array with fields d, tri, p, status (host), or, for a
+    CUDA tensor input, a CUDA tensor of n x 6 float64 holding the raw
+    gd_point_result records."""
+    x = _x(x)
+    if hasattr(points, "is_cuda") and points.is_cuda:
+        import torch
+        if points.dtype != torch.float64 or not points.is_contiguous() or points.numel() % 3:
+            raise ValueError("device points must be a contiguous float64 tensor of n x 3 values")
+        n = points.numel() // 3
+        out = torch.empty((n, C.sizeof(gd_point_result) // 8), dtype=torch.float64, device=points.device)
+        _check(load().gd_point_distance(ctx, M, x.ctypes.data_as(_dp), _vp(points.data_ptr()), n,
+                                        _vp(out.data_ptr())), ctx)
+        return out
+    P = np.ascontiguousarray(np.asarray(points, dtype=np.float64).reshape(-1, 3))
+    n = len(P)
+    out = (gd_point_result * max(n, 1))()
+    _check(load().gd_point_distance(ctx, M, x.ctypes.data_as(_dp), _vp(P.ctypes.data), n,
+                                    C.cast(out, _vp)), ctx)
+    dt = np.dtype([("d", np.float64), ("tri", np.int64), ("p", np.float64, 3), ("status", np.uint32),
+                   ("pad", np.uint32)])
+    return np.frombuffer(bytes(out), dtype=dt, count=n).copy()
+
+
+def gd_point_records(raw):
+    """View raw gd_point_result records (a CPU copy of the tensor that
+    gd_point_distance returns for device points) as a structured array."""
+    dt = np.dtype([("d", np.float64), ("tri", np.int64), ("p", np.float64, 3), ("status", np.uint32),
+                   ("pad", np.uint32)])
+    return np.frombuffer(np.ascontiguousarray(raw).tobytes(), dtype=dt).copy()
+
+
+def gd_point_stats(ctx):
+    a, b = C.c_uint64(), C.c_uint64()
+    _check(load().gd_point_stats(ctx, C.byref(a), C.byref(b)), ctx)
+    return {"node_tests": a.value, "exact_tests": b.value}
 
 
 def gd_naive_query(ctx, A, B, kind: int, xa, xb, timeout_ns: int = 0) -> dict:

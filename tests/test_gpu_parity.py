@@ -694,6 +694,100 @@ def test_mesh_update_rejects_bad_input(G, ctx, oracle_mod):
         G.gd_mesh_destroy(h)
 
 
+# ------------------------------------------------------------------ point-to-mesh queries
+
+def _probe_points(rng, mesh, x, n):
+    """World points around a placed mesh: uniform in its grown bounding box,
+    vertices pushed off the surface by small offsets, exact vertices (d = 0)
+    and far points."""
+    w = oracle_world(mesh, x)
+    lo, hi = w.min(0), w.max(0)
+    ext = hi - lo
+    a = rng.uniform(lo - 0.3 * ext, hi + 0.3 * ext, (n, 3))
+    v = w[rng.integers(0, len(w), n)]
+    b = v + rng.normal(size=(n, 3)) * 1e-3 * ext.max()
+    c = w[rng.integers(0, len(w), max(1, n // 8))]
+    d = (lo + hi) / 2 + rng.normal(size=(max(1, n // 8), 3)) * 20 * ext.max()
+    return np.concatenate([a, b, c, d])
+
+
+def oracle_world(mesh, x):
+    v = np.asarray(mesh[0], dtype=np.float64)
+    X = np.asarray(x, dtype=np.float64).reshape(3, 4)
+    return v @ X[:, :3].T + X[:, 3]
+
+
+def check_points(res, mesh, x, pts, oracle):
+    d_ref, _, _ = oracle.point_mesh(mesh, x, pts)
+    w = oracle_world(mesh, x)
+    t = np.asarray(mesh[1])
+    scale = np.abs(pts).max(1) + np.abs(w).max()
+    tol = 1e-13 * scale
+    assert (res["status"] == 0).all()
+    assert np.all(np.abs(res["d"] - d_ref) <= tol), np.max(np.abs(res["d"] - d_ref) / scale)
+    for i in range(len(pts)):
+        dw, _ = oracle.point_triangle(pts[i], *w[t[res["tri"][i]]])
+        assert abs(dw - d_ref[i]) <= tol[i], (i, dw, d_ref[i])
+        assert abs(np.linalg.norm(res["p"][i] - pts[i]) - res["d"][i]) <= tol[i]
+        assert oracle.point_triangle(res["p"][i], *w[t[res["tri"][i]]])[0] <= tol[i]
+
+
+def test_point_distance_matches_oracle(G, ctx, oracle_mod):
+    rng = np.random.default_rng(51)
+    meshes = [
+        synth.torus(1.0, 0.3, 24, 16),
+        synth.geosphere(6, 0.8, 2e-3, 1),
+        synth.gear(96, 3, teeth=12, seed=2),
+        _soup(rng, 200, 0.7),
+        _soup(rng, 1),
+    ]
+    for m in meshes:
+        h = _mesh(G, ctx, m)
+        try:
+            for _ in range(2):
+                x = _rigid(rng)
+                # plus the placed mesh's centre (the middle of the torus hole,
+                # the centre of the sphere: many triangles at nearly one distance)
+                X = np.asarray(x).reshape(3, 4)
+                centre = X[:, :3] @ np.asarray(m[0], dtype=np.float64).mean(0) + X[:, 3]
+                pts = np.concatenate([_probe_points(rng, m, x, 160), centre[None, :]])
+                res = G.gd_point_distance(ctx, h, x, pts)
+                check_points(res, m, x, pts, oracle_mod)
+        finally:
+            G.gd_mesh_destroy(h)
+
+
+def test_point_distance_device_io_and_edges(G, ctx, oracle_mod):
+    """Device-resident points and results give the same records as host
+    ones; n = 0 is a no-op; a non-finite point fails alone; the centre of a
+    geodesic sphere (every face nearly equidistant, the concentric-sphere
+    case of Section 10) is still exact."""
+    import torch
+    rng = np.random.default_rng(52)
+    m = synth.geosphere(8, 1.0)
+    h = _mesh(G, ctx, m)
+    try:
+        x = _rigid(rng)
+        X = np.asarray(x).reshape(3, 4)
+        pts = np.concatenate([_probe_points(rng, m, x, 64), X[:, 3][None, :]])  # + the centre
+        host = G.gd_point_distance(ctx, h, x, pts)
+        check_points(host, m, x, pts, oracle_mod)
+        raw = G.gd_point_distance(ctx, h, x, torch.from_numpy(pts).cuda())
+        dev = G.gd_point_records(raw.cpu().numpy())
+        for f in ("d", "tri", "p", "status"):
+            assert np.array_equal(dev[f], host[f])
+        st = G.gd_point_stats(ctx)
+        assert st["node_tests"] > 0 and st["exact_tests"] >= len(pts)
+        assert len(G.gd_point_distance(ctx, h, x, np.zeros((0, 3)))) == 0
+        bad = pts[:4].copy()
+        bad[2, 1] = np.nan
+        r = G.gd_point_distance(ctx, h, x, bad)
+        assert list(r["status"]) == [0, 0, G.GD_ERR_INVALID_ARG, 0]
+        assert np.array_equal(r["d"][[0, 1, 3]], host["d"][[0, 1, 3]])
+    finally:
+        G.gd_mesh_destroy(h)
+
+
 # ------------------------------------------------------------------ naive comparator
 
 def test_naive_comparator_matches_oracle(G, ctx, oracle_mod):

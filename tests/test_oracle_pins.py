@@ -291,3 +291,58 @@ def test_config1_seed_fixture(oracle_mod):
     for s in range(fx["seed"]):
         A, B, xa, xb = synth.config_tori(s)
         assert oracle_mod.brute(A, xa, B, xb).d == 0.0
+
+
+# ----------------------------------------------------------- point to mesh
+
+def test_point_mesh_box_closed_forms(oracle_mod):
+    """Distance from points to the surface of the unit cube (12 triangles):
+    face, edge and corner regions outside, and the nearest face from inside;
+    the same under a rigid motion of cube and points together."""
+    cube = synth.box((0, 0, 0), (1, 1, 1))
+    pts = np.array([
+        [2.0, 0.5, 0.5],      # face region: 1
+        [0.25, -0.75, 0.5],   # face region: 0.75
+        [1.5, 1.25, 0.5],     # edge region: sqrt(0.5^2 + 0.25^2)
+        [-1.0, -2.0, 3.0],    # corner region: sqrt(1 + 4 + 4)
+        [0.5, 0.5, 0.3],      # inside, nearest face z = 0: 0.3
+        [0.9, 0.4, 0.5],      # inside, nearest face x = 1: 0.1
+        [1.0, 0.5, 0.5],      # on the surface: 0
+    ])
+    want = [1.0, 0.75, math.hypot(0.5, 0.25), 3.0, 0.3, 0.1, 0.0]
+    I = synth.identity_xform()
+    d, tri, q = oracle_mod.point_mesh(cube, I, pts)
+    assert np.allclose(d, want, rtol=0, atol=1e-15)
+    assert np.allclose(np.linalg.norm(pts - q, axis=1), want, atol=1e-15)
+    # every closest point lies on the cube's surface
+    inside = np.all((q >= -1e-15) & (q <= 1 + 1e-15), axis=1)
+    on_face = np.any(np.isclose(q, 0, atol=1e-15) | np.isclose(q, 1, atol=1e-15), axis=1)
+    assert inside.all() and on_face.all()
+    assert ((tri >= 0) & (tri < 12)).all()
+    # rigid invariance
+    rng = np.random.default_rng(3)
+    X = synth.xform(synth.random_rotation(rng), rng.normal(size=3))
+    Xm = np.asarray(X).reshape(3, 4)
+    d2, tri2, _ = oracle_mod.point_mesh(cube, X, pts @ Xm[:, :3].T + Xm[:, 3])
+    assert np.allclose(d2, want, atol=1e-14)
+
+
+def test_point_mesh_sphere_bounds(oracle_mod):
+    """A point at distance s from the centre of a geodesic sphere of radius r
+    (vertices on the sphere): s - r <= d <= s - r cos(theta) outside, where
+    theta bounds the angle from a face's centre to its vertices."""
+    f = 6
+    S = synth.geosphere(f, 1.0)
+    v, t = S
+    w = np.asarray(v, dtype=np.float64)[np.asarray(t)]
+    cen = w.mean(1)
+    cos_t = min(float(np.min(np.sum(w[:, k] * cen, 1) / (np.linalg.norm(w[:, k], axis=1) * np.linalg.norm(cen, axis=1))))
+                for k in range(3))
+    r = float(np.linalg.norm(np.asarray(v, dtype=np.float64), axis=1).max())
+    rng = np.random.default_rng(8)
+    dirs = rng.normal(size=(20, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    s = rng.uniform(1.2, 3.0, 20)
+    d, _, _ = oracle_mod.point_mesh(S, synth.identity_xform(), dirs * s[:, None])
+    assert np.all(d >= s - r - 1e-12)
+    assert np.all(d <= s - r * cos_t + 1e-12)
