@@ -133,13 +133,15 @@ typedef struct {
                               the first refit, at least one per query.  A min
                               query's repeated probes on fronts beyond 4 C use
                               at least 256 */
-    int64_t batch_budget;  /* batches: entries one query may push per level in
-                              the first round (default 2^18); a launch takes
-                              max_capacity / (2 x share) queries; a query that
-                              pushes more than its share in one level leaves
-                              the launch and goes to the next round, whose
-                              share is 16x larger (chunks 16x smaller); a
-                              chunk of one runs alone */
+    int64_t batch_budget;  /* batches: room per query and level in the first
+                              round (default 2^23); a launch takes max_capacity
+                              / (2 x budget) queries; half of the room is each
+                              query's own share, the other half a pool common
+                              to the launch; a query that pushes more than its
+                              share in one level draws on the pool, and when
+                              the pool is spent leaves the launch for the next
+                              round, whose budget is 16x larger (chunks 16x
+                              smaller); a chunk of one runs alone */
     int32_t bounds_mode;   /* 1: enhanced bounds, Eq. 10 (upper bound of the
                               min) and Eq. 11 (lower bound of the max), the
                               default; 2: conventional bounds only, Eq. 9 (the

@@ -74,6 +74,10 @@ struct gd_ctx {
     double* pts_dev = nullptr;               // staged host points and results
     gd_point_result* pres_dev = nullptr;
     long long cap_pts = 0;
+    unsigned long long* pkeys[2] = {nullptr, nullptr};  // Morton ordering of the points
+    unsigned* pvals[2] = {nullptr, nullptr};
+    unsigned* phist = nullptr;
+    long long cap_psort = 0;
     unsigned long long last_point_tests = 0, last_point_exact = 0;  // counters of the last point call
     gd_stats last{};
     bool stats_pending = false;  // last run was device-resident: stats still on the device
@@ -200,10 +204,18 @@ bool grow(gd_ctx* c) {
 // Entries one query of an m-query batch may push per level: every query at
 // its limit fills a front buffer, or half the leaf queue (the traversal
 // empties the leaf queue once it is half full).
-unsigned batch_share(long long cap_front, long long cap_leaf, long long m) {
-    if (m < 2) return 0u;
-    long long b = std::min(cap_front / m, cap_leaf / (2 * m));
-    return (unsigned)std::max(1ll, std::min(b, 0xffffffffll));
+// Per-level limits of a batch of m queries: each query's guaranteed share
+// (half of an even split of the room for one level's pushes: the front, or
+// the half of the leaf queue that a level may fill) and the common pool, the
+// rest of that room, from which queries that outgrow their share draw.
+void batch_limits(long long cap_front, long long cap_leaf, long long m, unsigned* share, unsigned* pool) {
+    *share = 0u;
+    *pool = 0u;
+    if (m < 2) return;
+    const long long room = std::min(cap_front, cap_leaf / 2);
+    const long long b = std::max(1ll, std::min(room / m / 2, 0xffffffffll));
+    *share = (unsigned)b;
+    *pool = (unsigned)std::max(0ll, std::min(room - m * b, 0xffffffffll));
 }
 
 // Queues of a batch of m queries: room for share entries per query and
@@ -391,7 +403,7 @@ gd_status batch_pass(gd_ctx* ctx, const gd_query* q, const std::vector<int64_t>&
     a.slot_of = ctx->slot_of;
     a.n_slot_of = (unsigned long long)tab;
     a.out = ctx->out_dev;
-    a.q_budget = batch_share(ctx->cap_front, ctx->cap_leaf, m);
+    batch_limits(ctx->cap_front, ctx->cap_leaf, m, &a.q_budget, &a.q_pool);
     int grid = grid_blocks(ctx, kind);
     GD_CUDA(ctx, launch_query(kind, a, grid, ctx->stream));
     GD_CUDA(ctx, cudaMemcpyAsync(ctx->out_host, ctx->out_dev, sizeof(gd_result) * m, cudaMemcpyDeviceToHost, ctx->stream));
@@ -455,7 +467,7 @@ GD_API gd_status gd_ctx_create(int device, gd_ctx** out) {
     c->tun.refit_mode = 1;
     c->tun.refit_slots = 1 << 13;
     c->tun.probes = 64;
-    c->tun.batch_budget = 1ll << 18;
+    c->tun.batch_budget = 1ll << 23;
     c->tun.bounds_mode = 1;
     *out = c;
     return GD_OK;
@@ -473,6 +485,8 @@ GD_API void gd_ctx_destroy(gd_ctx* c) {
     cudaFree(c->slot_of);
     cudaFree(c->naive_ws);
     cudaFree(c->point_ws); cudaFree(c->pts_dev); cudaFree(c->pres_dev);
+    cudaFree(c->pkeys[0]); cudaFree(c->pkeys[1]); cudaFree(c->pvals[0]); cudaFree(c->pvals[1]);
+    cudaFree(c->phist);
     cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -547,7 +561,7 @@ GD_API gd_status gd_autotune(gd_ctx* c, const gd_query* sample, int64_t n, int32
         {nullptr, &c->tun.probes, {1, 16, 64, 128}},
         {nullptr, &c->tun.blocks_per_sm, {1, 2}},
     };
-    if (n > 1) axes.push_back({&c->tun.batch_budget, nullptr, {1ll << 16, 1ll << 18, 1ll << 20}});
+    if (n > 1) axes.push_back({&c->tun.batch_budget, nullptr, {1ll << 18, 1ll << 20, 1ll << 22, 1ll << 23, 1ll << 24}});
     for (Axis& ax : axes) {
         const int64_t keep = ax.f64 ? *ax.f64 : *ax.f32;
         int64_t chosen = keep;
@@ -753,6 +767,8 @@ GD_API gd_status gd_mesh_download(const gd_mesh* m, float* boxes, int32_t* order
 }
 
 namespace {
+constexpr long long kPointSortMin = 1 << 14;  // smaller calls walk the points in the caller's order
+
 bool on_device(const void* p) {
     cudaPointerAttributes a{};
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -767,6 +783,7 @@ GD_API gd_status gd_point_distance(gd_ctx* ctx, const gd_mesh* M, const double x
                                    int64_t n, gd_point_result* out) {
     if (!ctx) return GD_ERR_INVALID_ARG;
     if (!x || n < 0 || (n > 0 && (!points || !out))) return fail(ctx, GD_ERR_INVALID_ARG, "NULL argument or n < 0");
+    if (n > (1ll << 31)) return fail(ctx, GD_ERR_INVALID_ARG, "at most 2^31 points per call");
     if (!M) return fail(ctx, GD_ERR_INVALID_ARG, "NULL mesh");
     if (M->ctx != ctx) return fail(ctx, GD_ERR_INVALID_ARG, "mesh belongs to another context");
     if (!M->built) return fail(ctx, GD_ERR_NOT_BUILT, "BVH not built (call gd_bvh_build)");
@@ -793,6 +810,27 @@ GD_API gd_status gd_point_distance(gd_ctx* ctx, const gd_mesh* M, const double x
     g.timeout_ns = ctx->tun.timeout_ns;
     if (!dev_in)
         GD_CUDA(ctx, cudaMemcpyAsync(ctx->pts_dev, points, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, ctx->stream));
+    // enough points to fill the GPU: walk them in Morton order (warps of
+    // nearby points visit the same nodes)
+    if (n >= kPointSortMin) {
+        if (n > ctx->cap_psort) {
+            for (int k = 0; k < 2; ++k) {
+                cudaFree(ctx->pkeys[k]); cudaFree(ctx->pvals[k]);
+                ctx->pkeys[k] = nullptr; ctx->pvals[k] = nullptr;
+            }
+            cudaFree(ctx->phist);
+            ctx->phist = nullptr;
+            ctx->cap_psort = 0;
+            for (int k = 0; k < 2; ++k) {
+                GD_CUDA(ctx, cudaMalloc(&ctx->pkeys[k], sizeof(unsigned long long) * n));
+                GD_CUDA(ctx, cudaMalloc(&ctx->pvals[k], sizeof(unsigned) * n));
+            }
+            GD_CUDA(ctx, cudaMalloc(&ctx->phist, sizeof(unsigned) * build_hist_words(n)));
+            ctx->cap_psort = n;
+        }
+        const int cur = sort_points(g, ctx->pkeys, ctx->pvals, ctx->phist, ctx->stream);
+        g.order = ctx->pvals[cur];
+    }
     GD_CUDA(ctx, launch_point(g, ctx->stream));
     if (!dev_out)
         GD_CUDA(ctx, cudaMemcpyAsync(out, ctx->pres_dev, sizeof(gd_point_result) * n, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1096,7 +1134,7 @@ gd_status serve_launch_batch(gd_ctx* ctx, SlotBuffers& sb, const gd_query* qs, l
     a.conventional = ctx->tun.bounds_mode == 2 ? 1 : 0;
     a.probes = ctx->tun.probes;
     a.n_slot_of = refit ? (unsigned long long)tab : 0ull;
-    a.q_budget = batch_share(sb.cap_front, sb.cap_leaf, m);
+    batch_limits(sb.cap_front, sb.cap_leaf, m, &a.q_budget, &a.q_pool);
     a.work_ctas = m == 1 ? single_work_ctas(ctx, grid) : (unsigned)grid;
     GD_CUDA(ctx, launch_query(kind, a, grid, sb.stream));
     GD_CUDA(ctx, cudaMemcpyAsync(sb.out_host, sb.out_dev, sizeof(gd_result) * m, cudaMemcpyDeviceToHost, sb.stream));

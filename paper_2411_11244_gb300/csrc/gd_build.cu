@@ -349,22 +349,28 @@ cudaError_t build_validate(const BuildBuffers& b, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+int radix_sort_pairs(unsigned long long* const keys[2], unsigned* const vals[2], long long n, int key_bits,
+                     unsigned* hist, cudaStream_t st) {
+    const long long nb = (n + kSortTile - 1) / kSortTile;
+    const int passes = (key_bits + 7) / 8;
+    int cur = 0;
+    for (int p = 0; p < passes; ++p) {
+        k_rs_hist<<<(unsigned)nb, kSortThreads, 0, st>>>(keys[cur], n, 8 * p, hist);
+        unsigned* sums = hist + nb * 256;
+        k_scan_sums<<<kScanCtas, kScanThreads, 0, st>>>(hist, nb * 256, sums);
+        k_scan_top<<<1, kScanThreads, 0, st>>>(sums);
+        k_scan_chunks<<<kScanCtas, kScanThreads, 0, st>>>(hist, nb * 256, sums);
+        k_rs_scatter<<<(unsigned)nb, kSortThreads, 0, st>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n,
+                                                             8 * p, hist);
+        cur ^= 1;
+    }
+    return cur;
+}
+
 cudaError_t build_tree(const BuildBuffers& b, cudaStream_t st) {
     k_morton<<<grid_for(b.nt, 256), 256, 0, st>>>(b.verts, b.tris, b.nt, b.flags, b.morton_bits, b.keys[0],
                                                   b.vals[0]);
-    const long long nb = (b.nt + kSortTile - 1) / kSortTile;
-    const int passes = (3 * b.morton_bits + 7) / 8;
-    int cur = 0;
-    for (int p = 0; p < passes; ++p) {
-        k_rs_hist<<<(unsigned)nb, kSortThreads, 0, st>>>(b.keys[cur], b.nt, 8 * p, b.hist);
-        unsigned* sums = b.hist + nb * 256;
-        k_scan_sums<<<kScanCtas, kScanThreads, 0, st>>>(b.hist, nb * 256, sums);
-        k_scan_top<<<1, kScanThreads, 0, st>>>(sums);
-        k_scan_chunks<<<kScanCtas, kScanThreads, 0, st>>>(b.hist, nb * 256, sums);
-        k_rs_scatter<<<(unsigned)nb, kSortThreads, 0, st>>>(b.keys[cur], b.vals[cur], b.keys[cur ^ 1],
-                                                             b.vals[cur ^ 1], b.nt, 8 * p, b.hist);
-        cur ^= 1;
-    }
+    const int cur = radix_sort_pairs(b.keys, b.vals, b.nt, 3 * b.morton_bits, b.hist, st);
     cudaError_t e = cudaMemcpyAsync(b.order, b.vals[cur], sizeof(unsigned) * b.nt, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return e;
     tree_boxes(b.verts, b.tris, b.nt, b.L, b.order, b.tri, b.box, nullptr, nullptr, nullptr, st);

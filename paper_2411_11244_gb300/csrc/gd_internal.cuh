@@ -93,12 +93,14 @@ enum : int {
     kCtrRem = 3,      // [3..5] max remaining depth of the entries of that front
     kCtrLeaf = 6,     // leaf-pair count
     kCtrCand = 7,     // candidate count
+    kCtrPool0 = 8,    // batch: entries taken from the common pool in the current level
     kCtrOverflow = 9, // some push exceeded its capacity
     kCtrJobs = 10,    // refit jobs appended (slot j refits job j)
     kCtrJobsDone = 11,// refit jobs already run
     kCtrTailDone = 12,// CTAs done with their candidate in the one-per-CTA tail
     kCtrBadIndex = 13,// an index check failed (bit per site); the access was skipped
     kCtrRefined = 14, // candidates refined in float64 (their indices are listed)
+    kCtrPool1 = 15,   //   ... by level parity (kCtrPool0: even pushes, kCtrPool1: odd)
     kCtrReset = 16,   // counters [0, kCtrReset) are cleared at kernel start
     kCtrAbort = 20,   // a wait gave up: every CTA leaves at its next barrier
     kCtrLastAbort = 21, // the abort flag of the last finished launch
@@ -166,6 +168,8 @@ struct KArgs {
     int k_max;
     long long timeout_ns;
     unsigned q_budget;          // batch: entries one query may push per level (0: no limit)
+    unsigned q_pool;            // batch: entries per level beyond their shares that the
+                                // queries of the launch may take, first come first served
     int fuse_root;              // single query, no refit claim at the root: phase 0 pushes
                                 // the root pair (phase 1 and its barrier are skipped)
     unsigned work_ctas;         // CTAs [0, work_ctas) run the traversal and meet at the

@@ -25,6 +25,12 @@ struct BuildBuffers {
 };
 
 size_t build_hist_words(long long nt);
+// stable LSD radix sort of n (key, value) pairs on the low key_bits bits of
+// the keys, 8 bits per pass, ping-ponging between keys[0|1] and vals[0|1]
+// (hist: build_hist_words(n) words); returns the index of the buffers that
+// hold the sorted pairs
+int radix_sort_pairs(unsigned long long* const keys[2], unsigned* const vals[2], long long n, int key_bits,
+                     unsigned* hist, cudaStream_t stream);
 // checks indices and finiteness, and bounds the referenced vertices (flags)
 cudaError_t build_validate(const BuildBuffers& b, cudaStream_t stream);
 // the rest of the build; only after build_validate reported clean flags
@@ -82,10 +88,16 @@ struct PointArgs {
     const double* pts;    // n x 3 world points, device
     long long n;
     gd_point_result* out; // n results, device
+    const unsigned* order;// thread i answers point order[i] (nullptr: point i)
     unsigned long long* ws;
     long long timeout_ns;
 };
 
+// order the points along a Morton curve in the mesh's frame so that a warp's
+// walks visit the same nodes: keys[0], vals[0] in, sorted pairs in buffers
+// [returned index]; hist: build_hist_words(n) words
+int sort_points(const PointArgs& g, unsigned long long* const keys[2], unsigned* const vals[2], unsigned* hist,
+                cudaStream_t stream);
 cudaError_t launch_point(const PointArgs& g, cudaStream_t stream);
 
 // ---- query (gd_query.cu)

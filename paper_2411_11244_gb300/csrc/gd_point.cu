@@ -182,7 +182,8 @@ __global__ void __launch_bounds__(kPointThreads) k_point(PointArgs g) {
         s_deadline = (old ? old : now) + (unsigned long long)g.timeout_ns;
     }
     __syncthreads();
-    const long long i = (long long)blockIdx.x * kPointThreads + threadIdx.x;
+    const long long t = (long long)blockIdx.x * kPointThreads + threadIdx.x;
+    const long long i = t < g.n && g.order ? (long long)g.order[t] : t;
     unsigned long long tests = 0, exact = 0;
     if (i < g.n && !(isfinite(g.pts[3 * i]) && isfinite(g.pts[3 * i + 1]) && isfinite(g.pts[3 * i + 2]))) {
         gd_point_result r{};
@@ -233,16 +234,47 @@ __global__ void __launch_bounds__(kPointThreads) k_point(PointArgs g) {
         }
         g.out[i] = r;
     }
-    unsigned long long t = tests, e = exact;
+    unsigned long long nt = tests, ne = exact;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        t += __shfl_down_sync(kFull, t, o);
-        e += __shfl_down_sync(kFull, e, o);
+        nt += __shfl_down_sync(kFull, nt, o);
+        ne += __shfl_down_sync(kFull, ne, o);
     }
     if ((threadIdx.x & 31) == 0) {
-        if (t) atomicAdd(ws + kPointTests, t);
-        if (e) atomicAdd(ws + kPointExact, e);
+        if (nt) atomicAdd(ws + kPointTests, nt);
+        if (ne) atomicAdd(ws + kPointExact, ne);
     }
+}
+
+// 10 bits of v spread to every third bit
+__device__ __forceinline__ unsigned long long spread10(unsigned v) {
+    unsigned long long r = 0;
+#pragma unroll
+    for (int b = 0; b < 10; ++b) r |= (unsigned long long)((v >> b) & 1u) << (3 * b);
+    return r;
+}
+
+// Morton key of each point in the mesh's frame, quantised in the root box
+// (points outside clamp to its faces: the key only orders the work)
+__global__ void k_point_keys(PointArgs g, unsigned long long* keys, unsigned* vals) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n) return;
+    const double* P = g.pts + 3 * i;
+    const double w0 = P[0] - g.x[3], w1 = P[1] - g.x[7], w2 = P[2] - g.x[11];
+    const double l[3] = {g.x[0] * w0 + g.x[4] * w1 + g.x[8] * w2, g.x[1] * w0 + g.x[5] * w1 + g.x[9] * w2,
+                         g.x[2] * w0 + g.x[6] * w1 + g.x[10] * w2};
+    unsigned long long key = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float lo = g.box[6 + k], hi = g.box[9 + k];
+        const float ext = hi - lo;
+        float f = ext > 0.f ? (float)((l[k] - lo) / ext) : 0.f;
+        f = f == f ? fminf(fmaxf(f, 0.f), 1.f) : 0.f;  // NaN (a non-finite point) to 0
+        const unsigned c = min(1023u, (unsigned)(f * 1024.f));
+        key |= spread10(c) << k;
+    }
+    keys[i] = key;
+    vals[i] = (unsigned)i;
 }
 
 __global__ void k_point_init(unsigned long long* ws) {
@@ -250,6 +282,12 @@ __global__ void k_point_init(unsigned long long* ws) {
 }
 
 }  // namespace
+
+int sort_points(const PointArgs& g, unsigned long long* const keys[2], unsigned* const vals[2], unsigned* hist,
+                cudaStream_t st) {
+    k_point_keys<<<(unsigned)((g.n + 255) / 256), 256, 0, st>>>(g, keys[0], vals[0]);
+    return radix_sort_pairs(keys, vals, g.n, 30, hist, st);
+}
 
 cudaError_t launch_point(const PointArgs& g, cudaStream_t st) {
     k_point_init<<<1, 32, 0, st>>>(g.ws);

@@ -983,8 +983,10 @@ __device__ void expand_level(const KArgs& A, int level, unsigned n, int s, unsig
         warp_bound_update<KIND>(A, survive, q, newU);
         if (A.q_budget) {
             // a batch query that pushes more than its share of the queues in
-            // this level leaves the batch (kStatEvict) and runs alone later,
-            // so that a few very large queries cannot crowd out the rest
+            // this level takes the excess from the launch's common pool; when
+            // that is spent it leaves the batch (kStatEvict) and runs later
+            // with a larger share, so that a few very large queries cannot
+            // crowd out the rest (shares plus pool never exceed the queues)
             const unsigned peers = __match_any_sync(kFull, survive ? q : 0xffffffffu);
             const int leader = __ffs(peers) - 1;
             unsigned over = 0u;
@@ -992,8 +994,11 @@ __device__ void expand_level(const KArgs& A, int level, unsigned n, int s, unsig
                 const unsigned cnt = __popc(peers);
                 const unsigned old = atomicAdd(&A.qs[q].pushed[(level + 1) & 1], cnt);
                 if (old + cnt > A.q_budget) {
-                    over = 1u;
-                    atomicOr(&A.qs[q].status, kStatEvict);
+                    const unsigned pold = atomicAdd(A.ctr + (((level + 1) & 1) ? kCtrPool1 : kCtrPool0), cnt);
+                    if (pold + cnt > A.q_pool) {
+                        over = 1u;
+                        atomicOr(&A.qs[q].status, kStatEvict);
+                    }
                 }
             }
             if (__shfl_sync(kFull, over, leader)) survive = false;
@@ -1031,18 +1036,80 @@ __device__ __forceinline__ void cta_merge_bound(unsigned long long w) {
     if (st) atomicOr(&c.stat, st);
 }
 
+// Tight bounds of the triangle pairs queued in the CTA's list (thread i takes
+// entry i < n; every thread calls, for the CTA-wide push): running-bound
+// update, candidates, and the D = 0 check of a pair that may touch.
+template <int KIND>
+__device__ __forceinline__ void leaf_tight(const KArgs& A, const uint4* list, unsigned n, int& pit, QView& V,
+                                          unsigned& tripairs, unsigned long long& bytes) {
+    bool have = false, emit = false;
+    float cb = 0.f;
+    unsigned newU = KIND == 0 ? 0xffffffffu : 0u;
+    unsigned ta = 0u, tb = 0u, q = 0u;
+    if (threadIdx.x < n) {
+        const uint4 e = list[threadIdx.x];
+        ta = e.x; tb = e.y; q = e.z;
+        view(A, q, V);
+        bool stop;
+        const float Ucur = load_Uq(A, q, &stop);
+        if (!stop) {
+            const Tri32 TA = load_tri(V.triA, ta), TB = load_tri(V.triB, tb);
+            // the bound may have moved since the pair was queued: test again
+            if (tri_pair_may_hold<KIND>(V, TA, TB, Ucur)) {
+                ++tripairs;
+                float lo, up;
+                tri_pair_bounds_tight<KIND>(A, q, V, TA, TB, &lo, &up);
+                have = true;
+                if (KIND == 0) {
+                    newU = __float_as_uint(up);
+                    cb = lo;
+                    emit = lo <= fminf(Ucur, up);
+                } else {
+                    newU = __float_as_uint(lo);
+                    cb = up;
+                    emit = up >= fmaxf(Ucur, lo);
+                }
+            }
+        }
+    }
+    warp_bound_update<KIND>(A, have, q, newU);
+    Cand c = {ta, tb, cb, q};
+    if (!cta_push2(pit++, c, emit, A.cand, A.ctr + kCtrCand, A.cap_cand, false, (Cand*)nullptr, (unsigned*)nullptr,
+                   0u))
+        mark_overflow(A, q);
+    if (emit) bytes += 16ull;
+    if (KIND == 0) {
+        // a pair that may touch: try to prove D_min = 0 with it
+        const unsigned m = __ballot_sync(kFull, emit && cb <= 0.f);
+        if (m) {
+            const int src = __ffs(m) - 1;
+            certify_zero(A, __shfl_sync(kFull, q, src), __shfl_sync(kFull, ta, src), __shfl_sync(kFull, tb, src));
+        }
+    }
+}
+
+// The leaf pairs' triangle pairs, 4 slots per leaf pair (<= 2 x 2 triangles),
+// in two stages per CTA: every thread takes one slot, loads its two
+// triangles and runs the cheap float32 test; the pairs that pass go to a
+// list in shared memory, and whenever it holds a CTA's worth (and at the
+// end) every thread takes one listed pair for the tight bounds.  Only a few
+// per cent of the pairs pass the cheap test, so bounding them densely keeps
+// whole warps on the expensive part instead of one lane in each.
 template <int KIND>
 __device__ void leaf_phase(const KArgs& A, unsigned nleaf, unsigned& tripairs, unsigned long long& bytes) {
+    __shared__ uint4 list[2 * kBlock];
+    __shared__ unsigned list_n;
     const unsigned long long total = (unsigned long long)nleaf * 4ull;
     const unsigned long long gstride = (unsigned long long)work_ctas(A) * blockDim.x;
-    unsigned* cand_cnt = A.ctr + kCtrCand;
     const bool pull = A.nq == 1 && threadIdx.x == 0;
+    const int lane = threadIdx.x & 31;
     QView V;
-    int iter = 0;
-    for (unsigned long long cbase = (unsigned long long)blockIdx.x * blockDim.x; cbase < total;
-         cbase += gstride, ++iter) {
+    int pit = 0;
+    if (threadIdx.x == 0) list_n = 0u;
+    for (unsigned long long cbase = (unsigned long long)blockIdx.x * blockDim.x; cbase < total; cbase += gstride) {
         // a single query whose traversal stopped (D = 0 proven) skips the rest
-        if (A.nq == 1 && __syncthreads_or((((volatile CtaState&)cta()).stat & kStatStop) != 0u)) break;
+        // (this barrier also publishes list_n)
+        if (__syncthreads_or(A.nq == 1 && (((volatile CtaState&)cta()).stat & kStatStop) != 0u)) break;
         // issued now, merged at the end of the iteration (the load's latency
         // hides behind this iteration's work)
         unsigned long long gw = 0;
@@ -1077,47 +1144,30 @@ __device__ void leaf_phase(const KArgs& A, unsigned nleaf, unsigned& tripairs, u
         if (KIND == 0) valid = valid && it.bound <= min_keep_threshold(Ucur, V.E_box);
         else valid = valid && it.bound >= max_keep_threshold(Ucur, V.E_box);
         if (valid && sub == 0) bytes += 16ull + 36ull * ((a1 - a0) + (b1 - b0));
-        bool emit = false;
-        float cb = 0.f;
-        unsigned newU = KIND == 0 ? 0xffffffffu : 0u;
-        bool have = false;
-        Tri32 TA, TB;
         if (valid) {
-            TA = load_tri(V.triA, ta);
-            TB = load_tri(V.triB, tb);
+            const Tri32 TA = load_tri(V.triA, ta), TB = load_tri(V.triB, tb);
             valid = tri_pair_may_hold<KIND>(V, TA, TB, Ucur);
         }
-        if (valid) {
-            ++tripairs;
-            float lo, up;
-            tri_pair_bounds_tight<KIND>(A, q, V, TA, TB, &lo, &up);
-            have = true;
-            if (KIND == 0) {
-                newU = __float_as_uint(up);
-                cb = lo;
-                emit = lo <= fminf(Ucur, up);
-            } else {
-                newU = __float_as_uint(lo);
-                cb = up;
-                emit = up >= fmaxf(Ucur, lo);
-            }
-        }
-        warp_bound_update<KIND>(A, have, q, newU);
-        Cand c = {ta, tb, cb, q};
-        if (!cta_push2(iter, c, emit, A.cand, cand_cnt, A.cap_cand, false, (Cand*)nullptr, (unsigned*)nullptr, 0u))
-            mark_overflow(A, q);
-        if (emit) bytes += 16ull;
-        if (KIND == 0) {
-            // a pair that may touch: try to prove D_min = 0 with it
-            const unsigned m = __ballot_sync(kFull, emit && cb <= 0.f);
-            if (m) {
-                const int src = __ffs(m) - 1;
-                certify_zero(A, __shfl_sync(kFull, q, src), __shfl_sync(kFull, ta, src),
-                             __shfl_sync(kFull, tb, src));
-            }
+        // queue the pairs that passed (one shared atomic per warp); the list
+        // holds < kBlock entries between iterations, so it never overflows
+        const unsigned m = __ballot_sync(kFull, valid);
+        unsigned base = 0u;
+        if (lane == 0 && m) base = atomicAdd(&list_n, (unsigned)__popc(m));
+        base = __shfl_sync(kFull, base, 0);
+        if (valid) list[base + __popc(m & lanemask_lt())] = make_uint4(ta, tb, q, 0u);
+        __syncthreads();
+        const unsigned n = list_n;
+        if (n >= (unsigned)kBlock) {
+            leaf_tight<KIND>(A, list + (n - kBlock), kBlock, pit, V, tripairs, bytes);
+            __syncthreads();
+            if (threadIdx.x == 0) list_n = n - kBlock;
         }
         if (pull) cta_merge_bound<KIND>(gw);
     }
+    __syncthreads();
+    const unsigned n = list_n;
+    if (n > 0u) leaf_tight<KIND>(A, list, n, pit, V, tripairs, bytes);
+    __syncthreads();
 }
 
 // ------------------------------------------------------------- phases 4-6
@@ -1654,6 +1704,7 @@ levels:
         if (lead) {
             A.ctr[kCtrCnt + (level + 2) % 3] = 0u;
             A.ctr[kCtrRem + (level + 2) % 3] = 0u;
+            A.ctr[(level & 1) ? kCtrPool1 : kCtrPool0] = 0u;  // the pool of level + 1's pushes
             if (level < 32) {
                 A.stats->front[level] = n;
                 A.stats->slots[level] = (unsigned)s;
