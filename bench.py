@@ -373,7 +373,7 @@ def bench_served(G, ctx, rates=(1000, 3000, 10000, 30000, 100000), n_req=1500, s
     for lam in rates:
         arrivals = np.cumsum(rng.exponential(1.0 / lam, size=n_req))
         # served
-        srv = G.gd_serve_start(ctx, slots=4, max_batch=256)
+        srv = G.gd_serve_start(ctx)  # default slots and batch size
         lat = [None] * n_req
         slot_of = {}
         serr = 0

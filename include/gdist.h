@@ -331,8 +331,8 @@ GD_API gd_status gd_batch_query(gd_ctx *ctx, const gd_query *q, int64_t n, gd_re
 /* ---- serving ----------------------------------------------------------- */
 
 typedef struct {
-    int32_t slots;            /* concurrent in-flight batches (default 4) */
-    int32_t max_batch;        /* queries per launch (default 1024) */
+    int32_t slots;            /* concurrent in-flight batches (default 2) */
+    int32_t max_batch;        /* queries per launch (default 16) */
     int64_t memory_budget;    /* bytes of work buffers across slots (default 8 GiB) */
     int32_t linger_us;        /* wait this long for more requests before
                                  launching a partial batch (default 0) */
@@ -341,8 +341,9 @@ typedef struct {
 /* Start a serving loop on ctx (continuous batching: queued requests are
  * admitted into free slots and launched while other slots are running). */
 GD_API gd_status gd_serve_start(gd_ctx *ctx, const gd_serve_opts *opts, gd_server **out);
-/* Enqueue one query; GD_ERR_BUSY if the queue is full or its footprint does
- * not fit the memory budget.  *ticket identifies the request. */
+/* Enqueue one query; GD_ERR_BUSY if the queue is full (max(4096, 16 x
+ * max_batch x slots) waiting requests) or the footprint of the waiting
+ * requests would exceed the memory budget.  *ticket identifies the request. */
 GD_API gd_status gd_serve_submit(gd_server *srv, const gd_query *q, uint64_t *ticket);
 /* GD_OK and *out filled if the ticket is done (the ticket is then released);
  * GD_ERR_NOT_READY otherwise. */
