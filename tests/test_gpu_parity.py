@@ -378,7 +378,7 @@ def test_autotune_keeps_answers(G, oracle_mod):
         t1 = G.gd_autotune(c, items[:1], reps=2)
         assert t1["k_max"] in (4, 5, 6, 7) and t1["work_target"] >= 1 << 16
         t2 = G.gd_autotune(c, items, reps=2)
-        assert t2["batch_budget"] in (1 << 16, 1 << 18, 1 << 20)
+        assert t2["batch_budget"] in (1 << 18, 1 << 20, 1 << 22, 1 << 23, 1 << 24)
         after = G.gd_batch_query(c, items)
         for i, (a, b, xa, xb, kind) in enumerate(items):
             same_answer(before[i], after[i], oracle_mod, A, xa, B, xb, "min" if kind == 0 else "max")
