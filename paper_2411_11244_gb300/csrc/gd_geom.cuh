@@ -60,12 +60,21 @@ __device__ __forceinline__ T clamp01(T s) {
     return s < T(0) ? T(0) : (s > T(1) ? T(1) : s);
 }
 
+// num / den clamped to [0, 1], for den > 0: the clamped cases are decided on
+// the numerator, so the (slow) division runs only for an interior value.
+template <class T>
+__device__ __forceinline__ T clamp_div(T num, T den) {
+    if (!(num > T(0))) return T(0);
+    if (num >= den) return T(1);
+    return clamp01(sdiv(num, den));
+}
+
 // Closest point to p on the segment a + s d, s in [0, 1].
 template <class T>
 __device__ __forceinline__ V3<T> closest_on_segment(V3<T> p, V3<T> a, V3<T> d) {
     T dd = dot(d, d);
     T s = T(0);
-    if (dd > T(0)) s = clamp01(sdiv(dot(p - a, d), dd));
+    if (dd > T(0)) s = clamp_div(dot(p - a, d), dd);
     return a + d * s;
 }
 
@@ -92,11 +101,13 @@ __device__ __forceinline__ V3<T> closest_on_triangle(V3<T> p, V3<T> a, V3<T> b, 
     T det = ssub(smul(g00, g11), smul(g01, g01));
     if (det > smul(smul(Tiny<T>::rel_det, g00), g11) && det > T(0)) {
         T r0 = dot(w, e0), r1 = dot(w, e1);
-        T u = sdiv(ssub(smul(g11, r0), smul(g01, r1)), det);
-        T v = sdiv(ssub(smul(g00, r1), smul(g01, r0)), det);
-        if (u >= T(0) && v >= T(0) && sadd(u, v) <= T(1)) {
+        // barycentric weights u = un / det, v = vn / det: the inside test on
+        // the numerators (det > 0), the divisions only for an inside point
+        T un = ssub(smul(g11, r0), smul(g01, r1));
+        T vn = ssub(smul(g00, r1), smul(g01, r0));
+        if (un >= T(0) && vn >= T(0) && sadd(un, vn) <= det) {
             *inside = true;
-            return a + e0 * u + e1 * v;
+            return a + e0 * sdiv(un, det) + e1 * sdiv(vn, det);
         }
     }
     *inside = false;
@@ -126,23 +137,23 @@ __device__ __forceinline__ void closest_segment_segment(V3<T> p0, V3<T> d1, V3<T
         s = t = T(0);
     } else if (!(a > T(0))) {
         s = T(0);
-        t = clamp01(sdiv(f, e));
+        t = clamp_div(f, e);
     } else {
         T c = dot(d1, r);
         if (!(e > T(0))) {
             t = T(0);
-            s = clamp01(sdiv(-c, a));
+            s = clamp_div(-c, a);
         } else {
             T b = dot(d1, d2);
             T den = ssub(smul(a, e), smul(b, b));
-            s = den > T(0) ? clamp01(sdiv(ssub(smul(b, f), smul(c, e)), den)) : T(0);
+            s = den > T(0) ? clamp_div(ssub(smul(b, f), smul(c, e)), den) : T(0);
             T tn = sadd(smul(b, s), f);
             if (tn < T(0)) {
                 t = T(0);
-                s = clamp01(sdiv(-c, a));
+                s = clamp_div(-c, a);
             } else if (tn > e) {
                 t = T(1);
-                s = clamp01(sdiv(ssub(b, c), a));
+                s = clamp_div(ssub(b, c), a);
             } else {
                 t = sdiv(tn, e);
             }
