@@ -840,6 +840,48 @@ def test_naive_comparator_deadline(G, ctx, oracle_mod):
         G.gd_mesh_destroy(ma)
 
 
+def test_one_to_many_batch(G, ctx, oracle_mod):
+    """1-to-N (Section 10): one mesh against N meshes of different kinds and
+    sizes in one batch; every answer matches the oracle, and so does the
+    nearest (farthest) of the N."""
+    rng = np.random.default_rng(61)
+    A = synth.torus(1.0, 0.3, 20, 12)
+    others = [synth.geosphere(4 + i % 4, 0.5 + 0.1 * i, 1e-3, i) if i % 3 == 0 else
+              synth.gear(64 + 16 * i, 2, teeth=8, seed=i) if i % 3 == 1 else
+              _soup(rng, 40 + 20 * i, 0.6) for i in range(9)]
+    ma = _mesh(G, ctx, A)
+    hs = [_mesh(G, ctx, m) for m in others]
+    try:
+        xa = _rigid(rng, 0.1)
+        for kind, gk in (("min", G.GD_MIN), ("max", G.GD_MAX)):
+            xbs = [synth.compose(synth.xform(np.eye(3), rng.normal(size=3) * 2.0),
+                                 synth.xform(synth.random_rotation(rng), (0, 0, 0))) for _ in others]
+            out = G.gd_batch_query(ctx, [(ma, h, xa, xb, gk) for h, xb in zip(hs, xbs)])
+            refs = []
+            for i, (m, xb) in enumerate(zip(others, xbs)):
+                ref = oracle_mod.brute(A, xa, m, xb, kind)
+                check(out[i], A, xa, m, xb, kind, ref, oracle_mod.diag(A, xa, m, xb), oracle_mod)
+                refs.append(ref.d)
+            best = min if kind == "min" else max
+            assert best(r.d for r in out) == pytest.approx(best(refs), rel=1e-12, abs=1e-15)
+    finally:
+        G.gd_mesh_destroy(ma)
+        for h in hs:
+            G.gd_mesh_destroy(h)
+
+
+def test_concentric_shells_min_max(G, ctx, oracle_mod):
+    """Two concentric geodesic spheres (the case Section 10 names as hard for
+    culling: every triangle of the inner one sits at nearly one distance from
+    the outer one), min and max against the oracle."""
+    outer = synth.geosphere(20, 1.0)
+    inner = synth.geosphere(14, 0.7)
+    rng = np.random.default_rng(62)
+    R = synth.random_rotation(rng)
+    c = rng.normal(size=3)
+    run_pair(G, ctx, oracle_mod, outer, inner, [(synth.xform(np.eye(3), c), synth.xform(R, c))])
+
+
 # ------------------------------------------------------------------ full-size workloads
 
 def test_rings_full_size_frames(G, ctx, oracle_mod):
