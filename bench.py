@@ -255,8 +255,29 @@ def bench_deformable(G, ctx, ma, frames=8):
 
     u_dev, q_dev, d_dev = run(dev)
     u_host, q_host, d_host = run([h.numpy() for h in host])
+    # device time of the update from device memory (events on the engine's
+    # stream around the synchronous call) against the HBM roofline: per
+    # triangle 4 B order + 12 B indices + 36 B vertices read and 48 B stored,
+    # 24 B per tree node, and the vertex copy (12 B per vertex each way)
+    es = torch.cuda.ExternalStream(G.gd_ctx_stream(ctx))
+    dt = []
+    for i in range(frames):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(es)
+        G.gd_mesh_update(mb, dev[i], ctx=ctx)
+        e1.record(es)
+        e1.synchronize()
+        dt.append(e0.elapsed_time(e1))
+    L, T = G.gd_mesh_info(mb)
+    nv = dev[0].numel() // 3
+    alg = 100 * T + 24 * (2 << L) + 24 * nv
+    peak, peak_kind = _peaks()
+    refit_ms = statistics.mean(dt)
     G.gd_mesh_destroy(mb)
     return {
+        "refit_device_ms": refit_ms,
+        "refit_roofline": {"bound": "hbm", "alg_bytes": alg, "achieved": alg / (refit_ms * 1e-3) / 1e9, "peak": peak,
+                           "unit": "GB/s", "frac": alg / (refit_ms * 1e-3) / 1e9 / peak, "peak_source": peak_kind},
         "workload": f"rings: 2 x {len(tb)} tris, B warped per frame (amplitude 0.01, surfaces apart)",
         "frames": frames,
         "update_ms_device_src": u_dev, "update_ms_host_src": u_host,
