@@ -10,6 +10,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import threading
 
 import numpy as np
 
@@ -261,10 +262,26 @@ def gd_mesh_download(mesh):
     return boxes, order
 
 
+_tls = threading.local()
+
+
+def _xbufs():
+    """Per-thread ctypes arrays for two transforms and numpy views of them
+    (numpy's .ctypes.data_as costs microseconds per call; filling a
+    preallocated array does not)."""
+    b = getattr(_tls, "x", None)
+    if b is None:
+        ba, bb = (C.c_double * 12)(), (C.c_double * 12)()
+        b = _tls.x = (ba, bb, np.frombuffer(ba, dtype=np.float64), np.frombuffer(bb, dtype=np.float64))
+    return b
+
+
 def _query(fn, ctx, A, B, xa, xb):
-    xa, xb = _x(xa), _x(xb)
+    ba, bb, va, vb = _xbufs()
+    va[:] = np.asarray(xa, dtype=np.float64).reshape(12)
+    vb[:] = np.asarray(xb, dtype=np.float64).reshape(12)
     r = gd_result()
-    rc = fn(ctx, A, B, xa.ctypes.data_as(_dp), xb.ctypes.data_as(_dp), C.byref(r))
+    rc = fn(ctx, A, B, ba, bb, C.byref(r))
     _check(rc, ctx)
     return r
 
