@@ -252,10 +252,10 @@ GD_API gd_status gd_max_distance(gd_ctx *ctx, const gd_mesh *A, const gd_mesh *B
  * direction of Section 10's future work, with N query points): for each of
  * n world points, the closest point of mesh M placed by x (12 doubles, as
  * for the mesh queries).  Exact in float64: one thread per point walks M's
- * tree twice (a float32 walk finds a near triangle whose float64 distance
- * bounds the answer; a second walk takes the float64 distance of every
- * triangle whose box is within that bound, boxes widened by the float32
- * error of the mapped point), so the result is the minimum over all
+ * tree once in float32 with a running bound that is always a true upper
+ * bound (each triangle's float32 closest point, widened for the float32
+ * errors), and takes the float64 distance of every triangle whose rigorous
+ * float32 lower bound is within it, so the result is the minimum over all
  * triangles, the smallest index among ties.  points: n x 3 float64; points
  * and out may each be host or device memory.  Synchronous.  Per-point
  * status in out; the call returns GD_ERR_TIMEOUT if some point passed the

@@ -4,21 +4,18 @@
 //
 // One thread per point walks the mesh's f12-BVH depth first, nearer child
 // first, with its own running bound (no atomics: the points are independent
-// problems).  Two passes keep float64 off the walk:
-//   1. a float32 walk in the mesh's frame finds the triangle with the least
-//      float32 distance; its float64 distance d1 is a true distance, hence an
-//      upper bound of the answer;
-//   2. a second walk with bound d1 computes the float64 distance of every
-//      triangle that may lie within d1: its box and its float32 separation
-//      from the point (along the direction to its float32 closest point) are
-//      both within d1, all tests widened outward by the float32 error of the
-//      mapped point and of the arithmetic; the least (d, original index)
-//      pair wins.
-// Pruning only ever drops triangles that are provably farther than a true
-// distance, so the answer is the exact minimum over all triangles, the
-// smallest original index among ties.  The separation test keeps float64
-// work to the near-ties even for a point that many triangles surround at
-// nearly one distance (the centre of a ring or a sphere).
+// problems).  Float64 stays off the walk: every triangle reached gets its
+// float32 closest point, which gives a rigorous float32 upper bound of its
+// distance (lowering the bound) and a rigorous lower bound (its separation
+// from the point along the direction to that closest point, widened for the
+// float32 error of the mapped point and of the arithmetic); only triangles
+// whose lower bound is within the bound get their float64 distance, and the
+// least (d, original index) pair wins.  Pruning only ever drops triangles
+// that are provably farther than a true distance, so the answer is the exact
+// minimum over all triangles, the smallest original index among ties.  The
+// separation test keeps float64 work to the near-ties even for a point that
+// many triangles surround at nearly one distance (the centre of a ring or a
+// sphere).
 #include <cfloat>
 #include <cstdint>
 
@@ -100,13 +97,36 @@ __device__ __forceinline__ double dist2_64(V3<double> p, const V3<float>* v, V3<
     return dot(d, d);
 }
 
-// One depth-first walk.  PASS 1: float32 distances, returns the triangle of
-// the least one in *best_j.  PASS 2: float64 distances of the triangles whose
-// box is within the bound, least (d2, id) in *best_d2, *best_id, *best_q.
-template <int PASS>
-__device__ bool walk(const PointArgs& g, V3<float> c, float E, V3<double> p64, float bound, unsigned* best_j,
-                     double* best_d2, int* best_id, V3<double>* best_q, unsigned long long* tests,
-                     unsigned long long* exact, unsigned long long deadline) {
+__device__ __forceinline__ float abs_max(V3<float> a) { return fmaxf(fabsf(a.x), fmaxf(fabsf(a.y), fabsf(a.z))); }
+
+// Rigorous float32 upper bound of the squared distance from any point within
+// E (per coordinate) of c to triangle v, given q, its float32 closest point
+// to c: q lies within a few units in the last place of the largest vertex
+// coordinate M of a point of the triangle (its barycentric or edge parameter
+// is clamped to the triangle, the rounding of the point's arithmetic is
+// charged as 2^-18 M per coordinate), so |c - q| grown by that and by E
+// bounds the true distance from above.  Rounded up throughout.
+__device__ __forceinline__ float upper_sq(V3<float> c, float E, const V3<float>* v, V3<float> q) {
+    const V3<float> d = c - q;
+    const float M = fmaxf(abs_max(v[0]), fmaxf(abs_max(v[1]), abs_max(v[2])));
+    const float slack = __fmul_ru(1.7320509f, __fadd_ru(E, __fmul_ru(M, 0x1p-18f)));
+    const float len = __fmul_ru(__fsqrt_ru(dot(d, d)), 1.f + 0x1p-20f);
+    const float up = __fadd_ru(len, slack);
+    return __fmul_ru(up, up);
+}
+
+// One depth-first walk, nearer child first, with a running bound U (squared)
+// that is a true upper bound of the answer at every step: each triangle
+// reached gets its float32 closest point, whose rigorous upper bound lowers
+// U, and a rigorous lower bound (the separation along the direction to that
+// point) decides whether the triangle can hold the minimum; those that can
+// get their float64 distance at once (least (d2, original index) kept).
+// Boxes and triangles beyond U are dropped, so every triangle at the
+// minimum is evaluated in float64; one evaluated while U was still looser
+// only costs work.
+__device__ bool walk(const PointArgs& g, V3<float> c, float E, V3<double> p64, double* best_d2, int* best_id,
+                     V3<double>* best_q, unsigned long long* tests, unsigned long long* exact,
+                     unsigned long long deadline) {
     const unsigned first_leaf = 1u << g.L;
     const float grow = 1.f + 0x1p-20f;
     unsigned st_node[kStack];
@@ -115,7 +135,7 @@ __device__ bool walk(const PointArgs& g, V3<float> c, float E, V3<double> p64, f
     st_gap[0] = node_gap_sq(g.box, 1u, c, E);
     int sp = 1;
     *tests += 1;
-    float U = bound;  // squared; pass 1: float32 distances, pass 2: float64 ones rounded up
+    float U = INFINITY;
     for (unsigned iter = 1; sp > 0; ++iter) {
         if ((iter & 127u) == 0u && globaltimer() > deadline) return false;
         --sp;
@@ -128,33 +148,23 @@ __device__ bool walk(const PointArgs& g, V3<float> c, float E, V3<double> p64, f
                 V3<float> v[3];
                 int id;
                 load_tri(g.tri, j, v, &id);
-                if (PASS == 1) {
-                    bool inside;
-                    const V3<float> q = closest_on_triangle<float>(c, v[0], v[1], v[2], &inside);
-                    const V3<float> d = c - q;
-                    const float d2 = dot(d, d);
-                    if (d2 < U || *best_j == 0xffffffffu) {
-                        U = fminf(U, d2);
-                        *best_j = j;
-                    }
-                } else {
-                    const float lo[3] = {fminf(v[0].x, fminf(v[1].x, v[2].x)), fminf(v[0].y, fminf(v[1].y, v[2].y)),
-                                         fminf(v[0].z, fminf(v[1].z, v[2].z))};
-                    const float hi[3] = {fmaxf(v[0].x, fmaxf(v[1].x, v[2].x)), fmaxf(v[0].y, fmaxf(v[1].y, v[2].y)),
-                                         fmaxf(v[0].z, fmaxf(v[1].z, v[2].z))};
-                    if (gap_sq(lo, hi, c, E) > U * grow) continue;
-                    bool inside;
-                    const V3<float> q32 = closest_on_triangle<float>(c, v[0], v[1], v[2], &inside);
-                    if (sep_lower_sq(c, E, v, q32) > U * grow) continue;
-                    V3<double> q;
-                    const double d2 = dist2_64(p64, v, &q);
-                    *exact += 1;
-                    if (d2 < *best_d2 || (d2 == *best_d2 && id < *best_id)) {
-                        *best_d2 = d2;
-                        *best_id = id;
-                        *best_q = q;
-                        U = fminf(U, __double2float_ru(d2));
-                    }
+                const float lo[3] = {fminf(v[0].x, fminf(v[1].x, v[2].x)), fminf(v[0].y, fminf(v[1].y, v[2].y)),
+                                     fminf(v[0].z, fminf(v[1].z, v[2].z))};
+                const float hi[3] = {fmaxf(v[0].x, fmaxf(v[1].x, v[2].x)), fmaxf(v[0].y, fmaxf(v[1].y, v[2].y)),
+                                     fmaxf(v[0].z, fmaxf(v[1].z, v[2].z))};
+                if (gap_sq(lo, hi, c, E) > U * grow) continue;
+                bool inside;
+                const V3<float> q32 = closest_on_triangle<float>(c, v[0], v[1], v[2], &inside);
+                U = fminf(U, upper_sq(c, E, v, q32));
+                if (sep_lower_sq(c, E, v, q32) > U * grow) continue;
+                V3<double> q;
+                const double d2 = dist2_64(p64, v, &q);
+                *exact += 1;
+                if (d2 < *best_d2 || (d2 == *best_d2 && id < *best_id)) {
+                    *best_d2 = d2;
+                    *best_id = id;
+                    *best_q = q;
+                    U = fminf(U, __double2float_ru(d2));
                 }
             }
             continue;
@@ -203,23 +213,10 @@ __global__ void __launch_bounds__(kPointThreads) k_point(PointArgs g) {
         const float E = fmaxf(fabsf(c.x), fmaxf(fabsf(c.y), fabsf(c.z))) * 0x1p-22f + FLT_MIN;
         gd_point_result r{};
         r.tri = -1;
-        unsigned best_j = 0xffffffffu;
         double d2 = INFINITY;
         int id = 0x7fffffff;
         V3<double> q = mk3(0.0, 0.0, 0.0);
-        bool ok = walk<1>(g, c, E, p64, INFINITY, &best_j, &d2, &id, &q, &tests, &exact, s_deadline);
-        if (ok && best_j != 0xffffffffu) {
-            V3<float> v[3];
-            int bid;
-            load_tri(g.tri, best_j, v, &bid);
-            V3<double> bq;
-            const double b2 = dist2_64(p64, v, &bq);
-            exact += 1;
-            d2 = b2;
-            id = bid;
-            q = bq;
-            ok = walk<2>(g, c, E, p64, __double2float_ru(b2), &best_j, &d2, &id, &q, &tests, &exact, s_deadline);
-        }
+        const bool ok = walk(g, c, E, p64, &d2, &id, &q, &tests, &exact, s_deadline);
         if (ok && id != 0x7fffffff) {
             r.d = sqrt(d2);
             r.tri = id;
