@@ -15,12 +15,13 @@ with host transforms and a host result (launch parameters in, result record
 out).  `--impl reference` times the FP64 CPU oracle on the same frames.
 
 Also reported (same run): "batched" -- 4,096 rigid transforms of one gear pair
-(204,800 triangles each) in one persistent launch against one launch per
-query; "served" -- a pool of 64 resident meshes under Poisson arrivals,
+(204,800 triangles each) in persistent launches of 64 queries against one
+launch per query; "served" -- a pool of 64 resident meshes under Poisson arrivals,
 continuous batching against one call per request, p50/p99 latency.
 
 Multi-GPU: queries are independent, so N ranks run replicas (each its own
-frames, no collective); value = queries of all ranks / max rank time.
+frames, no collective on the data path); value = max rank time / queries of
+all ranks (one all-reduce of the timed totals after the timed region).
 """
 
 from __future__ import annotations
@@ -67,6 +68,30 @@ def _dist():
     return rank, world, local
 
 
+def rank_frames(rank: int, world: int, n_frames: int, count: int):
+    """Frames of replica `rank` of `world`: rank, rank + world, ... (modulo the
+    frame count), so that the ranks' frames are disjoint while count * world
+    does not exceed n_frames."""
+    return [(rank + world * i) % n_frames for i in range(count)]
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest x over the ranks of the process group (x itself for one rank)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_ms(slowest_sum_ms: float, steps: int, world: int):
+    """Whole-job ms per query (the slowest rank's time over the queries of all
+    ranks) and ms per step of the slowest rank."""
+    return slowest_sum_ms / (steps * world), slowest_sum_ms / steps
+
+
 class ClockSampler:
     """nvidia-smi clock and throttle-reason samples during the timed region."""
 
@@ -81,7 +106,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "25"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -526,7 +551,7 @@ def main():
     stream = torch.cuda.Stream(dev)  # the engine's kernels, the flush and the events share it
     torch.cuda.set_stream(stream)
     sptr = stream.cuda_stream
-    frames = [(rank + world * i) % len(xbs) for i in range(args.warmup + args.steps)]
+    frames = rank_frames(rank, world, len(xbs), args.warmup + args.steps)
     d_xa = torch.tensor(np.asarray(xa), dtype=torch.float64, device=dev)
     d_xb = torch.tensor(np.stack([xbs[f] for f in frames]), dtype=torch.float64, device=dev)
     d_out = torch.zeros((len(frames), 10), dtype=torch.float64, device=dev)
@@ -556,11 +581,7 @@ def main():
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
     ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(ms), world, dev)
     # every result must be valid
     res = d_out.cpu().numpy()
     import ctypes
@@ -576,13 +597,14 @@ def main():
         t1 = time.perf_counter()
         G.gd_min_distance(ctx, ma, mb, xa, xbs[frames[args.warmup + s]])
         e2e_ms.append(1000.0 * (time.perf_counter() - t1))
+    e2e_mean, _ = whole_job_ms(max_over_ranks(sum(e2e_ms), world, dev), args.steps, world)
 
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
         return
     # whole job: the slowest rank's time over the queries of all ranks
-    mean_ms = total_ms / (args.steps * world)
+    mean_ms, step_ms = whole_job_ms(total_ms, args.steps, world)
     sorted_ms = sorted(ms)
     p50 = sorted_ms[len(ms) // 2]
     p99 = sorted_ms[min(len(ms) - 1, int(0.99 * len(ms)))]
@@ -591,12 +613,12 @@ def main():
     achieved = alg / (statistics.mean(ms) * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": mean_ms, "unit": "ms/query", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "frames": 100, "l2": "flushed (512 MB write) before every step",
                    "p50_ms": p50, "p99_ms": p99, "bvh_build_ms_per_mesh": build_ms,
                    "paper_context_ms": 0.38, "paper_context_gpu": "RTX 4090 (FP32 only)"},
-        "e2e": {"value": statistics.mean(e2e_ms), "unit": "ms/query", "h2d_bytes_per_step": 192,
+        "e2e": {"value": e2e_mean, "unit": "ms/query", "h2d_bytes_per_step": 192,
                 "d2h_bytes_per_step": 336, "p50_ms": sorted(e2e_ms)[len(e2e_ms) // 2]},
         "gpu_launches": args.steps * world,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
