@@ -3,6 +3,7 @@
 // buffers and launches; every step of the computation runs in the kernels of
 // gd_build.cu and gd_query.cu.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -58,6 +59,8 @@ struct gd_ctx {
     long long cap_front = 0, cap_leaf = 0, cap_cand = 0;
     Mailbox* mb_dev = nullptr;   // single-query results, stats and counters
     Mailbox* mb_host = nullptr;  // pinned mirror
+    HostDone* hd = nullptr;      // pinned result record of a single query, written by the kernel
+    unsigned long long hd_seq = 0;
     QState* qs = nullptr;
     QIn* qin_dev = nullptr;
     QIn* qin_host = nullptr;
@@ -167,6 +170,8 @@ gd_status ensure_ws(gd_ctx* c, long long nq) {
         GD_CUDA(c, cudaMalloc(&c->mb_dev, sizeof(Mailbox)));
         GD_CUDA(c, cudaMemset(c->mb_dev, 0, sizeof(Mailbox)));
         GD_CUDA(c, cudaMallocHost(&c->mb_host, sizeof(Mailbox)));
+        GD_CUDA(c, cudaMallocHost(&c->hd, sizeof(HostDone)));
+        std::memset(c->hd, 0, sizeof(HostDone));
     }
     if (!c->ready) {
         c->cap_front = std::min<long long>(c->tun.front_capacity, 0xffffffffll);
@@ -350,23 +355,51 @@ gd_status run_single(gd_ctx* ctx, const gd_mesh* A, const gd_mesh* B, int kind, 
         int grid = grid_blocks(ctx, kind);
         a.work_ctas = single_work_ctas(ctx, grid);
         a.fuse_root = single_fuse_root(ctx, B);
+        // the launch's last CTA writes the result record to pinned host
+        // memory and stamps it with seq: no copy to enqueue and no stream
+        // synchronisation on the way back
+        const unsigned long long seq = ++ctx->hd_seq;
+        a.host_done = ctx->hd;
+        a.seq = seq;
         GD_CUDA(ctx, launch_query(kind, a, grid, ctx->stream));
-        GD_CUDA(ctx, cudaMemcpyAsync(ctx->mb_host, ctx->mb_dev, kResultBytes, cudaMemcpyDeviceToHost, ctx->stream));
-        GD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-        const Mailbox& m = *ctx->mb_host;
+        const volatile unsigned long long* stamp = &ctx->hd->seq;
+        bool got = false;
+        for (unsigned spin = 1;; ++spin) {
+            if (*stamp == seq) { got = true; break; }
+            if ((spin & 4095u) == 0u) {
+                // a launch that ended (or failed) without the record
+                const cudaError_t q = cudaStreamQuery(ctx->stream);
+                if (q == cudaSuccess) { got = *stamp == seq; break; }
+                if (q != cudaErrorNotReady) return cuda_fail(ctx, q, "query launch");
+            }
+        }
+        std::atomic_thread_fence(std::memory_order_acquire);
+        gd_result r;
+        unsigned last_abort, bad_index;
+        if (got) {
+            std::memcpy(&r, (const void*)&ctx->hd->out, sizeof(r));
+            last_abort = ctx->hd->last_abort;
+            bad_index = ctx->hd->bad_index;
+        } else {
+            GD_CUDA(ctx, cudaMemcpyAsync(ctx->mb_host, ctx->mb_dev, kResultBytes, cudaMemcpyDeviceToHost, ctx->stream));
+            GD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+            r = ctx->mb_host->out;
+            last_abort = ctx->mb_host->ctr[kCtrLastAbort];
+            bad_index = ctx->mb_host->ctr[kCtrBadIndex];
+        }
         ctx->stats_pending = true;
         ctx->last_grid = grid;
         ctx->pending_retries = retries;
-        if (m.ctr[kCtrLastAbort]) return fail(ctx, GD_ERR_TIMEOUT, "a device-side wait timed out");
-        if (m.ctr[kCtrBadIndex])
-            return fail(ctx, GD_ERR_CUDA, "internal index check failed (sites " + std::to_string(m.ctr[kCtrBadIndex]) + ")");
-        if (m.out.status == GD_ERR_OVERFLOW) {
+        if (last_abort) return fail(ctx, GD_ERR_TIMEOUT, "a device-side wait timed out");
+        if (bad_index)
+            return fail(ctx, GD_ERR_CUDA, "internal index check failed (sites " + std::to_string(bad_index) + ")");
+        if (r.status == GD_ERR_OVERFLOW) {
             if (!grow(ctx)) return fail(ctx, GD_ERR_OVERFLOW, "work queues exceeded max_capacity");
             ++retries;
             continue;
         }
-        *out = m.out;
-        if (m.out.status != GD_OK) return fail(ctx, (gd_status)m.out.status, "query failed");
+        *out = r;
+        if (r.status != GD_OK) return fail(ctx, (gd_status)r.status, "query failed");
         return GD_OK;
     }
 }
@@ -480,6 +513,7 @@ GD_API void gd_ctx_destroy(gd_ctx* c) {
     free_ws(c);
     cudaFree(c->mb_dev);
     cudaFreeHost(c->mb_host);
+    cudaFreeHost(c->hd);
     cudaFree(c->qs); cudaFree(c->qin_dev); cudaFree(c->out_dev);
     cudaFreeHost(c->qin_host); cudaFreeHost(c->out_host);
     cudaFree(c->slot_of);
@@ -597,6 +631,7 @@ GD_API gd_status gd_get_stats(gd_ctx* c, gd_stats* o) {
         // a device-resident query ran on a caller's stream: wait for the device
         cudaSetDevice(c->device);
         GD_CUDA(c, cudaDeviceSynchronize());
+        GD_CUDA(c, cudaStreamSynchronize(c->stream));  // the launch may still be leaving
         GD_CUDA(c, cudaMemcpy(&c->mb_host->stats, &c->mb_dev->stats, sizeof(StatsDev), cudaMemcpyDeviceToHost));
         to_stats(c->mb_host->stats, (unsigned)c->last_grid, c->pending_retries, &c->last);
         c->stats_pending = false;

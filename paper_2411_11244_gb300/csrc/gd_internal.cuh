@@ -134,6 +134,15 @@ struct StatsDev {
     unsigned refits;        // B subtrees refit into A's frame
 };
 
+// Result record of a single query in pinned host memory, written by the
+// launch's last CTA (the host polls seq instead of copying and synchronising)
+struct HostDone {
+    gd_result out;
+    unsigned last_abort;          // the launch's abort flag
+    unsigned bad_index;           // sites of failed index checks
+    unsigned long long seq;       // written last: the launch's sequence number
+};
+
 struct KArgs {
     int nq;
     const QIn* qin;             // batch: per-query meshes and transforms
@@ -174,6 +183,8 @@ struct KArgs {
                                 // the root pair (phase 1 and its barrier are skipped)
     unsigned work_ctas;         // CTAs [0, work_ctas) run the traversal and meet at the
                                 // grid barriers; the rest run background probes (0: all)
+    HostDone* host_done;        // single query: copy of the result for the host (or nullptr)
+    unsigned long long seq;     // ... stamped with this sequence number
 };
 
 // ------------------------------------------------------------------ memory

@@ -1909,6 +1909,19 @@ done:
                 atomicExch(A.ctr + kCtrSetupDone, 0u);
                 atomicExch(A.ctr + kCtrExit, 0u);
                 __threadfence();
+                if (A.host_done) {
+                    // every other CTA has left (their writes, the result
+                    // record among them, were fenced before their exit count)
+                    HostDone* h = A.host_done;
+                    static_assert(sizeof(gd_result) % 8 == 0, "result record copied in 8-byte words");
+                    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(A.out);
+                    unsigned long long* dst = reinterpret_cast<unsigned long long*>(&h->out);
+                    for (int k = 0; k < (int)(sizeof(gd_result) / 8); ++k) dst[k] = __ldcg(src + k);
+                    h->last_abort = ab;
+                    h->bad_index = ld_relaxed(A.ctr + kCtrBadIndex);
+                    __threadfence_system();
+                    *reinterpret_cast<volatile unsigned long long*>(&h->seq) = A.seq;
+                }
             }
         }
     }
