@@ -241,8 +241,10 @@ GD_API gd_status gd_mesh_download(const gd_mesh *mesh, float *boxes, int32_t *tr
 /* ---- queries (Algorithms 1-2; Sections 5-7) ------------------------------ */
 
 /* Minimum distance D_min (Eq. 1).  xa, xb: host transforms.  Synchronous:
- * copies the transforms to the device, runs one persistent traversal launch,
- * copies the result back. */
+ * the transforms travel as launch parameters, one persistent traversal
+ * launch runs, and its last CTA writes the result record to the context's
+ * pinned host memory, which the call waits for (bounded by the launch's own
+ * completion; no stream synchronisation on the way back). */
 GD_API gd_status gd_min_distance(gd_ctx *ctx, const gd_mesh *A, const gd_mesh *B, const double xa[12],
                                  const double xb[12], gd_result *out);
 /* Maximum distance D_max (Eq. 2); same contract as gd_min_distance. */
