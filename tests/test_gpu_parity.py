@@ -891,6 +891,24 @@ def test_rings_full_size_frames(G, ctx, oracle_mod):
     run_pair(G, ctx, oracle_mod, A, B, [(xa, xbs[i]) for i in (0, 37, 99)], kinds=("min",), bvh_oracle=True)
 
 
+def test_gears_full_size_batch_sample(G, ctx, oracle_mod):
+    """The 4,096-transform gear workload at full size (204,800 triangles per
+    gear): 16 transforms spread over the set (4 of them intersecting), in one
+    batch as `bench.py` runs them, against the oracle's float64 BVH traversal."""
+    A, B, xa, xbs = synth.config_gears(4096)
+    idx = [256 * i + 7 for i in range(16)]
+    ma, mb = _mesh(G, ctx, A), _mesh(G, ctx, B)
+    try:
+        out = G.gd_batch_query(ctx, [(ma, mb, xa, xbs[i], G.GD_MIN) for i in idx])
+        refs = oracle_mod.bvh_query_batch(oracle_mod.Bvh(A), xa, oracle_mod.Bvh(B), [xbs[i] for i in idx], "min")
+        assert sum(1 for r in refs if r.d == 0.0) == 4
+        for k, i in enumerate(idx):
+            check(out[k], A, xa, B, xbs[i], "min", refs[k], oracle_mod.diag(A, xa, B, xbs[i]), oracle_mod)
+    finally:
+        G.gd_mesh_destroy(ma)
+        G.gd_mesh_destroy(mb)
+
+
 def test_icospheres_full_size_min_max(G, ctx, oracle_mod):
     """Two 1.31 M-triangle noisy spheres at a gap of 1e-5 x diag, min and max."""
     A, B, xa, xb = synth.config_icospheres(level=8)
