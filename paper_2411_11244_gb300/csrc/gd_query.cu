@@ -411,10 +411,24 @@ template <int KIND>
 __device__ __forceinline__ void tri_bounds_core(const V3<float>* Al, const V3<float>* Bl, float E, float* lo,
                                                 float* up) {
     if (KIND == 0) {
-        V3<float> P, Q;
-        float d2;
-        bool hit;
-        tri_tri_min(Al, Bl, &P, &Q, &d2, &hit);
+        // the 21 feature pairs one after another (not unrolled): this code
+        // runs once or a few times per CTA and query, and a compact loop is
+        // fetched once where the unrolled form is fetched instruction by
+        // instruction from L2
+        V3<float> P = Al[0], Q = Bl[0];
+        float d2 = INFINITY;
+#pragma unroll 1
+        for (int f = 0; f < 21; ++f) {
+            V3<float> p, q;
+            float e2;
+            bool h;
+            tri_feature(f, Al, Bl, &p, &q, &e2, &h);
+            if (h) {
+                P = p; Q = p; d2 = 0.f;
+                break;
+            }
+            if (e2 < d2) { d2 = e2; P = p; Q = q; }
+        }
         *up = upper_from_sq(d2, E);
         float l = 0.f;
         V3<float> nrm = P - Q;
