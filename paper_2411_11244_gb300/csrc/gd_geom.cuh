@@ -257,12 +257,16 @@ __device__ __forceinline__ void tri_feature(int f, const V3<T>* A, const V3<T>* 
         const V3<T> a0 = pick3(A, i), a1 = pick3(A, i == 2 ? 0 : i + 1);
         const V3<T> b0 = pick3(B, j), b1 = pick3(B, j == 2 ? 0 : j + 1);
         closest_segment_segment(a0, a1 - a0, b0, b1 - b0, P, Q);
-    } else if (f < 12) {
-        *P = pick3(A, f - 9);
-        *Q = closest_on_triangle(*P, B[0], B[1], B[2], &in);
     } else if (f < 15) {
-        *Q = pick3(B, f - 12);
-        *P = closest_on_triangle(*Q, A[0], A[1], A[2], &in);
+        // a vertex of one triangle against the other (one code path for both
+        // directions: the lanes of a warp that hold f in [9, 15) do not split)
+        const bool va = f < 12;
+        const int i = f - (va ? 9 : 12);
+        const V3<T> v = va ? pick3(A, i) : pick3(B, i);
+        const V3<T> t0 = va ? B[0] : A[0], t1 = va ? B[1] : A[1], t2 = va ? B[2] : A[2];
+        const V3<T> c = closest_on_triangle(v, t0, t1, t2, &in);
+        *P = va ? v : c;
+        *Q = va ? c : v;
     } else if (f < 21) {
         const bool ea = f < 18;
         const int i = f - (ea ? 15 : 18), j = i == 2 ? 0 : i + 1;
