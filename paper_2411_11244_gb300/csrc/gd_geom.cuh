@@ -148,14 +148,16 @@ __device__ __forceinline__ void closest_segment_segment(V3<T> p0, V3<T> d1, V3<T
             T den = ssub(smul(a, e), smul(b, b));
             s = den > T(0) ? clamp_div(ssub(smul(b, f), smul(c, e)), den) : T(0);
             T tn = sadd(smul(b, s), f);
-            if (tn < T(0)) {
-                t = T(0);
-                s = clamp_div(-c, a);
-            } else if (tn > e) {
-                t = T(1);
-                s = clamp_div(ssub(b, c), a);
+            // t clamped to 0 or 1 re-optimises s; otherwise t = tn / e.  One
+            // division on every path, so the lanes of a warp do not split
+            // over three copies of it
+            const bool lo = tn < T(0), hi = tn > e;
+            const T r = clamp_div(lo ? -c : (hi ? ssub(b, c) : tn), (lo || hi) ? a : e);
+            if (lo || hi) {
+                t = lo ? T(0) : T(1);
+                s = r;
             } else {
-                t = sdiv(tn, e);
+                t = r;
             }
         }
     }
