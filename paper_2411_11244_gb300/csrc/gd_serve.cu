@@ -151,6 +151,10 @@ void harvest(gd_server* S, Slot& s) {
 
 void run_loop(gd_server* S) {
     cudaSetDevice(serve_device(S->ctx));
+    // the loop stays awake (yielding) this long after its last work, so that
+    // a request arriving in a steady stream is not delayed by a thread wake-up
+    const auto kStayAwake = std::chrono::milliseconds(20);
+    auto last_work = std::chrono::steady_clock::now();
     for (;;) {
         bool worked = false;
         // harvest finished slots; a slot whose stream reports an error (the
@@ -242,14 +246,18 @@ void run_loop(gd_server* S) {
             std::lock_guard<std::mutex> g(S->mu);
             if (idle && S->queue.empty()) break;
         }
+        const auto now = std::chrono::steady_clock::now();
+        if (worked) last_work = now;
         if (!worked) {
             std::unique_lock<std::mutex> g(S->mu);
             bool any_busy = false;
             for (Slot& s : S->slots) any_busy = any_busy || s.busy;
-            if (S->queue.empty() && !any_busy && !S->stop.load())
+            if (S->queue.empty() && !any_busy && !S->stop.load() && now - last_work > kStayAwake) {
                 S->cv.wait_for(g, std::chrono::milliseconds(2));
-            else
+            } else {
+                g.unlock();
                 std::this_thread::yield();
+            }
         }
     }
 }
