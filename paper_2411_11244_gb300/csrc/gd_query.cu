@@ -1550,6 +1550,50 @@ __device__ void finalize_phase(const KArgs& A, RefinedSet R, unsigned long long 
     }
 }
 
+// Single query, CTA 0 alone: the witness selection and the result record in
+// one pass (select_phase then finalize_phase load every refined candidate
+// twice, each through a chain of dependent loads): every thread keeps its
+// least original (tri_a, tri_b) at the extreme, the CTA takes the least, and
+// the thread that holds it writes the record.  The triangle arrays come from
+// the CTA's copy of the query's constants.
+__device__ void select_finalize_single(const KArgs& A, RefinedSet R) {
+    __shared__ unsigned long long s_key;
+    if (threadIdx.x == 0) s_key = 0xffffffffffffffffull;
+    __syncthreads();
+    QState& s = A.qs[0];
+    const unsigned long long best = ld_relaxed64(&s.best_d);
+    const float4* triA = cta().v.triA;
+    const float4* triB = cta().v.triB;
+    unsigned long long mykey = 0xffffffffffffffffull;
+    unsigned myi = 0;
+    for (unsigned k = threadIdx.x; k < R.n; k += blockDim.x) {
+        const unsigned i = R.at(k);
+        if (i >= A.cap_cand) continue;
+        if ((unsigned long long)__double_as_longlong(__ldcg(A.cand_d + i)) != best) continue;
+        float4 raw = __ldcg(reinterpret_cast<const float4*>(A.cand + i));
+        const Cand c = *reinterpret_cast<Cand*>(&raw);
+        if (c.q != 0u) continue;  // flagged by the refinement
+        const unsigned ia = (unsigned)__float_as_int(__ldg(triA + 3ull * c.ta + 2).y);
+        const unsigned ib = (unsigned)__float_as_int(__ldg(triB + 3ull * c.tb + 2).y);
+        const unsigned long long key = ((unsigned long long)ia << 32) | ib;
+        if (key < mykey) { mykey = key; myi = i; }
+    }
+    if (mykey != 0xffffffffffffffffull) atomicMin(&s_key, mykey);
+    __syncthreads();
+    if (mykey != 0xffffffffffffffffull && mykey == s_key) {
+        // ties hold the same pair: equal records
+        const double* w = A.cand_pts + 6ull * myi;
+        gd_result& r = A.out[0];
+        r.d = __longlong_as_double((long long)best);
+        r.tri_a = (long long)(mykey >> 32);
+        r.tri_b = (long long)(mykey & 0xffffffffull);
+        r.pa[0] = __ldcg(w); r.pa[1] = __ldcg(w + 1); r.pa[2] = __ldcg(w + 2);
+        r.pb[0] = __ldcg(w + 3); r.pb[1] = __ldcg(w + 4); r.pb[2] = __ldcg(w + 5);
+        s.best_key = mykey;
+    }
+    __syncthreads();
+}
+
 __device__ void status_phase(const KArgs& A, unsigned long long first, unsigned long long gstride) {
     for (unsigned long long q = first; q < (unsigned)A.nq; q += gstride) {
         QState& s = A.qs[q];
@@ -1841,11 +1885,16 @@ levels:
                 if (s_go) {
                     lap(6);
                     const RefinedSet R{nullptr, nc};
-                    select_phase(A, R, threadIdx.x, blockDim.x);
-                    __syncthreads();
-                    lap(7);
-                    finalize_phase(A, R, threadIdx.x, blockDim.x);
-                    __syncthreads();
+                    if (A.nq == 1) {
+                        select_finalize_single(A, R);
+                        lap(7);
+                    } else {
+                        select_phase(A, R, threadIdx.x, blockDim.x);
+                        __syncthreads();
+                        lap(7);
+                        finalize_phase(A, R, threadIdx.x, blockDim.x);
+                        __syncthreads();
+                    }
                     status_phase(A, threadIdx.x, blockDim.x);
                     __syncthreads();
                     lap(8);
@@ -1861,11 +1910,8 @@ levels:
             // one query: CTA 0 selects and writes the witness alone (the refined
             // candidates are few), no further grid barrier
             if (blockIdx.x == 0) {
-                select_phase(A, R, threadIdx.x, blockDim.x);
-                __syncthreads();
+                select_finalize_single(A, R);
                 lap(7);
-                finalize_phase(A, R, threadIdx.x, blockDim.x);
-                __syncthreads();
                 status_phase(A, threadIdx.x, blockDim.x);
                 lap(8);
             }
