@@ -588,7 +588,6 @@ def main():
     total_ms = max_over_ranks(sum(ms), world, dev)
     # every result must be valid
     res = d_out.cpu().numpy()
-    import ctypes
     for i in range(len(frames)):
         r = G.gd_result.from_buffer_copy(res[i].tobytes())
         assert r.status == 0, (i, r.status)
