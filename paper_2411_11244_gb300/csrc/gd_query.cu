@@ -370,11 +370,15 @@ __device__ __forceinline__ bool cta_push2(int it, const E& v, bool want0, E* buf
     return ok;
 }
 
-// Refit slot holding B node b (depth db >= dR) in A's frame, or kNoSlot.
+// Refit slot holding B node b (depth db >= dR) in A's frame, or kNoSlot.  A
+// refit publishes its slot index (after a fence) only once its boxes are
+// written, and the refit jobs run beside the next level's expansion (no grid
+// barrier between them): the acquire load makes the boxes visible with the
+// index; a root still being refit reads as kNoSlot (mapped local boxes).
 __device__ __forceinline__ unsigned refit_slot(const KArgs& A, const QView& V, unsigned b, int db) {
     if (V.dR < 0 || db < V.dR) return kNoSlot;
     unsigned root = b >> (db - V.dR);
-    unsigned s = __ldcg(A.slot_of + V.slot_base + (root - (1u << V.dR)));
+    unsigned s = ld_acquire(A.slot_of + V.slot_base + (root - (1u << V.dR)));
     return s < A.cap_slots ? s : kNoSlot;
 }
 
@@ -1636,7 +1640,9 @@ __device__ bool refit_jobs(const KArgs& A, bool lead, unsigned& refits, bool* ra
         if (ok) refit_subtree(A, job.x, job.y, j);
         else if (threadIdx.x == 0) flag_bad(A, kBadJob);
     }
-    if (!sync(A)) return false;
+    // no grid barrier: every CTA goes on to the level with its own job done;
+    // the others' refits become visible root by root (refit_slot).  The
+    // counter is read again only after the level's barrier.
     if (lead) {
         A.ctr[kCtrJobsDone] = jobs;
         refits = jobs;
