@@ -883,6 +883,111 @@ __device__ void bg_probe_cta(const KArgs& A) {
 
 // ------------------------------------------------------------- phase 0
 
+// Widening of a query's float32 map: every mapped coordinate is within
+// e_c = gamma_10 (sqrt(3) P_B + |t|_inf) of its exact value; E_box =
+// sqrt(3) e_c; the triangle narrow phase adds 256 u X for its own
+// arithmetic on coordinates of magnitude <= X; the double-float map
+// (including the shift to A's vertex) makes about a dozen roundings of
+// relative size 2^-46 on terms of magnitude <= P_A + sqrt(3) P_B + |t|, plus
+// the float64 relative map itself.  The inputs are floats, the constants are
+// rounded up and every operation rounds up, so each result bounds its
+// real-valued expression from above (the 1.000001 factors are margin).
+__device__ __forceinline__ void setup_widening(QState& s, float PA, float PB0, float tinf) {
+    constexpr float kSqrt3Up = 1.7320509f;        // > sqrt(3)
+    constexpr float kGamma10Up = 5.9604682e-07f;  // > 10 u / (1 - 10 u), u = 2^-24
+    constexpr float kMarginUp = 1.0000011f;       // > 1.000001
+    const float PB = __fmul_ru(PB0, kMarginUp);
+    const float reach = __fadd_ru(__fmul_ru(kSqrt3Up, PB), tinf);  // sqrt(3) P_B + |t|_inf
+    const float Eb = __fmul_ru(__fmul_ru(kSqrt3Up, __fmul_ru(kGamma10Up, reach)), kMarginUp);
+    const float Xm = __fadd_ru(__fmul_ru(fmaxf(PA, reach), kMarginUp), Eb);
+    s.E_box = Eb;
+    s.E_tri = __fadd_ru(Eb, __fmul_ru(256.f * kU, Xm));
+    s.E_df = __fmul_ru(1.0000001e-12f, __fadd_ru(__fadd_ru(PA, reach), 1.f));
+}
+
+// The fields of a query's state that the traversal changes, at their
+// starting values.
+__device__ __forceinline__ void setup_state(QState& s, int kind, unsigned slot_base, int LB, bool refit) {
+    s.U = kind == 0 ? kFltMaxBits : 0u;
+    s.status = 0u;
+    s.best_d = kind == 0 ? 0x7ff0000000000000ull : 0ull;  // +inf / +0
+    s.best_key = 0xffffffffffffffffull;
+    s.slot_base = slot_base;
+    s.dR = refit ? max(0, LB - kRefitH) : -1;
+    s.cert = 0u;
+    s.pushed[0] = s.pushed[1] = 0u;
+}
+
+// The setup of a launch's only query by one warp (every lane calls it).  The
+// nine entries of B's rotation in A's frame and the three of its translation
+// are independent three-term dot products of A's inverted 3x3 part with B's
+// transform, so lanes 0-8 compute one rotation entry each (row lane / 3,
+// column lane % 3) and lanes 9-11 one translation entry each.  A float64
+// instruction costs the same for one active lane as for a whole warp, and the
+// single thread of setup_query evaluating all twelve in turn spent
+// microseconds on them.  Lanes 0-8 also hold one entry of the adjugate each;
+// the determinant takes the first column from lanes 0, 3 and 6.
+__device__ void setup_query_warp(const KArgs& A, int kind) {
+    const int lane = threadIdx.x & 31;
+    QState& s = A.qs[0];
+    const MeshDev* ma;
+    const MeshDev* mb;
+    const double* xa;
+    const double* xb;
+    unsigned slot_base = 0;
+    if (A.qin) {
+        ma = A.qin[0].A; mb = A.qin[0].B;
+        xa = A.qin[0].xa; xb = A.qin[0].xb;
+        slot_base = A.qin[0].slot_base;
+    } else {
+        ma = A.mA; mb = A.mB;
+        xa = A.xa_src ? A.xa_src : A.xa_val;
+        xb = A.xb_src ? A.xb_src : A.xb_val;
+    }
+    const bool rot = lane < 9, tra = lane >= 9 && lane < 12;
+    const int i = rot ? lane / 3 : (tra ? lane - 9 : 0);  // row of A's inverse
+    const int j = rot ? lane - 3 * (lane / 3) : 0;        // column (rotation lanes)
+    // adjugate entry (i, j) of A's 3x3 part a[r][c] = xa[4 r + c]
+    const int r1 = j == 2 ? 0 : j + 1, r2 = j == 0 ? 2 : j - 1;
+    const int c1 = i == 2 ? 0 : i + 1, c2 = i == 0 ? 2 : i - 1;
+    const double adj = xa[4 * r1 + c1] * xa[4 * r2 + c2] - xa[4 * r1 + c2] * xa[4 * r2 + c1];
+    const double det = xa[0] * __shfl_sync(kFull, adj, 0) + xa[1] * __shfl_sync(kFull, adj, 3) +
+                       xa[2] * __shfl_sync(kFull, adj, 6);
+    const double ai = adj * (1.0 / det);  // entry (i, j) of A's inverse (lanes 0-8)
+    const double i0 = __shfl_sync(kFull, ai, 3 * i), i1 = __shfl_sync(kFull, ai, 3 * i + 1),
+                 i2 = __shfl_sync(kFull, ai, 3 * i + 2);
+    // rotation lanes: column j of B's 3x3 part; translation lanes: t_B - t_A
+    const double v0 = tra ? xb[3] - xa[3] : xb[j];
+    const double v1 = tra ? xb[7] - xa[7] : xb[4 + j];
+    const double v2 = tra ? xb[11] - xa[11] : xb[8 + j];
+    const double r = i0 * v0 + i1 * v1 + i2 * v2;
+    const float h = (float)r;
+    const float lo = (float)(r - (double)h);
+    if (rot) {
+        s.R[lane] = h;
+        s.Rl[lane] = lo;
+    } else if (tra) {
+        s.t[i] = h;
+        s.tl[i] = lo;
+    }
+    if (lane < 12) {
+        s.xa[lane] = xa[lane];
+        s.xb[lane] = xb[lane];
+    }
+    const float tinf = fmaxf(fabsf(__shfl_sync(kFull, h, 9)), fmaxf(fabsf(__shfl_sync(kFull, h, 10)),
+                                                                   fabsf(__shfl_sync(kFull, h, 11))));
+    if (lane == 0) {
+        setup_widening(s, ma->P, mb->P, tinf);
+        s.A = ma;
+        s.B = mb;
+        setup_state(s, kind, slot_base, mb->L, A.refit);
+    }
+    // every lane's fields are published before the CTA's barrier that
+    // precedes the setup flag or the grid barrier
+    __threadfence();
+    __syncwarp();
+}
+
 __device__ void setup_query(const KArgs& A, int q, int kind) {
     QState& s = A.qs[q];
     const MeshDev* ma;
@@ -926,34 +1031,11 @@ __device__ void setup_query(const KArgs& A, int q, int kind) {
         s.tl[i] = (float)(tt - (double)h);
         tinf = fmaxf(tinf, fabsf(h));
     }
-    // widening: every mapped coordinate is within e_c of its exact value,
-    // e_c = gamma_10 (sqrt(3) P_B + |t|_inf); E_box = sqrt(3) e_c; the
-    // triangle narrow phase adds 256 u X for its own arithmetic on
-    // coordinates of magnitude <= X.
-    const double u = 5.9604644775390625e-08;
-    const double g10 = 10.0 * u / (1.0 - 10.0 * u);
-    double PB = (double)mb->P * 1.000001, PA = (double)ma->P;
-    double ec = g10 * (1.7320508075688772 * PB + (double)tinf);
-    double Eb = 1.7320508075688772 * ec * 1.000001;
-    double Xm = fmax(PA, 1.7320508075688772 * PB + (double)tinf) * 1.000001 + Eb;
-    double Et = Eb + 256.0 * u * Xm;
-    s.E_box = __double2float_ru(Eb);
-    s.E_tri = __double2float_ru(Et);
-    // double-float map (including the shift to A's vertex): about a dozen
-    // roundings of relative size 2^-46 on terms of magnitude
-    // <= P_A + sqrt(3) P_B + |t|, plus the float64 relative map itself
-    s.E_df = __double2float_ru(1e-12 * (PA + 1.7320508075688772 * PB + (double)tinf + 1.0));
+    setup_widening(s, ma->P, mb->P, tinf);
     s.A = ma;
     s.B = mb;
     for (int i = 0; i < 12; ++i) { s.xa[i] = Xa[i]; s.xb[i] = Xb[i]; }
-    s.U = kind == 0 ? kFltMaxBits : 0u;
-    s.status = 0u;
-    s.best_d = kind == 0 ? 0x7ff0000000000000ull : 0ull;  // +inf / +0
-    s.best_key = 0xffffffffffffffffull;
-    s.slot_base = slot_base;
-    s.dR = A.refit ? max(0, mb->L - kRefitH) : -1;
-    s.cert = 0u;
-    s.pushed[0] = s.pushed[1] = 0u;
+    setup_state(s, kind, slot_base, mb->L, A.refit);
 }
 
 // ------------------------------------------------------------- phase 2
@@ -1355,7 +1437,8 @@ __device__ __noinline__ double refine_pair_warp(const QState& s, unsigned ta, un
 // needed.  The per-feature arithmetic is the explicitly rounded float64 of
 // tri_feature and the winner is the same (hit first, else the smallest
 // (d2, feature)), so the result equals refine_pair_warp's bit for bit.  Every
-// thread of the CTA calls it; the result is valid on every thread.
+// thread of the CTA calls it; the result (return value, P, Q) is valid in
+// warp 0, *ida and *idb on every thread.
 template <int KIND>
 __device__ __noinline__ double refine_pair_cta(const QState& s, unsigned ta, unsigned tb, V3<double>* P,
                                                V3<double>* Q, int* ida, int* idb) {
@@ -1401,6 +1484,19 @@ __device__ __noinline__ double refine_pair_cta(const QState& s, unsigned ta, uns
         if (hits) {
             win = __ffs(hits) - 1;
             best = -1.0;  // marks a hit
+        } else if (KIND == 0) {
+            // the values are non-negative (or +inf): their bit patterns order
+            // like them, so the (d2, lane) minimum takes integer compares
+            // (float64 compares issue on the float64 pipe)
+            unsigned long long key = (unsigned long long)__double_as_longlong(d2);
+            win = lane;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long ok = __shfl_xor_sync(kFull, key, o);
+                const int ow = __shfl_xor_sync(kFull, win, o);
+                if (ok < key || (ok == key && ow < win)) { key = ok; win = ow; }
+            }
+            best = __longlong_as_double((long long)key);
         } else {
             best = d2;
             win = lane;
@@ -1423,6 +1519,11 @@ __device__ __noinline__ double refine_pair_cta(const QState& s, unsigned ta, uns
         }
     }
     __syncthreads();
+    // the result is taken from thread 0: the other warps leave the float64
+    // selection and square root to warp 0 (a float64 instruction occupies
+    // its SM sub-partition's float64 pipe as long for one warp as for any
+    // other, so eight warps computing it would queue on those pipes)
+    if (warp != 0) return 0.0;
     // min kind: a hit (-1) wins, the smallest feature index first; otherwise
     // the smallest (d2, feature).  Max kind: the values are -d2.
     int bw = 0;
@@ -1682,7 +1783,11 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
         for (int i = threadIdx.x; i < kCtrReset; i += blockDim.x) A.ctr[i] = 0u;
         if (A.fuse_root) __syncthreads();  // cleared before the root is pushed below
     }
-    for (int q = (int)gfirst; q < A.nq; q += (int)gstride) setup_query(A, q, KIND);
+    if (A.nq == 1) {
+        if (gfirst < 32) setup_query_warp(A, KIND);
+    } else {
+        for (int q = (int)gfirst; q < A.nq; q += (int)gstride) setup_query(A, q, KIND);
+    }
     if (A.fuse_root && gfirst == 0) {
         // one query whose root needs no refit claim: the thread that set it up
         // pushes its root pair now, and phase 1 with its barrier is skipped
