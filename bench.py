@@ -285,9 +285,11 @@ def bench_deformable(G, ctx, ma, frames=8):
     u_dev, q_dev, d_dev = run(dev)
     u_host, q_host, d_host = run([h.numpy() for h in host])
     # device time of the update from device memory (events on the engine's
-    # stream around the synchronous call) against the HBM roofline: per
-    # triangle 4 B order + 12 B indices + 36 B vertices read and 48 B stored,
-    # 24 B per tree node, and the vertex copy (12 B per vertex each way)
+    # stream around the synchronous call) against the HBM roofline, with the
+    # bytes the update must move: per triangle 4 B order + 12 B indices read
+    # and a 48 B record stored, 12 B per distinct vertex gathered (repeated
+    # gathers of a vertex are cache hits), 24 B per tree node stored, and the
+    # vertex copy (12 B per vertex each way)
     es = torch.cuda.ExternalStream(G.gd_ctx_stream(ctx))
     dt = []
     for i in range(frames):
@@ -299,7 +301,7 @@ def bench_deformable(G, ctx, ma, frames=8):
         dt.append(e0.elapsed_time(e1))
     L, T = G.gd_mesh_info(mb)
     nv = dev[0].numel() // 3
-    alg = 100 * T + 24 * (2 << L) + 24 * nv
+    alg = 64 * T + 12 * nv + 24 * ((2 << L) - 1) + 24 * nv
     peak, peak_kind = _peaks()
     refit_ms = statistics.mean(dt)
     G.gd_mesh_destroy(mb)
