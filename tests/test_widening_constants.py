@@ -2,9 +2,9 @@
 
 The error radii E_box, E_tri and E_df of a query (the widening that keeps
 the float32 traversal's bounds rigorous: gamma_10 (sqrt(3) P_B + |t|) and the
-terms added to it) are evaluated in float32 with upward rounding, from float inputs and from constants that must
-not lie below the real numbers they stand for.  This test reads each constant
-from the kernel source, rounds its decimal literal to float32 exactly as a C
+terms added to it) are evaluated in float32 with upward rounding, from float
+inputs and from constants that must not lie below the real numbers they
+stand for.  This test reads each constant from the kernel source, rounds its decimal literal to float32 exactly as a C
 compiler does (to nearest, ties to even), and checks it against the exact
 value with rational arithmetic.  No GPU is needed.
 """
