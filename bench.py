@@ -635,21 +635,24 @@ def main():
         "clocks": clk.summary(),
         "wall_s": wall,
     }
-    if not args.no_ablation:
+    # the other legs and the oracle's CPU baseline run at one GPU only: with
+    # more ranks the others have left, and their GPUs would wait for rank 0
+    one = world == 1
+    if one and not args.no_ablation:
         line["ablation"] = bench_ablation(G, ctx, ma, mb, xa, xbs)
-    if not args.no_points:
+    if one and not args.no_points:
         line["points"] = bench_points(G, ctx, ma)
-    if not args.no_naive:
+    if one and not args.no_naive:
         line["naive"] = bench_naive(G, ctx, ma, mb, xa, xbs)
-    if not args.no_deformable:
+    if one and not args.no_deformable:
         line["deformable"] = bench_deformable(G, ctx, ma)
     G.gd_mesh_destroy(ma)
     G.gd_mesh_destroy(mb)
-    if not args.no_batched:
+    if one and not args.no_batched:
         line["batched"] = bench_batched(G, ctx)
-    if not args.no_served:
+    if one and not args.no_served:
         line["served"] = bench_served(G, ctx)
-    if not args.no_cpu_baseline:
+    if one and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(A, xa, xbs, args.cpu_frames)
     print(json.dumps(line), flush=True)
     G.gd_ctx_destroy(ctx)
