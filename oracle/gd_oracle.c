@@ -118,13 +118,23 @@ static double seg_seg(v3 p0, v3 p1, v3 q0, v3 q1, v3 *cp, v3 *cq) {
     if (d < best) { best = d; *cp = t; *cq = q0; }
     d = pt_seg(q1, p0, p1, &t);
     if (d < best) { best = d; *cp = t; *cq = q1; }
+    /* The stationary point of |p0 + s d1 - q0 - u d2|^2 solves a 2x2 system
+     * whose determinant and numerators, (d1.d1)(d2.d2) - (d1.d2)^2 and so on,
+     * are written here through the Binet-Cauchy identity
+     * (a x b).(c x d) = (a.c)(b.d) - (a.d)(b.c) as dot products of cross
+     * products: the same values, but without the cancellation of the
+     * difference of products, so nearly parallel segments keep an accurate
+     * stationary point.  u is then taken as the exact minimiser over u for
+     * that s, (d2.r + s d1.d2) / d2.d2, so that a rounding error in s moves
+     * the pair along the nearly flat valley of the quadratic instead of
+     * across it.  Any (s, u) in the square gives a pair of points on the two
+     * segments, so taking it can never undercut the true minimum. */
     v3 d1 = vsub(p1, p0), d2 = vsub(q1, q0), r = vsub(p0, q0);
-    double a = vdot(d1, d1), b = vdot(d1, d2), c = vdot(d2, d2);
-    double e1 = vdot(d1, r), e2 = vdot(d2, r);
-    double det = a * c - b * b;
-    if (det > 1e-14 * a * c && det > 0.0) {
-        double s = (b * e2 - c * e1) / det;
-        double u = (a * e2 - b * e1) / det;
+    v3 n = vcross(d1, d2);
+    double det = vdot(n, n);
+    if (det > 0.0) {
+        double s = vdot(n, vcross(d2, r)) / det;
+        double u = (vdot(d2, r) + s * vdot(d1, d2)) / vdot(d2, d2);
         if (s >= 0.0 && s <= 1.0 && u >= 0.0 && u <= 1.0) {
             v3 x = vadd(p0, vscale(d1, s)), y = vadd(q0, vscale(d2, u));
             double dd = vdist(x, y);

@@ -83,6 +83,30 @@ def test_segment_segment_closed_forms(oracle_mod):
     assert d == pytest.approx(math.sqrt(2), abs=1e-15)
 
 
+def test_segment_segment_nearly_parallel(oracle_mod):
+    """Two segments at a tiny angle eps whose projections cross at their
+    midpoints, h apart: the distance is h, attained at the midpoints (the
+    interior stationary point).  With eps^2 below the float64 resolution of
+    |d1|^2 |d2|^2 the difference-of-products determinant vanishes; a stationary
+    point lost that way leaves only endpoint pairs, at sqrt(h^2 + eps^2) (for
+    eps = 2^-26, h = 2^-10: 1.2e-10 relative too high)."""
+    h = 2.0 ** -10
+    for k in (20, 26, 40):
+        eps = 2.0 ** -k
+        d, cp, cq = oracle_mod.segment_segment((-1, 0, 0), (1, 0, 0), (-1, -eps, h), (1, eps, h))
+        assert d == h, (k, d)
+        if k <= 26:  # (for eps = 2^-40 the endpoint pairs are at h in float64 too)
+            assert np.array_equal(cp, [0, 0, 0]) and np.array_equal(cq, [0, 0, h])
+    # the same under rigid motions: within the rounding of the moved inputs
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        R, t = synth.random_rotation(rng), rng.normal(size=3)
+        eps = 2.0 ** -int(rng.integers(12, 44))
+        P = [R @ np.asarray(x, dtype=np.float64) + t for x in ((-1, 0, 0), (1, 0, 0), (-1, -eps, h), (1, eps, h))]
+        d, _, _ = oracle_mod.segment_segment(*P)
+        assert abs(d - h) <= 4e-15, (eps, d - h)
+
+
 def test_segment_segment_matches_line_distance(oracle_mod):
     """Interior closest points: distance equals |(q0 - p0) . (d1 x d2)| / |d1 x d2|."""
     rng = np.random.default_rng(11)
@@ -199,6 +223,91 @@ def test_parallel_grids_closed_form(oracle_mod):
     # massive ties: the witness is the smallest (ta, tb) at distance g
     rm = oracle_mod.brute(A, synth.identity_xform(), B, synth.identity_xform(), "max")
     assert rm.d == pytest.approx(math.sqrt(1.3 ** 2 + 1.25 ** 2 + g * g), rel=1e-7)
+
+
+def _tie_meshes(kind):
+    """Meshes whose extreme pairs tie exactly by construction.  Min: triangle
+    a (index 5 of A) lies in z = 0 and b (index 2 of B) right above its
+    interior in z = 1/2, so they are 1/2 apart; a copy of both shifted by 8
+    along x sits at indices 3 (A) and 6 (B); a duplicate of b at index 4 of B.
+    Max: a (5) around (-2, 0, 0) and b (2) around (6, 0, 0), 8 apart at their
+    outer vertices, and their mirror images through the origin at 3 (A) and
+    6 (B).  The other triangles are fillers that stay clear of the extreme.
+    Every coordinate is a small dyadic rational and the transforms are the
+    identity, so the tied pairs repeat the same float64 operations on the
+    same differences and their distances are bit for bit equal.  Returns
+    (A, B, d_extreme, tied pairs)."""
+    def mesh(tris):
+        v = np.asarray([p for t in tris for p in t], dtype=np.float32)
+        return v, np.arange(len(v), dtype=np.int32).reshape(-1, 3)
+
+    def tri(o, pts):
+        return [tuple(np.add(o, p)) for p in pts]
+
+    if kind == "min":
+        ta = [(0, 0, 0), (1, 0, 0), (0, 1, 0)]
+        tb = [(0.25, 0.25, 0.5), (0.5, 0.25, 0.5), (0.25, 0.5, 0.5)]
+        fa = lambda i: tri((4 * i, 20, -8), ta)  # far below and aside
+        fb = lambda i: tri((4 * i, -20, 8), tb)
+        A = [fa(0), fa(1), fa(2), tri((8, 0, 0), ta), fa(4), tri((0, 0, 0), ta), fa(6)]
+        B = [fb(0), fb(1), tri((0, 0, 0), tb), fb(3), tri((0, 0, 0), tb), fb(5), tri((8, 0, 0), tb)]
+        return mesh(A), mesh(B), 0.5, {(5, 2), (5, 4), (3, 6)}
+    ta = [(-2, 0, 0), (-1.5, 0.5, 0), (-1.5, -0.5, 0)]
+    tb = [(6, 0, 0), (5.5, 0.5, 0), (5.5, -0.5, 0)]
+    neg = lambda t: [tuple(-np.asarray(p)) for p in t]
+    fa = lambda i: tri((0, 0, 0.25 * i), [(0, 0, 0), (0.25, 0, 0), (0, 0.25, 0)])
+    fb = lambda i: tri((0.5, 0, 0.25 * i), [(0, 0, 0), (0.25, 0, 0), (0, 0.25, 0)])
+    A = [fa(0), fa(1), fa(2), neg(ta), fa(4), ta, fa(6)]
+    B = [fb(0), fb(1), tb, fb(3), fb(4), fb(5), neg(tb)]
+    return mesh(A), mesh(B), 8.0, {(5, 2), (3, 6)}
+
+
+@pytest.mark.parametrize("kind", ["min", "max"])
+def test_witness_tie_break_is_smallest_pair(oracle_mod, kind):
+    """Among pairs at the same float64 extreme the witness is the smallest
+    (tri_a, tri_b).  The tied set is not a product of index sets: (3, 6) is
+    smallest by tri_a first, (5, 2) by tri_b first or by the largest pair, so
+    a reversed or transposed comparison fails here."""
+    A, B, dx, tied = _tie_meshes(kind)
+    I = synth.identity_xform()
+    # the construction's ties are exact in the oracle's arithmetic
+    for ta, tb in tied:
+        assert oracle_mod.witness_distance(A, I, B, I, ta, tb, kind)[0] == dx
+    want = min(tied)
+    assert want == (3, 6)
+    r = oracle_mod.brute(A, I, B, I, kind)
+    assert r.d == dx and (r.ta, r.tb) == want, (r.d, r.ta, r.tb)
+    for threads in (1, 2, 3):
+        r = oracle_mod.brute(A, I, B, I, kind, threads=threads)
+        assert (r.ta, r.tb) == want
+    bA, bB = oracle_mod.Bvh(A), oracle_mod.Bvh(B)
+    r = oracle_mod.bvh_query(bA, I, bB, I, kind)
+    assert r.d == dx and (r.ta, r.tb) == want, (r.d, r.ta, r.tb)
+
+
+def test_bvh_batch_equals_single_queries(oracle_mod):
+    """The threaded batch wrapper returns, query by query, what the single
+    BVH query and brute force return (value and witness), with one A
+    transform for all queries and with one per query, on more queries than
+    threads and on fewer."""
+    rng = np.random.default_rng(77)
+    A = synth.torus(1.0, 0.25, 14, 9)
+    B = synth.geosphere(3, 0.7, 0.01, 3)
+    bA, bB = oracle_mod.Bvh(A), oracle_mod.Bvh(B)
+    n = 7
+    xas = [_rigid(rng) for _ in range(n)]
+    xbs = [synth.compose(synth.xform(np.eye(3), rng.normal(size=3) * 1.5), x) for x in xas]
+    for kind in ("min", "max"):
+        for threads in (1, 3, 16):
+            per = oracle_mod.bvh_query_batch(bA, xas, bB, xbs, kind, threads=threads)
+            one = oracle_mod.bvh_query_batch(bA, xas[0], bB, xbs, kind, threads=threads)
+            assert len(per) == n and len(one) == n
+            for i in range(n):
+                s = oracle_mod.bvh_query(bA, xas[i], bB, xbs[i], kind)
+                b = oracle_mod.brute(A, xas[i], B, xbs[i], kind)
+                assert (per[i].d, per[i].ta, per[i].tb) == (s.d, s.ta, s.tb) == (b.d, b.ta, b.tb)
+                s0 = oracle_mod.bvh_query(bA, xas[0], bB, xbs[i], kind)
+                assert (one[i].d, one[i].ta, one[i].tb) == (s0.d, s0.ta, s0.tb)
 
 
 def test_geospheres_within_tessellation_bounds(oracle_mod):
