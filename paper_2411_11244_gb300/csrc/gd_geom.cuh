@@ -145,8 +145,24 @@ __device__ __forceinline__ void closest_segment_segment(V3<T> p0, V3<T> d1, V3<T
             s = clamp_div(-c, a);
         } else {
             T b = dot(d1, d2);
-            T den = ssub(smul(a, e), smul(b, b));
-            s = den > T(0) ? clamp_div(ssub(smul(b, f), smul(c, e)), den) : T(0);
+            T den, num;
+            if constexpr (sizeof(T) == 8) {
+                // float64: the determinant a e - b^2 and the numerator
+                // b f - c e as dot products of cross products (Binet-Cauchy:
+                // (p x q).(u x v) = (p.u)(q.v) - (p.v)(q.u)), which keep
+                // their accuracy for nearly parallel segments, where the
+                // differences of products cancel to nothing and the interior
+                // closest pair would be lost
+                const V3<T> n = cross(d1, d2);
+                den = dot(n, n);
+                num = dot(n, cross(d2, r));
+            } else {
+                // float32 (bounds only, widened): the cheaper Gram form; a
+                // stationary point lost to cancellation only loosens a bound
+                den = ssub(smul(a, e), smul(b, b));
+                num = ssub(smul(b, f), smul(c, e));
+            }
+            s = den > T(0) ? clamp_div(num, den) : T(0);
             T tn = sadd(smul(b, s), f);
             // t clamped to 0 or 1 re-optimises s; otherwise t = tn / e.  One
             // division on every path, so the lanes of a warp do not split

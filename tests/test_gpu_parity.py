@@ -311,21 +311,27 @@ def test_batch_eviction_matches_single(G, oracle_mod):
 
 
 def test_refit_modes_agree(G, oracle_mod):
-    """Refitting B's low subtrees only tightens bounds: the answer (value and
-    witness) is the same with and without it."""
+    """Refitting B's low subtrees only tightens bounds: with and without it
+    every answer matches the FP64 oracle (value and witness), and the two
+    modes give the same answer."""
     rng = np.random.default_rng(31)
     c = G.gd_ctx_create(0)
     try:
         A = synth.torus(1.0, 0.1, 96, 40)
         B = synth.geosphere(20, 0.5, 1e-3, 3)
         ma, mb = _mesh(G, c, A), _mesh(G, c, B)
+        oa, ob = oracle_mod.Bvh(A), oracle_mod.Bvh(B)
         for i in range(6):
             xa, xb = _rigid(rng, 0.3), _rigid(rng, 1.2)
+            diag = oracle_mod.diag(A, xa, B, xb)
             for kind, fn in (("min", G.gd_min_distance), ("max", G.gd_max_distance)):
+                ref = oracle_mod.bvh_query(oa, xa, ob, xb, kind)
                 G.gd_ctx_set_tunables(c, refit_mode=1)
                 r1 = fn(c, ma, mb, xa, xb)
+                check(r1, A, xa, B, xb, kind, ref, diag, oracle_mod)
                 G.gd_ctx_set_tunables(c, refit_mode=2)
                 r2 = fn(c, ma, mb, xa, xb)
+                check(r2, A, xa, B, xb, kind, ref, diag, oracle_mod)
                 same_answer(r1, r2, oracle_mod, A, xa, B, xb, kind)
         G.gd_mesh_destroy(ma)
         G.gd_mesh_destroy(mb)
@@ -335,25 +341,36 @@ def test_refit_modes_agree(G, oracle_mod):
 
 def test_conventional_bounds_ablation(G, oracle_mod):
     """Section 9's ablation: with conventional bounds only (Eq. 9 for the min,
-    the box gap for the max) the answers are the same and the traversal tests
-    at least as many node pairs; the enhanced bounds cull more."""
+    the box gap for the max) and with a fixed k (a huge work target, k = 5)
+    every answer matches the FP64 oracle, and the conventional bounds test at
+    least as many node pairs; the enhanced bounds cull more."""
     c = G.gd_ctx_create(0)
     try:
         rng = np.random.default_rng(19)
         A = synth.torus(1.0, 0.1, 96, 40)
         B = synth.geosphere(20, 0.5, 1e-3, 3)
         ma, mb = _mesh(G, c, A), _mesh(G, c, B)
+        oa, ob = oracle_mod.Bvh(A), oracle_mod.Bvh(B)
+        base = G.gd_ctx_get_tunables(c)
         more = 0
         for i in range(4):
             xa, xb = _rigid(rng, 0.3), _rigid(rng, 1.5)
+            diag = oracle_mod.diag(A, xa, B, xb)
             for kind, fn in (("min", G.gd_min_distance), ("max", G.gd_max_distance)):
+                ref = oracle_mod.bvh_query(oa, xa, ob, xb, kind)
                 G.gd_ctx_set_tunables(c, bounds_mode=1)
                 r1 = fn(c, ma, mb, xa, xb)
                 p1 = G.gd_get_stats(c)["pairs_tested"]
+                check(r1, A, xa, B, xb, kind, ref, diag, oracle_mod)
                 G.gd_ctx_set_tunables(c, bounds_mode=2)
                 r2 = fn(c, ma, mb, xa, xb)
                 p2 = G.gd_get_stats(c)["pairs_tested"]
+                check(r2, A, xa, B, xb, kind, ref, diag, oracle_mod)
                 same_answer(r1, r2, oracle_mod, A, xa, B, xb, kind)
+                G.gd_ctx_set_tunables(c, bounds_mode=1, k_max=5, work_target=1 << 40)
+                r3 = fn(c, ma, mb, xa, xb)
+                check(r3, A, xa, B, xb, kind, ref, diag, oracle_mod)
+                G.gd_ctx_set_tunables(c, k_max=base["k_max"], work_target=base["work_target"])
                 more += p2 > p1
         assert more > 0
         G.gd_ctx_set_tunables(c, bounds_mode=1)
@@ -380,14 +397,102 @@ def test_autotune_keeps_answers(G, oracle_mod):
         t2 = G.gd_autotune(c, items, reps=2)
         assert t2["batch_budget"] in (1 << 18, 1 << 20, 1 << 22, 1 << 23, 1 << 24)
         after = G.gd_batch_query(c, items)
+        oa, ob = oracle_mod.Bvh(A), oracle_mod.Bvh(B)
         for i, (a, b, xa, xb, kind) in enumerate(items):
-            same_answer(before[i], after[i], oracle_mod, A, xa, B, xb, "min" if kind == 0 else "max")
-        same_answer(one, G.gd_min_distance(c, ma, mb, items[0][2], items[0][3]), oracle_mod, A, items[0][2], B,
-                    items[0][3], "min")
+            name = "min" if kind == 0 else "max"
+            ref = oracle_mod.bvh_query(oa, xa, ob, xb, name)
+            diag = oracle_mod.diag(A, xa, B, xb)
+            check(before[i], A, xa, B, xb, name, ref, diag, oracle_mod)
+            check(after[i], A, xa, B, xb, name, ref, diag, oracle_mod)
+            same_answer(before[i], after[i], oracle_mod, A, xa, B, xb, name)
+        tuned = G.gd_min_distance(c, ma, mb, items[0][2], items[0][3])
+        ref = oracle_mod.bvh_query(oa, items[0][2], ob, items[0][3], "min")
+        diag = oracle_mod.diag(A, items[0][2], B, items[0][3])
+        check(one, A, items[0][2], B, items[0][3], "min", ref, diag, oracle_mod)
+        check(tuned, A, items[0][2], B, items[0][3], "min", ref, diag, oracle_mod)
+        same_answer(one, tuned, oracle_mod, A, items[0][2], B, items[0][3], "min")
         G.gd_mesh_destroy(ma)
         G.gd_mesh_destroy(mb)
     finally:
         G.gd_ctx_destroy(c)
+
+
+def _tie_meshes(kind):
+    """Meshes whose extreme pairs tie exactly (dyadic coordinates, identity
+    transforms, tied pairs that repeat the same float64 operations on the
+    same differences).  Min: two copies of a triangle pair 1/2 apart (one
+    shifted by 8 along x) at (5, 2) and (3, 6), and a duplicate of B's
+    triangle at index 4.  Max: a pair 8 apart at its outer vertices at (5, 2)
+    and its mirror image through the origin at (3, 6).  The tied set is no
+    product of index sets, so only the smallest (tri_a, tri_b) rule gives
+    (3, 6)."""
+    def mesh(tris):
+        v = np.asarray([p for t in tris for p in t], dtype=np.float32)
+        return v, np.arange(len(v), dtype=np.int32).reshape(-1, 3)
+
+    def tri(o, pts):
+        return [tuple(np.add(o, p)) for p in pts]
+
+    if kind == "min":
+        ta = [(0, 0, 0), (1, 0, 0), (0, 1, 0)]
+        tb = [(0.25, 0.25, 0.5), (0.5, 0.25, 0.5), (0.25, 0.5, 0.5)]
+        fa = lambda i: tri((4 * i, 20, -8), ta)
+        fb = lambda i: tri((4 * i, -20, 8), tb)
+        A = [fa(0), fa(1), fa(2), tri((8, 0, 0), ta), fa(4), tri((0, 0, 0), ta), fa(6)]
+        B = [fb(0), fb(1), tri((0, 0, 0), tb), fb(3), tri((0, 0, 0), tb), fb(5), tri((8, 0, 0), tb)]
+        return mesh(A), mesh(B), 0.5
+    ta = [(-2, 0, 0), (-1.5, 0.5, 0), (-1.5, -0.5, 0)]
+    tb = [(6, 0, 0), (5.5, 0.5, 0), (5.5, -0.5, 0)]
+    neg = lambda t: [tuple(-np.asarray(p)) for p in t]
+    fa = lambda i: tri((0, 0, 0.25 * i), [(0, 0, 0), (0.25, 0, 0), (0, 0.25, 0)])
+    fb = lambda i: tri((0.5, 0, 0.25 * i), [(0, 0, 0), (0.25, 0, 0), (0, 0.25, 0)])
+    A = [fa(0), fa(1), fa(2), neg(ta), fa(4), ta, fa(6)]
+    B = [fb(0), fb(1), tb, fb(3), fb(4), fb(5), neg(tb)]
+    return mesh(A), mesh(B), 8.0
+
+
+def test_witness_tie_break_exact_ties(G, ctx, oracle_mod):
+    """The engine's witness rule on exact ties (gd_result: the smallest
+    (tri_a, tri_b) at the extreme), single query and batch, min and max,
+    equal to the oracle's witness."""
+    I = synth.identity_xform()
+    for kind in ("min", "max"):
+        A, B, dx = _tie_meshes(kind)
+        ref = oracle_mod.brute(A, I, B, I, kind)
+        assert ref.d == dx and (ref.ta, ref.tb) == (3, 6)
+        ma, mb = _mesh(G, ctx, A), _mesh(G, ctx, B)
+        fn = G.gd_min_distance if kind == "min" else G.gd_max_distance
+        r = fn(ctx, ma, mb, I, I)
+        assert r.status == 0 and r.d == dx and (r.tri_a, r.tri_b) == (3, 6), (kind, r.d, r.tri_a, r.tri_b)
+        k = G.GD_MIN if kind == "min" else G.GD_MAX
+        out = G.gd_batch_query(ctx, [(ma, mb, I, I, k)] * 3)
+        for o in out:
+            assert o.status == 0 and o.d == dx and (o.tri_a, o.tri_b) == (3, 6)
+        G.gd_mesh_destroy(ma)
+        G.gd_mesh_destroy(mb)
+
+
+def test_nearly_parallel_edges(G, ctx, oracle_mod):
+    """Two triangles whose closest pair is interior to two edges at a tiny
+    angle eps, h apart (the stationary point of the edge pair, which a
+    difference-of-products determinant loses for eps below ~1e-7), under
+    rigid motions: the float64 refinement matches the oracle (value within
+    the parity tolerance, witness distance within 1e-12 relative)."""
+    rng = np.random.default_rng(88)
+    h = 2.0 ** -10
+    for k in (12, 20, 26, 34):
+        eps = 2.0 ** -k
+        A = (np.array([[-1, 0, 0], [1, 0, 0], [0, -1, -0.5]], dtype=np.float32), np.array([[0, 1, 2]], np.int32))
+        B = (np.array([[-1, -eps, h], [1, eps, h], [0, 1, h + 0.5]], dtype=np.float32), np.array([[0, 1, 2]], np.int32))
+        ma, mb = _mesh(G, ctx, A), _mesh(G, ctx, B)
+        for j in range(3):
+            M = synth.identity_xform() if j == 0 else _rigid(rng, 2.0)
+            ref = oracle_mod.brute(A, M, B, M, "min")
+            assert abs(ref.d - h) <= 4e-15
+            r = G.gd_min_distance(ctx, ma, mb, M, M)
+            check(r, A, M, B, M, "min", ref, oracle_mod.diag(A, M, B, M), oracle_mod)
+        G.gd_mesh_destroy(ma)
+        G.gd_mesh_destroy(mb)
 
 
 def test_device_resident_query(G, ctx, oracle_mod):
