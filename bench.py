@@ -61,6 +61,22 @@ def _traffic():
     return rec["dram_bytes_per_launch"] if h.hexdigest() == rec.get("source_sha256") else None
 
 
+def _counters():
+    """Per-launch counters of the query kernel (FP32 flops, pipe activity,
+    L2 hit rate) from the committed ncu summary, or None when the kernel's
+    sources changed since that capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_query_min_rings_counters.json")
+    try:
+        rec = json.load(open(path))
+        h = hashlib.sha256()
+        for f in KERNEL_SOURCES:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+    except (OSError, ValueError):
+        return None
+    return rec if h.hexdigest() == rec.get("source_sha256") else None
+
+
 def _dist():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -158,62 +174,260 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def cpu_baseline(A, xa, xbs, frames, threads=None):
+def cpu_baseline(A, xa, xbs, frames, threads=None, B=None, kind="min", name="rings"):
     """The FP64 oracle (BVH traversal), timed on this host's cores on a bounded
-    sample of frames; returns ms/query (wall time / queries, all cores)."""
+    sample of frames; returns ms/query (wall time / queries, all cores) and,
+    under "_answers", the oracle's answers for frames 0 .. frames-1 (for the
+    parity spot check; not printed)."""
     import oracle
     threads = threads or os.cpu_count() or 1
     t0 = time.perf_counter()
-    ob = oracle.Bvh(A)
+    oa = oracle.Bvh(A)
+    ob = oa if B is None else oracle.Bvh(B)
     build_s = time.perf_counter() - t0
     sample = [xbs[i % len(xbs)] for i in range(frames)]
     t0 = time.perf_counter()
-    oracle.bvh_query_batch(ob, xa, ob, sample, "min", threads=threads)
+    ans = oracle.bvh_query_batch(oa, xa, ob, sample, kind, threads=threads)
     wall = time.perf_counter() - t0
     return {"value": 1000.0 * wall / frames, "unit": "ms/query", "cores": threads, "kind": "oracle",
-            "sample": f"{frames} rings frames, FP64 BVH oracle on {threads} threads (one query per thread); "
-                      f"oracle BVH build {build_s:.1f} s excluded"}
+            "sample": f"{frames} {name} frames ({kind}), FP64 BVH oracle on {threads} threads (one query per "
+                      f"thread); oracle BVH build {build_s:.1f} s excluded",
+            "_answers": ans}
 
 
-def bench_batched(G, ctx, n=4096, reps=3):
+def parity_spot_check(G, ctx, ma, mb, A, B, xa, xbs, answers, kind):
+    """The engine's answers (synchronous C ABI calls) against the oracle's on
+    the CPU-baseline sample frames: max |d - d_ref| / diag (the tolerance is
+    1e-6) and whether every witness pair's oracle distance equals d_ref
+    within 1e-12 relative (+1e-15 diag)."""
+    import oracle
+    fn = G.gd_min_distance if kind == "min" else G.gd_max_distance
+    worst, ok = 0.0, True
+    for i, ref in enumerate(answers):
+        xb = xbs[i % len(xbs)]
+        r = fn(ctx, ma, mb, xa, xb)
+        diag = oracle.diag(A, xa, B, xb)
+        worst = max(worst, abs(r.d - ref.d) / diag)
+        dw = oracle.witness_distance(A, xa, B, xb, r.tri_a, r.tri_b, kind)[0]
+        ok = ok and r.status == 0 and abs(dw - ref.d) <= 1e-12 * abs(ref.d) + 1e-15 * diag
+    return {"frames": len(answers), "max_abs_err_over_diag": worst, "witness_ok": ok, "tolerance": 1e-6}
+
+
+def fp32_roofline(mean_ms, clocks, counters):
+    """FP32 side of the roofline for the query kernel: float32 flops per
+    launch from the committed ncu capture (fadd + fmul + 2 ffma thread
+    instructions), divided by the live mean query time, against the FP32 peak
+    derived as SMs x 128 FP32 lanes x 2 flops per FMA x the median SM clock
+    sampled during the timed region."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+    peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+    out = {"peak_tflops": peak, "peak_derivation": f"{sms} SMs x 128 FP32 lanes x 2 flop/FMA x {mhz:.0f} MHz"}
+    if counters:
+        f = counters["fp32_flops_per_launch"]
+        out.update({"flops_per_launch": f, "achieved_tflops": f / (mean_ms * 1e-3) / 1e12,
+                    "frac": f / (mean_ms * 1e-3) / 1e12 / peak,
+                    "fma_pipe_pct": counters.get("fma_pipe_pct"), "alu_pipe_pct": counters.get("alu_pipe_pct"),
+                    "l2_hit_pct": counters.get("l2_hit_pct"), "source": counters.get("summary")})
+    else:
+        out.update({"flops_per_launch": None, "frac": None,
+                    "note": "no ncu counters for the current kernel sources"})
+    return out
+
+
+def torch_device_index():
+    import torch
+    return torch.cuda.current_device()
+
+
+def _pct(sorted_vals, q):
+    return sorted_vals[min(len(sorted_vals) - 1, int(q * len(sorted_vals)))]
+
+
+def bench_batched(G, ctx, n=4096, reps=3, tune_sample=512):
     """4,096 rigid transforms of one gear pair (204,800 triangles each):
-    queries/s of the batched form (one persistent launch, gd_batch_query)
-    against the plain form (one gd_min_distance call per query)."""
+    queries/s of the batched form (gd_batch_query: persistent launches of
+    chunks of queries) against the plain form (one gd_min_distance call per
+    query), both with all n queries submitted at once.  Latency per query:
+    batched, the device completion stamp of its result record since the
+    call's first launch (gd_batch_times); plain, the completion of its call
+    since the first call started (the same arrival pattern), and the plain
+    call's own duration.  The tunables are first picked by gd_autotune on a
+    sample of the transforms (batch form), and the batch is timed with them
+    and with the defaults."""
     from paper_2411_11244_gb300 import synth
     A, B, xa, xbs = synth.config_gears(n)
-    ma, mb = G.gd_mesh_create(ctx, *A), G.gd_mesh_create(ctx, *B)
-    G.gd_bvh_build(ma, ctx=ctx)
-    G.gd_bvh_build(mb, ctx=ctx)
-    arr = G.make_queries([(ma, mb, xa, xb, G.GD_MIN) for xb in xbs])
-    out = G.gd_batch_query(ctx, arr)  # warm-up, sizes the buffers
-    walls = []
-    for _ in range(reps):
-        t0 = time.perf_counter()
-        out = G.gd_batch_query(ctx, arr)
-        walls.append(time.perf_counter() - t0)
-    st = G.gd_get_stats(ctx)
+
+    def meshes(c):
+        a, b = G.gd_mesh_create(c, *A), G.gd_mesh_create(c, *B)
+        G.gd_bvh_build(a, ctx=c)
+        G.gd_bvh_build(b, ctx=c)
+        return a, b
+
+    def timed_batch(c, arr):
+        G.gd_batch_query(c, arr)  # warm-up, sizes the buffers
+        walls, done = [], None
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            out = G.gd_batch_query(c, arr)
+            walls.append(time.perf_counter() - t0)
+            done = G.gd_batch_times(c, n)
+        return statistics.median(walls), out, done, G.gd_get_stats(c)
+
+    ma, mb = meshes(ctx)
+    wall_def, out_def, done_def, st_def = timed_batch(ctx, G.make_queries([(ma, mb, xa, xb, G.GD_MIN) for xb in xbs]))
+    # the tuned run on a context of its own (tunables are per context)
+    ctx2 = G.gd_ctx_create(torch_device_index())
+    ta, tb = meshes(ctx2)
+    sample = G.make_queries([(ta, tb, xa, xb, G.GD_MIN) for xb in xbs[::max(1, n // tune_sample)][:tune_sample]])
+    t0 = time.perf_counter()
+    tuned = G.gd_autotune(ctx2, sample, reps=1)
+    tune_s = time.perf_counter() - t0
+    wall, out, done, st = timed_batch(ctx2, G.make_queries([(ta, tb, xa, xb, G.GD_MIN) for xb in xbs]))
+    G.gd_mesh_destroy(ta)
+    G.gd_mesh_destroy(tb)
+    G.gd_ctx_destroy(ctx2)
     bad = sum(1 for i in range(n) if out[i].status != 0)
     zero = sum(1 for i in range(n) if out[i].status == 0 and out[i].d == 0.0)
-    lat = []
+    lat, comp = [], []
+    t00 = time.perf_counter()
     for xb in xbs:
         t0 = time.perf_counter()
         r = G.gd_min_distance(ctx, ma, mb, xa, xb)
-        lat.append(1000.0 * (time.perf_counter() - t0))
+        t1 = time.perf_counter()
+        lat.append(1000.0 * (t1 - t0))
+        comp.append(1000.0 * (t1 - t00))
         assert r.status == 0
+    plain_wall = time.perf_counter() - t00
     lat.sort()
-    wall = statistics.median(walls)
+    comp.sort()
+    bl = sorted(1e-6 * float(x) for x in done)
+    bl_def = sorted(1e-6 * float(x) for x in done_def)
     G.gd_mesh_destroy(ma)
     G.gd_mesh_destroy(mb)
     return {
-        "workload": f"gears: 2 x {len(A[1])} tris, {n} seeded rigid transforms (min distance)",
+        "workload": f"gears: 2 x {len(A[1])} tris, {n} seeded rigid transforms (min distance), all submitted at once",
         "batched_qps": n / wall, "batched_ms_per_batch": 1000.0 * wall,
-        "batched_latency_ms": {"p50": 1000.0 * wall, "p99": 1000.0 * wall},
-        "plain_qps": 1000.0 * n / sum(lat),
-        "plain_latency_ms": {"p50": lat[n // 2], "p99": lat[min(n - 1, int(0.99 * n))]},
-        "speedup_qps": (n / wall) / (1000.0 * n / sum(lat)),
+        "batched_latency_ms": {"p50": _pct(bl, 0.5), "p99": _pct(bl, 0.99),
+                               "what": "device completion stamp of each query's result since the call's first launch"},
+        "batched_default_tunables": {"qps": n / wall_def, "latency_ms": {"p50": _pct(bl_def, 0.5),
+                                                                         "p99": _pct(bl_def, 0.99)}},
+        "autotune": {"sample": len(sample), "seconds": tune_s,
+                     "chosen": {k: tuned[k] for k in ("work_target", "k_max", "probes", "blocks_per_sm",
+                                                      "batch_budget")}},
+        "plain_qps": n / plain_wall,
+        "plain_latency_ms": {"p50": _pct(comp, 0.5), "p99": _pct(comp, 0.99),
+                             "what": "completion of each call since the first call started (same arrival)"},
+        "plain_call_ms": {"p50": _pct(lat, 0.5), "p99": _pct(lat, 0.99), "what": "duration of each call"},
+        "speedup_qps": (n / wall) / (n / plain_wall),
         "mix": {"intersecting": zero, "errors": bad, "separate": n - zero - bad},
-        "batch_kernel": {"levels": st["levels"], "leaf_pairs": st["leaf_pairs"], "candidates": st["candidates"]},
+        "batch_kernel": {"levels": st["levels"], "leaf_pairs": st["leaf_pairs"], "candidates": st["candidates"],
+                         "retries": st["retries"]},
     }
+
+
+def build_roofline(G, meshes, peak, peak_kind):
+    """BVH build (Section 7.3 preprocessing) against the HBM roofline: device
+    time of the build's kernels (gd_mesh_build_time) and the bytes the build
+    must move per triangle T, vertex V and node N: index validation (12 B/T +
+    12 B/V read), Morton codes (12 B/T + 12 B/V read, 12 B/T of key and value
+    written), 8 radix passes of 8 bits over the 63-bit codes (8 B/T histogram
+    read, 12 B/T read and 12 B/T written by the scatter: 256 B/T), the sorted
+    order copied (8 B/T), leaves (4 B/T order + 12 B/T indices + 12 B/V read,
+    48 B/T triangle records written) and 24 B per node box written."""
+    out = []
+    for h, T, V in meshes:
+        L, _ = G.gd_mesh_info(h)
+        ms = G.gd_mesh_build_time(h)
+        alg = 364 * T + 36 * V + 24 * ((2 << L) - 1)
+        gbs = alg / (ms * 1e-3) / 1e9
+        out.append({"triangles": T, "device_ms": ms, "alg_bytes": alg, "achieved": gbs, "peak": peak,
+                    "unit": "GB/s", "frac": gbs / peak, "peak_source": peak_kind})
+    return out
+
+
+def bench_icospheres(G, ctx, steps, warmup, cpu_frames=64, cpu=True):
+    """Near-contact icospheres (2 x 1,310,720 triangles, radius 1, radial
+    noise N(0, 1e-3), x-gap 1e-5 x diag; frame f spins B about its own x-axis),
+    min and max: per kind the device time per query (CUDA events on the
+    query's stream, transforms resident, L2 flushed before every step), the
+    same through the synchronous C ABI call (e2e), the HBM roofline of the
+    query kernel from its counted algorithmic bytes, the FP64 oracle on the
+    host cores on a sample of frames, and the engine's answers against the
+    oracle's on that sample."""
+    import numpy as np
+    import torch
+    from paper_2411_11244_gb300 import synth
+    nfr = max(warmup + steps, cpu_frames)
+    A, B, xa, xbs = synth.config_icosphere_frames(frames=nfr)
+    ma, mb = G.gd_mesh_create(ctx, *A), G.gd_mesh_create(ctx, *B)
+    G.gd_bvh_build(ma, ctx=ctx)
+    G.gd_bvh_build(mb, ctx=ctx)
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    dev = stream.device
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    d_xa = torch.tensor(np.asarray(xa), dtype=torch.float64, device=dev)
+    d_xb = torch.tensor(np.stack(xbs[:warmup + steps]), dtype=torch.float64, device=dev)
+    peak, peak_kind = _peaks()
+    res = {"workload": f"icospheres: 2 x {len(A[1])} tris, radial noise 1e-3, x-gap 1e-5 diag, "
+                       f"B spun about its x-axis per frame", "frames": warmup + steps,
+           "paper_context": {"max_ms": 0.25, "max_workload": "MaxDist: 2 x 1 M tris, RTX 4090 (FP32 only)"}}
+    for kind, k, fn in (("min", G.GD_MIN, G.gd_min_distance), ("max", G.GD_MAX, G.gd_max_distance)):
+        fn(ctx, ma, mb, xa, xbs[0])  # sizes the work buffers
+        d_out = torch.zeros((warmup + steps, 10), dtype=torch.float64, device=dev)
+
+        def one(i):
+            G.gd_query_device(ctx, ma, mb, k, d_xa.data_ptr(), d_xb[i].data_ptr(), d_out[i].data_ptr(), sptr)
+
+        for i in range(warmup):
+            flush.fill_(float(i))
+            one(i)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        stats = []
+        for j in range(steps):
+            flush.fill_(float(j))
+            ev[j][0].record(stream)
+            one(warmup + j)
+            ev[j][1].record(stream)
+            ev[j][1].synchronize()
+            stats.append(G.gd_get_stats(ctx))
+        ms = [a.elapsed_time(b) for a, b in ev]
+        raw = d_out.cpu().numpy()
+        bad = sum(1 for i in range(warmup + steps) if G.gd_result.from_buffer_copy(raw[i].tobytes()).status != 0)
+        e2e = []
+        for j in range(steps):
+            flush.fill_(float(j))
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            fn(ctx, ma, mb, xa, xbs[warmup + j])
+            e2e.append(1000.0 * (time.perf_counter() - t1))
+        mean = statistics.mean(ms)
+        alg = statistics.mean(st["alg_bytes"] for st in stats)
+        sm = sorted(ms)
+        leg = {
+            "ms_per_query": mean, "p50_ms": sm[len(sm) // 2], "p99_ms": sm[min(len(sm) - 1, int(0.99 * len(sm)))],
+            "errors": bad,
+            "e2e": {"value": statistics.mean(e2e), "unit": "ms/query", "h2d_bytes_per_step": 192,
+                    "d2h_bytes_per_step": 336, "p50_ms": sorted(e2e)[len(e2e) // 2]},
+            "roofline": {"bound": "hbm", "achieved": alg / (mean * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": alg / (mean * 1e-3) / 1e9 / peak, "traffic": None, "peak_source": peak_kind,
+                         "kernel": f"k_query<{kind}>", "alg_bytes_per_launch": alg},
+            "traversal": {x: stats[-1][x] for x in ("levels", "pairs_tested", "leaf_pairs", "tri_pairs",
+                                                      "candidates", "refined", "phase_us")},
+        }
+        if cpu:
+            cb = cpu_baseline(A, xa, xbs, cpu_frames, B=B, kind=kind, name="icosphere")
+            answers = cb.pop("_answers")
+            leg["cpu_baseline"] = cb
+            leg["parity"] = parity_spot_check(G, ctx, ma, mb, A, B, xa, xbs, answers[:16], kind)
+        res[kind] = leg
+    G.gd_mesh_destroy(ma)
+    G.gd_mesh_destroy(mb)
+    del flush
+    return res
 
 
 def bench_ablation(G, ctx, ma, mb, xa, xbs, frames=4):
@@ -519,6 +733,7 @@ def main():
     ap.add_argument("--no-deformable", action="store_true")
     ap.add_argument("--no-naive", action="store_true")
     ap.add_argument("--no-points", action="store_true")
+    ap.add_argument("--no-icospheres", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -616,6 +831,7 @@ def main():
     alg = statistics.mean(s["alg_bytes"] for s in stats)
     peak, peak_kind = _peaks()
     achieved = alg / (statistics.mean(ms) * 1e-3) / 1e9
+    clocks = clk.summary()
     line = {
         "metric": METRIC, "value": mean_ms, "unit": "ms/query", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": False, "scaling": "weak",
@@ -628,16 +844,23 @@ def main():
         "gpu_launches": args.steps * world,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": _traffic(), "peak_source": peak_kind,
-                     "kernel": "k_query<min>", "alg_bytes_per_launch": alg},
+                     "kernel": "k_query<min>", "alg_bytes_per_launch": alg,
+                     "fp32": fp32_roofline(statistics.mean(ms), clocks, _counters())},
         "traversal": {k: stats[-1][k] for k in ("levels", "front", "slots", "pairs_tested", "leaf_pairs",
                                                   "tri_pairs", "candidates", "refined", "blocks", "probes",
                                                   "refits", "level_us", "phase_us", "u_probe", "u_level")},
-        "clocks": clk.summary(),
+        "clocks": clocks,
         "wall_s": wall,
+        "build": build_roofline(G, [(ma, len(A[1]), len(A[0]))], peak, peak_kind),
     }
     # the other legs and the oracle's CPU baseline run at one GPU only: with
     # more ranks the others have left, and their GPUs would wait for rank 0
     one = world == 1
+    if one and not args.no_cpu_baseline:
+        cb = cpu_baseline(A, xa, xbs, args.cpu_frames)
+        answers = cb.pop("_answers")
+        line["cpu_baseline"] = cb
+        line["parity"] = parity_spot_check(G, ctx, ma, mb, A, A, xa, xbs, answers[:16], "min")
     if one and not args.no_ablation:
         line["ablation"] = bench_ablation(G, ctx, ma, mb, xa, xbs)
     if one and not args.no_points:
@@ -652,8 +875,8 @@ def main():
         line["batched"] = bench_batched(G, ctx)
     if one and not args.no_served:
         line["served"] = bench_served(G, ctx)
-    if one and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(A, xa, xbs, args.cpu_frames)
+    if one and not args.no_icospheres:
+        line["icospheres"] = bench_icospheres(G, ctx, args.steps, args.warmup, cpu=not args.no_cpu_baseline)
     print(json.dumps(line), flush=True)
     G.gd_ctx_destroy(ctx)
     if world > 1:

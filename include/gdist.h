@@ -231,6 +231,12 @@ GD_API gd_status gd_bvh_build(gd_mesh *mesh, const gd_build_opts *opts);
  * left unbuilt until the next successful update or build). */
 GD_API gd_status gd_mesh_update(gd_mesh *mesh, const float *verts, int64_t nv);
 GD_API void gd_mesh_destroy(gd_mesh *mesh);
+/* Device time in ms of the kernels of the mesh's last gd_bvh_build (index
+ * validation, Morton codes, radix sort, leaves and level reduction; CUDA
+ * events on the context's stream around them, allocations excluded).
+ * Preprocessing: the paper times its builds apart from the queries (Section
+ * 8).  GD_ERR_NOT_BUILT for a mesh without a tree. */
+GD_API gd_status gd_mesh_build_time(const gd_mesh *mesh, double *device_ms);
 /* Tree depth L (leaves = 2^L) and triangle count of a built mesh. */
 GD_API gd_status gd_mesh_info(const gd_mesh *mesh, int32_t *levels, int64_t *triangles);
 /* Copy the BVH to the host for inspection: boxes (6 floats per node, node
@@ -294,15 +300,22 @@ GD_API gd_status gd_query_device(gd_ctx *ctx, const gd_mesh *A, const gd_mesh *B
  * a process whose device memory is held by another allocator).  Same inputs
  * and output as gd_query_device (device pointers; stream is a cudaStream_t,
  * NULL = the legacy default stream); A and B must belong to one context,
- * whose tunables are read.  Every work buffer comes from one 32 MiB array
- * compiled into the library (held by every GPU that loads the library, until
- * exit).  The first call on a device looks up that array's device address:
- * make it before any stream capture.  Limits: B with at most 24 tree levels
- * (fewer than 2^25 triangles; larger B: GD_ERR_INVALID_ARG); at most 2^18
- * front entries, 2^18 leaf pairs and 2^16 float64 candidates per call
+ * and the calling thread's current CUDA device must be that context's device
+ * (otherwise GD_ERR_INVALID_ARG; the call never changes the current device).
+ * The context's tunables (bounds, refit mode, probes, work target, k_max,
+ * timeout) are applied exactly as gd_query_device applies them, so both give
+ * the same traversal.  Every work buffer comes from one 32 MiB array compiled
+ * into the library (held by every GPU that loads the library, until exit).
+ * The first call on a device looks up that array's device address: make it
+ * before any stream capture.  Limits: with refit on, B with at most 24 tree
+ * levels (fewer than 2^25 triangles; larger B: GD_ERR_INVALID_ARG); at most
+ * 2^18 front entries, 2^18 leaf pairs and 2^16 float64 candidates per call
  * (beyond them d_out->status is GD_ERR_OVERFLOW: use gd_query_device).
- * Calls share the array: calls whose work overlaps on the GPU race, so
- * serialise them.  Asynchronous; returns argument and launch errors only. */
+ * Errors: GD_ERR_INVALID_ARG (NULL pointer, bad kind, meshes of two
+ * contexts, wrong current device, B too deep), GD_ERR_NOT_BUILT (a mesh
+ * without a tree), GD_ERR_CUDA (launch failure).  Calls share the array:
+ * calls whose work overlaps on the GPU race, so serialise them.
+ * Asynchronous; returns argument and launch errors only. */
 GD_API gd_status gd_query_device_noalloc(const gd_mesh *A, const gd_mesh *B, gd_kind kind, const double *d_xa,
                                          const double *d_xb, gd_result *d_out, void *stream);
 /* A captured CUDA graph of one device-resident query (the launch of
@@ -329,6 +342,15 @@ GD_API gd_status gd_graph_destroy(gd_graph *g);
  * Results equal those of single queries (the d = 0 witness may differ, see
  * gd_result). */
 GD_API gd_status gd_batch_query(gd_ctx *ctx, const gd_query *q, int64_t n, gd_result *out);
+
+/* Completion times of the queries of the last gd_batch_query on ctx (no
+ * counterpart in the paper): done_ns[i] = device-clock nanoseconds from the
+ * start of that call's first launch to the moment the kernel wrote query i's
+ * final result record (for a query rerun in a later launch, that launch's
+ * record).  Stamps come from the GPU's global timer, so host overheads
+ * before the first launch are not counted.  n must equal the batch's query
+ * count (else GD_ERR_INVALID_ARG); done_ns: n int64 values (host). */
+GD_API gd_status gd_batch_times(gd_ctx *ctx, int64_t n, int64_t *done_ns);
 
 /* ---- serving ----------------------------------------------------------- */
 

@@ -41,6 +41,7 @@ struct gd_mesh {
     unsigned* d_flags = nullptr;  // validation flags of gd_mesh_update
     bool tree = false;            // box, tri and L hold a sorted tree (refit may run)
     bool built = false;           // ... and its boxes bound the current vertices
+    float build_ms = 0.f;         // device time of the last build's kernels
 };
 
 struct gd_ctx {
@@ -66,7 +67,14 @@ struct gd_ctx {
     QIn* qin_host = nullptr;
     gd_result* out_dev = nullptr;
     gd_result* out_host = nullptr;
+    unsigned long long* done_dev = nullptr;   // per-query completion stamps of a launch
+    unsigned long long* done_host = nullptr;  // pinned mirror
     long long cap_q = 0;
+    // completion of each query of the last gd_batch_query, device ns since
+    // the start of the call's first launch
+    std::vector<long long> batch_done;
+    unsigned long long batch_t0 = 0;
+    bool in_batch = false;
     float* rbox = nullptr;        // refit slots
     uint2* jobs = nullptr;
     long long cap_slots = 0;
@@ -182,15 +190,18 @@ gd_status ensure_ws(gd_ctx* c, long long nq) {
     }
     if (nq > c->cap_q) {
         long long cap = std::max<long long>(nq, 2 * c->cap_q);
-        cudaFree(c->qs); cudaFree(c->qin_dev); cudaFree(c->out_dev);
-        cudaFreeHost(c->qin_host); cudaFreeHost(c->out_host);
+        cudaFree(c->qs); cudaFree(c->qin_dev); cudaFree(c->out_dev); cudaFree(c->done_dev);
+        cudaFreeHost(c->qin_host); cudaFreeHost(c->out_host); cudaFreeHost(c->done_host);
         c->qs = nullptr; c->qin_dev = nullptr; c->out_dev = nullptr; c->qin_host = nullptr; c->out_host = nullptr;
+        c->done_dev = nullptr; c->done_host = nullptr;
         c->cap_q = 0;
         GD_CUDA(c, cudaMalloc(&c->qs, sizeof(QState) * cap));
         GD_CUDA(c, cudaMalloc(&c->qin_dev, sizeof(QIn) * cap));
         GD_CUDA(c, cudaMalloc(&c->out_dev, sizeof(gd_result) * cap));
+        GD_CUDA(c, cudaMalloc(&c->done_dev, sizeof(unsigned long long) * cap));
         GD_CUDA(c, cudaMallocHost(&c->qin_host, sizeof(QIn) * cap));
         GD_CUDA(c, cudaMallocHost(&c->out_host, sizeof(gd_result) * cap));
+        GD_CUDA(c, cudaMallocHost(&c->done_host, sizeof(unsigned long long) * cap));
         c->cap_q = cap;
     }
     return GD_OK;
@@ -265,6 +276,16 @@ int grid_blocks(gd_ctx* c, int kind) {
     return b * c->sms;
 }
 
+// The launch fields that follow from the context's tunables.
+void fill_tunables(const gd_ctx* c, KArgs& a) {
+    a.work_target = c->tun.work_target;
+    a.k_max = c->tun.k_max;
+    a.timeout_ns = c->tun.timeout_ns;
+    a.refit = c->tun.refit_mode == 2 ? 0 : 1;
+    a.conventional = c->tun.bounds_mode == 2 ? 1 : 0;
+    a.probes = c->tun.probes;
+}
+
 void fill_common(gd_ctx* c, KArgs& a, unsigned* ctr, StatsDev* stats) {
     a.qs = c->qs;
     a.front0 = c->front[0];
@@ -278,16 +299,11 @@ void fill_common(gd_ctx* c, KArgs& a, unsigned* ctr, StatsDev* stats) {
     a.cap_cand = (unsigned)c->cap_cand;
     a.ctr = ctr;
     a.stats = stats;
-    a.work_target = c->tun.work_target;
-    a.k_max = c->tun.k_max;
-    a.timeout_ns = c->tun.timeout_ns;
     a.rbox = c->rbox;
     a.jobs = c->jobs;
     a.cap_slots = (unsigned)c->cap_slots;
     a.slot_of = c->slot_of;
-    a.refit = c->tun.refit_mode == 2 ? 0 : 1;
-    a.conventional = c->tun.bounds_mode == 2 ? 1 : 0;
-    a.probes = c->tun.probes;
+    fill_tunables(c, a);
     a.n_slot_of = 0;
 }
 
@@ -352,6 +368,7 @@ gd_status run_single(gd_ctx* ctx, const gd_mesh* A, const gd_mesh* B, int kind, 
         a.slot_of = ctx->slot_of;
         a.n_slot_of = (unsigned long long)tab;
         a.out = &ctx->mb_dev->out;
+        a.done_ns = ctx->in_batch ? ctx->done_dev : nullptr;
         int grid = grid_blocks(ctx, kind);
         a.work_ctas = single_work_ctas(ctx, grid);
         a.fuse_root = single_fuse_root(ctx, B);
@@ -436,12 +453,16 @@ gd_status batch_pass(gd_ctx* ctx, const gd_query* q, const std::vector<int64_t>&
     a.slot_of = ctx->slot_of;
     a.n_slot_of = (unsigned long long)tab;
     a.out = ctx->out_dev;
+    a.done_ns = ctx->done_dev;
     batch_limits(ctx->cap_front, ctx->cap_leaf, m, &a.q_budget, &a.q_pool);
     int grid = grid_blocks(ctx, kind);
     GD_CUDA(ctx, launch_query(kind, a, grid, ctx->stream));
     GD_CUDA(ctx, cudaMemcpyAsync(ctx->out_host, ctx->out_dev, sizeof(gd_result) * m, cudaMemcpyDeviceToHost, ctx->stream));
+    GD_CUDA(ctx, cudaMemcpyAsync(ctx->done_host, ctx->done_dev, sizeof(unsigned long long) * m,
+                                 cudaMemcpyDeviceToHost, ctx->stream));
     GD_CUDA(ctx, cudaMemcpyAsync(ctx->mb_host, ctx->mb_dev, sizeof(Mailbox), cudaMemcpyDeviceToHost, ctx->stream));
     GD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->batch_t0 == 0) ctx->batch_t0 = ctx->mb_host->stats.t_start;
     gd_stats st;
     to_stats(ctx->mb_host->stats, (unsigned)grid, 0, &st);
     agg->levels = std::max(agg->levels, st.levels);
@@ -462,6 +483,7 @@ gd_status batch_pass(gd_ctx* ctx, const gd_query* q, const std::vector<int64_t>&
                     "internal index check failed (sites " + std::to_string(ctx->mb_host->ctr[kCtrBadIndex]) + ")");
     for (long long j = 0; j < m; ++j) {
         out[ids[j]] = ctx->out_host[j];
+        ctx->batch_done[ids[j]] = (long long)(ctx->done_host[j] - ctx->batch_t0);
         if (ctx->out_host[j].status == GD_ERR_OVERFLOW) redo->push_back(ids[j]);
     }
     return GD_OK;
@@ -514,8 +536,8 @@ GD_API void gd_ctx_destroy(gd_ctx* c) {
     cudaFree(c->mb_dev);
     cudaFreeHost(c->mb_host);
     cudaFreeHost(c->hd);
-    cudaFree(c->qs); cudaFree(c->qin_dev); cudaFree(c->out_dev);
-    cudaFreeHost(c->qin_host); cudaFreeHost(c->out_host);
+    cudaFree(c->qs); cudaFree(c->qin_dev); cudaFree(c->out_dev); cudaFree(c->done_dev);
+    cudaFreeHost(c->qin_host); cudaFreeHost(c->out_host); cudaFreeHost(c->done_host);
     cudaFree(c->slot_of);
     cudaFree(c->naive_ws);
     cudaFree(c->point_ws); cudaFree(c->pts_dev); cudaFree(c->pres_dev);
@@ -619,6 +641,14 @@ GD_API gd_status gd_autotune(gd_ctx* c, const gd_query* sample, int64_t n, int32
     return GD_OK;
 }
 
+GD_API gd_status gd_batch_times(gd_ctx* c, int64_t n, int64_t* done_ns) {
+    if (!c) return GD_ERR_INVALID_ARG;
+    if (!done_ns || n != (int64_t)c->batch_done.size())
+        return fail(c, GD_ERR_INVALID_ARG, "n must be the query count of the last gd_batch_query");
+    for (int64_t i = 0; i < n; ++i) done_ns[i] = c->batch_done[(size_t)i];
+    return GD_OK;
+}
+
 GD_API gd_status gd_ctx_get_tunables(gd_ctx* c, gd_tunables* t) {
     if (!c || !t) return GD_ERR_INVALID_ARG;
     *t = c->tun;
@@ -704,17 +734,33 @@ GD_API gd_status gd_bvh_build(gd_mesh* m, const gd_build_opts* opts) {
     b.tri = m->d_tri;
     b.order = m->d_order;
     unsigned flags[8] = {0};
+    // device time of the build's kernels: events around the validation and
+    // around the tree build (not the allocations and the flag read-back)
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (cudaEvent_t& x : ev) cudaEventCreate(&x);
+    auto drop_events = [&]() { for (cudaEvent_t& x : ev) if (x) cudaEventDestroy(x); };
+    cudaEventRecord(ev[0], ctx->stream);
     e = build_validate(b, ctx->stream);
+    cudaEventRecord(ev[1], ctx->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(flags, b.flags, sizeof(flags), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) { cleanup(); return cuda_fail(ctx, e, "gd_bvh_build validate"); }
-    if (flags[0]) { cleanup(); return fail(ctx, GD_ERR_INVALID_ARG, "triangle index out of range"); }
-    if (flags[1]) { cleanup(); return fail(ctx, GD_ERR_INVALID_ARG, "non-finite vertex coordinate"); }
+    if (e != cudaSuccess) { drop_events(); cleanup(); return cuda_fail(ctx, e, "gd_bvh_build validate"); }
+    if (flags[0]) { drop_events(); cleanup(); return fail(ctx, GD_ERR_INVALID_ARG, "triangle index out of range"); }
+    if (flags[1]) { drop_events(); cleanup(); return fail(ctx, GD_ERR_INVALID_ARG, "non-finite vertex coordinate"); }
+    cudaEventRecord(ev[2], ctx->stream);
     e = build_tree(b, ctx->stream);
+    cudaEventRecord(ev[3], ctx->stream);
     float root[6];
     if (e == cudaSuccess) e = cudaMemcpyAsync(root, m->d_box + 6, sizeof(root), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     cleanup();
+    if (e == cudaSuccess) {
+        float t0 = 0.f, t1 = 0.f;
+        cudaEventElapsedTime(&t0, ev[0], ev[1]);
+        cudaEventElapsedTime(&t1, ev[2], ev[3]);
+        m->build_ms = t0 + t1;
+    }
+    drop_events();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "gd_bvh_build");
     float P = 0.f;
     for (int i = 0; i < 6; ++i) P = std::max(P, std::fabs(root[i]));
@@ -773,6 +819,13 @@ GD_API void gd_mesh_destroy(gd_mesh* m) {
     cudaFree(m->d_verts); cudaFree(m->d_tris); cudaFree(m->d_box); cudaFree(m->d_tri); cudaFree(m->d_desc);
     cudaFree(m->d_order); cudaFree(m->d_flags);
     delete m;
+}
+
+GD_API gd_status gd_mesh_build_time(const gd_mesh* m, double* device_ms) {
+    if (!m || !device_ms) return GD_ERR_INVALID_ARG;
+    if (!m->tree) return GD_ERR_NOT_BUILT;
+    *device_ms = m->build_ms;
+    return GD_OK;
 }
 
 GD_API gd_status gd_mesh_info(const gd_mesh* m, int32_t* levels, int64_t* triangles) {
@@ -1082,6 +1135,13 @@ GD_API gd_status gd_batch_query(gd_ctx* ctx, const gd_query* q, int64_t n, gd_re
     }
     unsigned total_retries = 0;
     gd_stats agg{};
+    ctx->batch_done.assign((size_t)n, -1);
+    ctx->batch_t0 = 0;
+    struct InBatch {
+        gd_ctx* c;
+        ~InBatch() { c->in_batch = false; }
+    } in_batch_guard{ctx};
+    ctx->in_batch = true;
     for (int kind = 0; kind < 2; ++kind) {
         std::vector<int64_t> idx;
         for (int64_t i = 0; i < n; ++i)
@@ -1106,6 +1166,16 @@ GD_API gd_status gd_batch_query(gd_ctx* ctx, const gd_query* q, int64_t n, gd_re
                     gd_status r = run_single(ctx, q[i].a, q[i].b, kind, q[i].xa, q[i].xb, &out[i]);
                     total_retries += ctx->pending_retries;
                     if (r != GD_OK && r != GD_ERR_OVERFLOW) return r;
+                    // its completion stamp (and, for a batch that starts with
+                    // a lone query, the call's first launch start)
+                    unsigned long long st[2] = {0ull, 0ull};
+                    GD_CUDA(ctx, cudaMemcpy(&st[0], ctx->done_dev, sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+                    if (ctx->batch_t0 == 0) {
+                        GD_CUDA(ctx, cudaMemcpy(&st[1], &ctx->mb_dev->stats.t_start, sizeof(unsigned long long),
+                                                cudaMemcpyDeviceToHost));
+                        ctx->batch_t0 = st[1];
+                    }
+                    ctx->batch_done[i] = (long long)(st[0] - ctx->batch_t0);
                     continue;
                 }
                 std::vector<int64_t> part(cur.begin() + b, cur.begin() + e);
@@ -1196,5 +1266,16 @@ long long serve_mesh_tris(const gd_mesh* m) { return m ? m->nt : 0; }
 gd_ctx* mesh_ctx(const gd_mesh* m) { return m ? m->ctx : nullptr; }
 const MeshDev* mesh_desc(const gd_mesh* m) { return m && m->built ? m->d_desc : nullptr; }
 int mesh_levels(const gd_mesh* m) { return m ? m->L : 0; }
+
+// The launch shape and the tunable-derived fields of a single query on ctx
+// against B, exactly as gd_query_device sets them: grid, background probe
+// CTAs, the fused root push, bounds and refit modes.  Returns the grid.
+int single_launch_fields(gd_ctx* c, const gd_mesh* B, int kind, KArgs& a) {
+    fill_tunables(c, a);
+    const int grid = grid_blocks(c, kind);
+    a.work_ctas = single_work_ctas(c, grid);
+    a.fuse_root = single_fuse_root(c, B);
+    return grid;
+}
 
 }  // namespace gd

@@ -132,6 +132,7 @@ struct StatsDev {
     float u_level[32];      // running bound of query 0 entering each level
     float u_probe;          // ... right after the probes
     unsigned refits;        // B subtrees refit into A's frame
+    unsigned long long t_start;  // globaltimer at the launch's start (CTA 0)
 };
 
 // Result record of a single query in pinned host memory, written by the
@@ -185,6 +186,8 @@ struct KArgs {
                                 // grid barriers; the rest run background probes (0: all)
     HostDone* host_done;        // single query: copy of the result for the host (or nullptr)
     unsigned long long seq;     // ... stamped with this sequence number
+    unsigned long long* done_ns;// per query of the launch: globaltimer when its result record
+                                // was final (or nullptr)
 };
 
 // ------------------------------------------------------------------ memory

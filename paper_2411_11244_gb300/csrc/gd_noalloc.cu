@@ -40,8 +40,9 @@ constexpr unsigned kNaTableBits = 16;       // refit-root table: B with at most 
 gd_ctx* mesh_ctx(const gd_mesh* m);
 const MeshDev* mesh_desc(const gd_mesh* m);
 int mesh_levels(const gd_mesh* m);
-int serve_sms(gd_ctx* ctx);
+int serve_device(gd_ctx* ctx);
 const gd_tunables& serve_tunables(gd_ctx* ctx);
+int single_launch_fields(gd_ctx* c, const gd_mesh* B, int kind, KArgs& a);
 
 namespace {
 
@@ -53,7 +54,7 @@ struct Layout {
 
 constexpr unsigned long long up256(unsigned long long x) { return (x + 255ull) & ~255ull; }
 
-Layout layout() {
+constexpr Layout layout() {
     Layout L{};
     unsigned long long o = 0;
     L.ctr = o; o = up256(o + sizeof(unsigned) * kCtrWords);
@@ -71,6 +72,8 @@ Layout layout() {
     L.end = o;
     return L;
 }
+static_assert(layout().end <= kScratchBytes, "the work buffers fit the static array");
+static_assert(sizeof(unsigned) * kCtrWords <= 256, "counters fit their slot");
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
@@ -103,23 +106,26 @@ extern "C" GD_API gd_status gd_query_device_noalloc(const gd_mesh* A, const gd_m
     const MeshDev* db = mesh_desc(B);
     if (!ctx || mesh_ctx(B) != ctx) return GD_ERR_INVALID_ARG;
     if (!da || !db) return GD_ERR_NOT_BUILT;
-    // the refit-root table of the array holds 2^16 entries: B may have at most
-    // 16 + 8 = 24 tree levels (fewer than 2^25 triangles)
+    // the meshes' descriptors live on their context's device, and the array
+    // used is the current device's: they must be the same device (this call
+    // changes no device state, so it is refused rather than switched)
+    int device = -1;
+    if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kMaxDevices) return GD_ERR_CUDA;
+    if (device != serve_device(ctx)) return GD_ERR_INVALID_ARG;
+    // the refit-root table of the array holds 2^16 entries: with refit on, B
+    // may have at most 16 + 8 = 24 tree levels (fewer than 2^25 triangles);
+    // with refit off the table is not used
+    const bool refit = serve_tunables(ctx).refit_mode != 2;
     const int LB = mesh_levels(B);
     const int dR = LB > kRefitH ? LB - kRefitH : 0;
-    if (dR > (int)kNaTableBits) return GD_ERR_INVALID_ARG;
-    static_assert(sizeof(unsigned) * kCtrWords <= 256, "counters fit their slot");
-    const Layout L = layout();
-    if (L.end > kScratchBytes) return GD_ERR_INVALID_ARG;
-    int device = 0;
-    if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kMaxDevices) return GD_ERR_CUDA;
+    if (refit && dR > (int)kNaTableBits) return GD_ERR_INVALID_ARG;
+    constexpr Layout L = layout();
     unsigned char* base = nullptr;
     if (scratch_base(device, &base) != cudaSuccess) return GD_ERR_CUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // counters and barrier words must start at zero
     if (cudaMemsetAsync(base + L.ctr, 0, sizeof(unsigned) * kCtrWords, st) != cudaSuccess) return GD_ERR_CUDA;
 
-    const gd_tunables& tun = serve_tunables(ctx);
     KArgs a{};
     a.nq = 1;
     a.qin = nullptr;
@@ -143,16 +149,11 @@ extern "C" GD_API gd_status gd_query_device_noalloc(const gd_mesh* A, const gd_m
     a.rbox = reinterpret_cast<float*>(base + L.rbox);
     a.cap_slots = kNaSlots;
     a.slot_of = reinterpret_cast<unsigned*>(base + L.slot_of);
-    a.n_slot_of = 1ull << dR;
+    a.n_slot_of = refit ? 1ull << dR : 0ull;
     a.jobs = reinterpret_cast<uint2*>(base + L.jobs);
-    a.refit = tun.refit_mode == 2 ? 0 : 1;
-    a.probes = tun.probes;
-    a.work_target = tun.work_target;
-    a.k_max = tun.k_max;
-    a.timeout_ns = tun.timeout_ns;
-    int occ = query_max_blocks_per_sm((int)kind);
-    int bps = tun.blocks_per_sm > 0 ? (tun.blocks_per_sm < occ ? tun.blocks_per_sm : occ) : occ;
-    if (bps < 1) bps = 1;
-    if (launch_query((int)kind, a, bps * serve_sms(ctx), st) != cudaSuccess) return GD_ERR_CUDA;
+    // tunables, grid, background probes and root push as gd_query_device
+    // sets them, so both entry points run the same traversal
+    const int grid = single_launch_fields(ctx, B, (int)kind, a);
+    if (launch_query((int)kind, a, grid, st) != cudaSuccess) return GD_ERR_CUDA;
     return GD_OK;
 }

@@ -1720,6 +1720,7 @@ __device__ void status_phase(const KArgs& A, unsigned long long first, unsigned 
             r.d = __longlong_as_double(0x7ff8000000000000ll);
             r.tri_a = r.tri_b = -1;
         }
+        if (A.done_ns) A.done_ns[q] = globaltimer();
     }
 }
 
@@ -1816,6 +1817,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
         S->leaf_pairs = S->candidates = 0;
         S->probes = 0;
         S->refits = 0;
+        S->t_start = t_start;
         S->u_probe = 0.f;
         for (int i = 0; i < 12; ++i) S->phase_ns[i] = 0;
         for (int i = 0; i < 32; ++i) { S->level_ns[i] = 0; S->u_level[i] = 0.f; }

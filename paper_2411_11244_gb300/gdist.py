@@ -30,7 +30,8 @@ EXPORTS = [
     "gd_ctx_create", "gd_ctx_destroy", "gd_last_error", "gd_ctx_set_tunables", "gd_ctx_get_tunables",
     "gd_get_stats", "gd_ctx_stream", "gd_mesh_create", "gd_bvh_build", "gd_mesh_update", "gd_mesh_destroy", "gd_mesh_info",
     "gd_mesh_download", "gd_min_distance", "gd_max_distance", "gd_naive_query", "gd_point_distance", "gd_point_stats", "gd_query_device", "gd_query_device_noalloc",
-    "gd_batch_query", "gd_autotune", "gd_graph_create", "gd_graph_launch", "gd_graph_destroy",
+    "gd_batch_query", "gd_batch_times", "gd_autotune", "gd_graph_create", "gd_graph_launch", "gd_graph_destroy",
+    "gd_mesh_build_time",
     "gd_serve_start", "gd_serve_submit", "gd_serve_poll", "gd_serve_drain", "gd_serve_stop",
 ]
 
@@ -137,6 +138,8 @@ def load(path: str = LIB_PATH):
         "gd_query_device": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp, _vp, _vp, _vp]),
         "gd_query_device_noalloc": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _vp, _vp]),
         "gd_batch_query": (C.c_int, [_vp, C.POINTER(gd_query), C.c_int64, C.POINTER(gd_result)]),
+        "gd_batch_times": (C.c_int, [_vp, C.c_int64, C.POINTER(C.c_int64)]),
+        "gd_mesh_build_time": (C.c_int, [_vp, C.POINTER(C.c_double)]),
         "gd_autotune": (C.c_int, [_vp, C.POINTER(gd_query), C.c_int64, C.c_int32, C.POINTER(gd_tunables)]),
         "gd_graph_create": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp, _vp, _vp, C.POINTER(_vp)]),
         "gd_graph_launch": (C.c_int, [_vp, _vp]),
@@ -251,6 +254,13 @@ def gd_mesh_info(mesh):
     T = C.c_int64()
     _check(load().gd_mesh_info(mesh, C.byref(L), C.byref(T)))
     return L.value, T.value
+
+
+def gd_mesh_build_time(mesh) -> float:
+    """Device ms of the kernels of the mesh's last BVH build."""
+    t = C.c_double()
+    _check(load().gd_mesh_build_time(mesh, C.byref(t)))
+    return t.value
 
 
 def gd_mesh_download(mesh):
@@ -402,6 +412,14 @@ def gd_batch_query(ctx, queries):
     n = len(queries)
     out = (gd_result * n)()
     _check(load().gd_batch_query(ctx, queries, n, out), ctx)
+    return out
+
+
+def gd_batch_times(ctx, n: int) -> np.ndarray:
+    """Per-query completion times of the last gd_batch_query (device ns since
+    the start of that call's first launch)."""
+    out = np.zeros(n, dtype=np.int64)
+    _check(load().gd_batch_times(ctx, n, out.ctypes.data_as(C.POINTER(C.c_int64))), ctx)
     return out
 
 

@@ -405,6 +405,21 @@ def config_icospheres(level: int = 8, seed: int = 0, noise: float = 1e-3, gap_fr
     return A, B, identity_xform(), xform(np.eye(3), (shift, 0.0, 0.0))
 
 
+def config_icosphere_frames(frames: int = 100, level: int = 8, seed: int = 0, noise: float = 1e-3,
+                            gap_frac: float = 1e-5):
+    """The near-contact icospheres of config_icospheres as a frame sequence:
+    frame 0 is that placement; frame f > 0 first spins B about its own x-axis
+    by a seeded uniform angle.  The spin keeps every x-coordinate of B, so the
+    x-extents stay gap_frac x diag apart while the noisy surfaces that face
+    each other change from frame to frame.  Returns (A, B, xa, [xb...])."""
+    A, B, xa, xb0 = config_icospheres(level, seed, noise, gap_frac)
+    rng = np.random.default_rng(seed + 11)
+    xbs = [xb0]
+    for _ in range(frames - 1):
+        xbs.append(compose(xb0, xform(rot_axis((1, 0, 0), rng.uniform(0.0, 2 * math.pi)), (0.0, 0.0, 0.0))))
+    return A, B, xa, xbs
+
+
 def config_gears(n: int = 4096, seed: int = 0, M: int = 2048, K: int = 24):
     """One gear pair (4*M*K + 4*M triangles each) under n seeded rigid
     transforms of B: uniform rotation, centre offset in a uniformly random
