@@ -452,16 +452,23 @@ def bench_ablation(G, ctx, ma, mb, xa, xbs, frames=4):
     p_enh, t_enh, d_enh = run(bounds_mode=1)
     p_conv, t_conv, d_conv = run(bounds_mode=2)
     p_fix, t_fix, d_fix = run(bounds_mode=1, k_max=5, work_target=1 << 40)
-    G.gd_ctx_set_tunables(ctx, bounds_mode=1, k_max=base["k_max"], work_target=base["work_target"])
+    G.gd_ctx_set_tunables(ctx, k_max=base["k_max"], work_target=base["work_target"])
+    p_full, t_full, d_full = run(bounds_mode=1, refit_mode=3)
+    p_none, t_none, d_none = run(bounds_mode=1, refit_mode=2)
+    G.gd_ctx_set_tunables(ctx, bounds_mode=1, refit_mode=base["refit_mode"])
     return {
         "frames": frames,
-        "enhanced": {"pairs_tested": p_enh, "ms": t_enh},
-        "conventional": {"pairs_tested": p_conv, "ms": t_conv},
-        "fixed_k5": {"pairs_tested": p_fix, "ms": t_fix},
+        "enhanced": {"pairs_tested": p_enh, "ms": t_enh, "what": "enhanced bounds (Eqs. 10-11), lazy refit"},
+        "conventional": {"pairs_tested": p_conv, "ms": t_conv, "what": "conventional bounds only (Eq. 9)"},
+        "fixed_k5": {"pairs_tested": p_fix, "ms": t_fix, "what": "fixed k = 5 (no adaptive depth)"},
+        "full_refit": {"pairs_tested": p_full, "ms": t_full,
+                       "what": "the paper's per-frame refit of all of B into A's frame, then AABB bounds"},
+        "no_refit": {"pairs_tested": p_none, "ms": t_none, "what": "B's boxes mapped on the fly, never refit"},
         "pairs_ratio_enhanced_over_conventional": p_enh / p_conv,
         "slowdown_conventional": t_conv / t_enh,
         "slowdown_fixed_k5": t_fix / t_enh,
-        "same_answers": d_enh == d_conv == d_fix,
+        "slowdown_full_refit": t_full / t_enh,
+        "same_answers": d_enh == d_conv == d_fix == d_full == d_none,
     }
 
 
@@ -609,8 +616,9 @@ def bench_points(G, ctx, ma, n=1 << 20, reps=3):
 def bench_served(G, ctx, rates=(1000, 3000, 10000, 30000, 100000), n_req=1500, seed=0):
     """A pool of 64 meshes (tori, geodesic spheres, gears; 1e3..4e6 triangles,
     BVHs resident) and a stream of random mesh pairs and transforms arriving
-    as a Poisson process of rate lambda.  Served: gd_serve_submit/poll
-    (continuous batching over stream slots).  Plain: one gd_min_distance per
+    as a Poisson process of rate lambda.  Served: gd_serve_submit/drain with
+    the default options (continuous batching on one whole-GPU lane, 8 GiB
+    footprint budget, batches of up to 16).  Plain: one gd_min_distance per
     request in arrival order.  Latency = completion - arrival (completion: when
     the result is collected, by gd_serve_drain or on return of the call)."""
     import numpy as np
@@ -734,6 +742,7 @@ def main():
     ap.add_argument("--no-naive", action="store_true")
     ap.add_argument("--no-points", action="store_true")
     ap.add_argument("--no-icospheres", action="store_true")
+    ap.add_argument("--batched-queries", type=int, default=4096)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -872,7 +881,7 @@ def main():
     G.gd_mesh_destroy(ma)
     G.gd_mesh_destroy(mb)
     if one and not args.no_batched:
-        line["batched"] = bench_batched(G, ctx)
+        line["batched"] = bench_batched(G, ctx, n=args.batched_queries)
     if one and not args.no_served:
         line["served"] = bench_served(G, ctx)
     if one and not args.no_icospheres:

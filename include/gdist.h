@@ -124,7 +124,13 @@ typedef struct {
     int64_t timeout_ns;    /* bound on every device-side wait (default 2e9) */
     int32_t refit_mode;    /* 1: refit B's low subtrees (2^8 leaves) into A's
                               frame when the front first reaches them (default);
-                              2: never, bound B's local boxes under the map */
+                              2: never, bound B's local boxes under the map;
+                              3: refit all of B into A's frame at the start of
+                              every single query, the paper's per-frame refit
+                              of Section 8 (batches, the server and
+                              gd_query_device_noalloc, which has no room for a
+                              whole tree, then run as 2).  Same results in
+                              every mode */
     int32_t refit_slots;   /* subtrees refit per launch (default 2^13) */
     int32_t probes;        /* greedy probes that seed the running bound
                               (default 64).  Single queries: they start at the
@@ -355,19 +361,42 @@ GD_API gd_status gd_batch_times(gd_ctx *ctx, int64_t n, int64_t *done_ns);
 /* ---- serving ----------------------------------------------------------- */
 
 typedef struct {
-    int32_t slots;            /* concurrent in-flight batches (default 2) */
+    int32_t slots;            /* ignored (kept for layout): the server runs one
+                                 launch at a time on the whole GPU, since CUDA
+                                 does not promise that cooperative grids
+                                 launched on different streams are resident
+                                 together */
     int32_t max_batch;        /* queries per launch (default 16) */
-    int64_t memory_budget;    /* bytes of work buffers across slots (default 8 GiB) */
+    int64_t memory_budget;    /* bytes of work buffers of the server's lane
+                                 (default 8 GiB); requests are admitted while
+                                 the predicted footprints of the queued and
+                                 running ones stay within it */
     int32_t linger_us;        /* wait this long for more requests before
                                  launching a partial batch (default 0) */
 } gd_serve_opts;
 
-/* Start a serving loop on ctx (continuous batching: queued requests are
- * admitted into free slots and launched while other slots are running). */
+/* Predicted work-buffer bytes of one query (the server's admission model:
+ * power laws in sqrt(T_A) + sqrt(T_B) fitted as upper envelopes of the front,
+ * leaf-pair and candidate peaks measured on single queries).  No counterpart
+ * in the paper; its memory analysis (Section 8) separates the static BVH
+ * memory from the dynamic front memory that this predicts. */
+GD_API gd_status gd_query_footprint(const gd_query *q, int64_t *bytes);
+
+/* Start a server on ctx's device (continuous batching: a serving thread takes
+ * all queued requests of the oldest request's kind, up to max_batch and
+ * within the memory budget, into one persistent launch on the whole GPU, and
+ * requests that arrive meanwhile join the next launch as soon as it ends; a
+ * lone request runs as a single query).  The server has its own stream and
+ * work buffers (sized from memory_budget, allocated here); ctx is used only to
+ * validate submissions and must outlive the server. */
 GD_API gd_status gd_serve_start(gd_ctx *ctx, const gd_serve_opts *opts, gd_server **out);
 /* Enqueue one query; GD_ERR_BUSY if the queue is full (max(4096, 16 x
- * max_batch x slots) waiting requests) or the footprint of the waiting
- * requests would exceed the memory budget.  *ticket identifies the request. */
+ * max_batch) waiting requests) or if its predicted footprint
+ * (gd_query_footprint) would take the footprints held by queued and running
+ * requests beyond the memory budget (a request's footprint is held from
+ * submission until its result is ready; a request larger than the whole
+ * budget is admitted only when nothing else is held, and runs alone with
+ * buffers grown for it).  *ticket identifies the request. */
 GD_API gd_status gd_serve_submit(gd_server *srv, const gd_query *q, uint64_t *ticket);
 /* GD_OK and *out filled if the ticket is done (the ticket is then released);
  * GD_ERR_NOT_READY otherwise. */

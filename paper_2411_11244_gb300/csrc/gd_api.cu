@@ -20,6 +20,9 @@ using namespace gd;
 
 // A single query's result and counters come back after every query (the
 // first kResultBytes); its statistics only when gd_get_stats asks.
+// single-query launches the server keeps in flight on its stream
+constexpr int kPipe = 2;
+
 struct Mailbox {
     gd_result out;
     unsigned ctr[kCtrWords];
@@ -60,7 +63,8 @@ struct gd_ctx {
     long long cap_front = 0, cap_leaf = 0, cap_cand = 0;
     Mailbox* mb_dev = nullptr;   // single-query results, stats and counters
     Mailbox* mb_host = nullptr;  // pinned mirror
-    HostDone* hd = nullptr;      // pinned result record of a single query, written by the kernel
+    HostDone* hd = nullptr;      // pinned result records, written by the kernel: [0] for the
+                                 // synchronous calls, [1..kPipe] for the server's pipelined launches
     unsigned long long hd_seq = 0;
     QState* qs = nullptr;
     QIn* qin_dev = nullptr;
@@ -80,6 +84,8 @@ struct gd_ctx {
     long long cap_slots = 0;
     unsigned* slot_of = nullptr;  // refit-root tables
     long long cap_table = 0;
+    float* ftree = nullptr;       // refit mode 3: B's whole tree in A's frame
+    long long cap_ftree = 0;      // ... its capacity in nodes
     unsigned long long* naive_ws = nullptr;  // scratch of the naive comparator
     unsigned long long* point_ws = nullptr;  // counters of point queries
     double* pts_dev = nullptr;               // staged host points and results
@@ -141,7 +147,7 @@ void free_ws(gd_ctx* c) {
 
 // entries of the refit-root table a query needs (0 when refit is off)
 long long table_entries(const gd_ctx* c, const gd_mesh* B) {
-    if (c->tun.refit_mode == 2) return 0;
+    if (c->tun.refit_mode != 1) return 0;
     int dR = B->L > kRefitH ? B->L - kRefitH : 0;
     return 1ll << dR;
 }
@@ -154,6 +160,24 @@ gd_status ensure_table(gd_ctx* c, long long n) {
     long long cap = std::max<long long>(n, 1 << 16);
     GD_CUDA(c, cudaMalloc(&c->slot_of, sizeof(unsigned) * cap));
     c->cap_table = cap;
+    return GD_OK;
+}
+
+// Refit mode 3 (single queries): B's whole tree is refit into A's frame at
+// the start of every launch, into this buffer (grown to B's node count).
+gd_status full_refit_tree(gd_ctx* c, const gd_mesh* B, KArgs& a) {
+    a.ftree = nullptr;
+    if (c->tun.refit_mode != 3) return GD_OK;
+    const long long nodes = 2ll << B->L;
+    if (nodes > c->cap_ftree) {
+        cudaFree(c->ftree);
+        c->ftree = nullptr;
+        c->cap_ftree = 0;
+        GD_CUDA(c, cudaMalloc(&c->ftree, sizeof(float) * 6 * nodes));
+        c->cap_ftree = nodes;
+        ++c->ws_gen;
+    }
+    a.ftree = c->ftree;
     return GD_OK;
 }
 
@@ -178,8 +202,8 @@ gd_status ensure_ws(gd_ctx* c, long long nq) {
         GD_CUDA(c, cudaMalloc(&c->mb_dev, sizeof(Mailbox)));
         GD_CUDA(c, cudaMemset(c->mb_dev, 0, sizeof(Mailbox)));
         GD_CUDA(c, cudaMallocHost(&c->mb_host, sizeof(Mailbox)));
-        GD_CUDA(c, cudaMallocHost(&c->hd, sizeof(HostDone)));
-        std::memset(c->hd, 0, sizeof(HostDone));
+        GD_CUDA(c, cudaMallocHost(&c->hd, sizeof(HostDone) * (1 + kPipe)));
+        std::memset(c->hd, 0, sizeof(HostDone) * (1 + kPipe));
     }
     if (!c->ready) {
         c->cap_front = std::min<long long>(c->tun.front_capacity, 0xffffffffll);
@@ -258,7 +282,7 @@ gd_status size_for_batch(gd_ctx* c, long long m, long long share) {
 // Whether phase 0 of a single query may push its root pair itself: only when
 // the root needs no refit claim (refit off, or B deeper than one refit tree).
 int single_fuse_root(const gd_ctx* c, const gd_mesh* B) {
-    return (c->tun.refit_mode == 2 || B->L > kRefitH) ? 1 : 0;
+    return (c->tun.refit_mode != 1 || B->L > kRefitH) ? 1 : 0;
 }
 
 // CTAs of a single-query launch that run the traversal: the others (one per
@@ -281,7 +305,7 @@ void fill_tunables(const gd_ctx* c, KArgs& a) {
     a.work_target = c->tun.work_target;
     a.k_max = c->tun.k_max;
     a.timeout_ns = c->tun.timeout_ns;
-    a.refit = c->tun.refit_mode == 2 ? 0 : 1;
+    a.refit = c->tun.refit_mode == 1 ? 1 : 0;
     a.conventional = c->tun.bounds_mode == 2 ? 1 : 0;
     a.probes = c->tun.probes;
 }
@@ -340,12 +364,16 @@ gd_status check_pair(gd_ctx* ctx, const gd_mesh* A, const gd_mesh* B) {
     return GD_OK;
 }
 
+// own: the meshes must belong to ctx (a server's private execution context
+// runs meshes of the user's context on the same device and passes false)
 gd_status run_single(gd_ctx* ctx, const gd_mesh* A, const gd_mesh* B, int kind, const double* xa, const double* xb,
-                     gd_result* out) {
+                     gd_result* out, bool own = true) {
     if (!ctx) return GD_ERR_INVALID_ARG;
     if (!out || !xa || !xb) return fail(ctx, GD_ERR_INVALID_ARG, "NULL argument");
-    gd_status s = check_pair(ctx, A, B);
+    gd_status s = own ? check_pair(ctx, A, B) : GD_OK;
     if (s != GD_OK) return s;
+    if (!own && (!A || !B || !A->built || !B->built || A->ctx->device != ctx->device))
+        return fail(ctx, GD_ERR_INVALID_ARG, "meshes not built on this device");
     std::string why;
     if (!xform_ok(xa, &why) || !xform_ok(xb, &why)) return fail(ctx, GD_ERR_INVALID_ARG, why);
     s = ensure_ws(ctx, 1);
@@ -369,6 +397,8 @@ gd_status run_single(gd_ctx* ctx, const gd_mesh* A, const gd_mesh* B, int kind, 
         a.n_slot_of = (unsigned long long)tab;
         a.out = &ctx->mb_dev->out;
         a.done_ns = ctx->in_batch ? ctx->done_dev : nullptr;
+        s = full_refit_tree(ctx, B, a);
+        if (s != GD_OK) return s;
         int grid = grid_blocks(ctx, kind);
         a.work_ctas = single_work_ctas(ctx, grid);
         a.fuse_root = single_fuse_root(ctx, B);
@@ -539,6 +569,7 @@ GD_API void gd_ctx_destroy(gd_ctx* c) {
     cudaFree(c->qs); cudaFree(c->qin_dev); cudaFree(c->out_dev); cudaFree(c->done_dev);
     cudaFreeHost(c->qin_host); cudaFreeHost(c->out_host); cudaFreeHost(c->done_host);
     cudaFree(c->slot_of);
+    cudaFree(c->ftree);
     cudaFree(c->naive_ws);
     cudaFree(c->point_ws); cudaFree(c->pts_dev); cudaFree(c->pres_dev);
     cudaFree(c->pkeys[0]); cudaFree(c->pkeys[1]); cudaFree(c->pvals[0]); cudaFree(c->pvals[1]);
@@ -562,7 +593,7 @@ GD_API gd_status gd_ctx_set_tunables(gd_ctx* c, const gd_tunables* t) {
     if (t->cand_capacity > 0) { c->tun.cand_capacity = t->cand_capacity; realloc = true; }
     if (t->max_capacity > 0) c->tun.max_capacity = t->max_capacity;
     if (t->timeout_ns > 0) c->tun.timeout_ns = t->timeout_ns;
-    if (t->refit_mode == 1 || t->refit_mode == 2) c->tun.refit_mode = t->refit_mode;
+    if (t->refit_mode >= 1 && t->refit_mode <= 3) c->tun.refit_mode = t->refit_mode;
     if (t->refit_slots > 0) { c->tun.refit_slots = t->refit_slots; realloc = true; }
     if (t->probes > 0) c->tun.probes = t->probes;
     if (t->batch_budget > 0) c->tun.batch_budget = t->batch_budget;
@@ -1019,6 +1050,8 @@ GD_API gd_status gd_query_device(gd_ctx* ctx, const gd_mesh* A, const gd_mesh* B
     a.slot_of = ctx->slot_of;
     a.n_slot_of = (unsigned long long)tab;
     a.out = d_out;
+    s = full_refit_tree(ctx, B, a);
+    if (s != GD_OK) return s;
     cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
     int grid = grid_blocks(ctx, (int)kind);
     a.work_ctas = single_work_ctas(ctx, grid);
@@ -1058,6 +1091,8 @@ gd_status graph_build(gd_graph* g) {
     a.slot_of = ctx->slot_of;
     a.n_slot_of = (unsigned long long)tab;
     a.out = g->d_out;
+    s = full_refit_tree(ctx, g->B, a);
+    if (s != GD_OK) return s;
     const int grid = grid_blocks(ctx, (int)g->kind);
     a.work_ctas = single_work_ctas(ctx, grid);
     a.fuse_root = single_fuse_root(ctx, g->B);
@@ -1198,10 +1233,99 @@ GD_API gd_status gd_batch_query(gd_ctx* ctx, const gd_query* q, int64_t n, gd_re
 // ---- hooks for the serving loop (gd_serve.cu)
 namespace gd {
 
-gd_status serve_launch_batch(gd_ctx* ctx, SlotBuffers& sb, const gd_query* qs, long long m, int kind, int grid) {
+gd_status serve_prepare(gd_ctx* ctx, long long m) {
+    cudaSetDevice(ctx->device);
+    gd_status s = ensure_ws(ctx, m);
+    if (s != GD_OK) return s;
+    return ensure_table(ctx, 1 << 16);
+}
+
+gd_status serve_single(gd_ctx* ctx, const gd_query& q, gd_result* out) {
+    return run_single(ctx, q.a, q.b, (int)q.kind, q.xa, q.xb, out, false);
+}
+
+// The server's pipelined single queries: launch one on ctx's stream with its
+// result record in pinned slot 1 + slot (stream order keeps launches from
+// overlapping, so they share the work buffers), and later collect it.  A
+// query that overflowed the buffers, or whose record is missing, is run
+// again synchronously (the buffers grow there).
+gd_status serve_single_launch(gd_ctx* ctx, const gd_query& q, int slot, unsigned long long* seq) {
+    const gd_mesh* A = q.a;
+    const gd_mesh* B = q.b;
+    const int kind = (int)q.kind;
+    if (!A || !B || !A->built || !B->built || A->ctx->device != ctx->device)
+        return fail(ctx, GD_ERR_INVALID_ARG, "meshes not built on this device");
+    gd_status s = ensure_ws(ctx, 1);
+    if (s != GD_OK) return s;
+    const long long tab = table_entries(ctx, B);
+    s = ensure_table(ctx, tab);
+    if (s != GD_OK) return s;
+    KArgs a{};
+    a.nq = 1;
+    a.mA = A->d_desc;
+    a.mB = B->d_desc;
+    std::memcpy(a.xa_val, q.xa, sizeof(a.xa_val));
+    std::memcpy(a.xb_val, q.xb, sizeof(a.xb_val));
+    fill_common(ctx, a, ctx->mb_dev->ctr, &ctx->mb_dev->stats);
+    a.slot_of = ctx->slot_of;
+    a.n_slot_of = (unsigned long long)tab;
+    a.out = &ctx->mb_dev->out;
+    s = full_refit_tree(ctx, B, a);
+    if (s != GD_OK) return s;
+    const int grid = grid_blocks(ctx, kind);
+    a.work_ctas = single_work_ctas(ctx, grid);
+    a.fuse_root = single_fuse_root(ctx, B);
+    *seq = ++ctx->hd_seq;
+    a.host_done = ctx->hd + 1 + slot;
+    a.seq = *seq;
+    GD_CUDA(ctx, launch_query(kind, a, grid, ctx->stream));
+    ctx->stats_pending = true;
+    ctx->last_grid = grid;
+    ctx->pending_retries = 0;
+    return GD_OK;
+}
+
+bool serve_single_ready(gd_ctx* ctx, int slot, unsigned long long seq) {
+    return *(const volatile unsigned long long*)&ctx->hd[1 + slot].seq == seq;
+}
+
+gd_status serve_single_finish(gd_ctx* ctx, const gd_query& q, int slot, unsigned long long seq, gd_result* out) {
+    HostDone* h = ctx->hd + 1 + slot;
+    const volatile unsigned long long* stamp = &h->seq;
+    bool got = false;
+    for (unsigned spin = 1;; ++spin) {
+        if (*stamp == seq) { got = true; break; }
+        if ((spin & 4095u) == 0u) {
+            const cudaError_t e = cudaStreamQuery(ctx->stream);
+            if (e == cudaSuccess) { got = *stamp == seq; break; }
+            if (e != cudaErrorNotReady) return cuda_fail(ctx, e, "serving launch");
+        }
+    }
+    std::atomic_thread_fence(std::memory_order_acquire);
+    if (!got) return fail(ctx, GD_ERR_CUDA, "serving launch ended without its result record");
+    if (h->last_abort) return fail(ctx, GD_ERR_TIMEOUT, "a device-side wait timed out");
+    if (h->bad_index)
+        return fail(ctx, GD_ERR_CUDA, "internal index check failed (sites " + std::to_string(h->bad_index) + ")");
+    gd_result r;
+    std::memcpy(&r, (const void*)&h->out, sizeof(r));
+    if (r.status == GD_ERR_OVERFLOW) return serve_single(ctx, q, out);
+    *out = r;
+    return r.status == GD_OK ? GD_OK : (gd_status)r.status;
+}
+
+// One launch of m queries of one kind on ctx's own buffers, for the server:
+// the kernel reads the queries from pinned host memory, and its last CTA
+// copies the m result records and its abort and index-check words to pinned
+// memory and stamps them, so the host neither copies nor synchronises the
+// stream on the way (a lost stamp falls back to the stream's status).
+// Queries that outgrew their share of the queues come back with status
+// GD_ERR_OVERFLOW; the caller reruns them alone.
+gd_status serve_batch(gd_ctx* ctx, const gd_query* qs, long long m, int kind, gd_result* out) {
+    gd_status s = ensure_ws(ctx, m);
+    if (s != GD_OK) return s;
     long long tab = 0;
     for (long long j = 0; j < m; ++j) {
-        QIn& in = sb.qin_host[j];
+        QIn& in = ctx->qin_host[j];
         in.A = qs[j].a->d_desc;
         in.B = qs[j].b->d_desc;
         std::memcpy(in.xa, qs[j].xa, sizeof(in.xa));
@@ -1209,47 +1333,44 @@ gd_status serve_launch_batch(gd_ctx* ctx, SlotBuffers& sb, const gd_query* qs, l
         in.slot_base = (unsigned)tab;
         tab += table_entries(ctx, qs[j].b);
     }
-    // without room for the refit tables this batch bounds B's local boxes only
-    const bool refit = ctx->tun.refit_mode != 2 && tab <= sb.cap_table;
-    GD_CUDA(ctx, cudaMemcpyAsync(sb.qin_dev, sb.qin_host, sizeof(QIn) * m, cudaMemcpyHostToDevice, sb.stream));
+    if (tab > 0xfffffff0ll) return fail(ctx, GD_ERR_INVALID_ARG, "batch too large for the refit tables");
+    s = ensure_table(ctx, tab);
+    if (s != GD_OK) return s;
     KArgs a{};
     a.nq = (int)m;
-    a.qin = sb.qin_dev;
-    a.qs = sb.qs;
-    a.front0 = sb.front[0];
-    a.front1 = sb.front[1];
-    a.cap_front = (unsigned)sb.cap_front;
-    a.leafq = sb.leafq;
-    a.cap_leaf = (unsigned)sb.cap_leaf;
-    a.cand = sb.cand;
-    a.cand_d = sb.cand_d;
-    a.cand_pts = sb.cand_pts;
-    a.cap_cand = (unsigned)sb.cap_cand;
-    a.ctr = sb.mb_dev_ctr;
-    a.stats = sb.stats_dev;
-    a.work_target = ctx->tun.work_target;
-    a.k_max = ctx->tun.k_max;
-    a.timeout_ns = ctx->tun.timeout_ns;
-    a.out = sb.out_dev;
-    a.rbox = sb.rbox;
-    a.jobs = sb.jobs;
-    a.cap_slots = (unsigned)sb.cap_slots;
-    a.slot_of = sb.slot_of;
-    a.refit = refit ? 1 : 0;
-    a.conventional = ctx->tun.bounds_mode == 2 ? 1 : 0;
-    a.probes = ctx->tun.probes;
-    a.n_slot_of = refit ? (unsigned long long)tab : 0ull;
-    batch_limits(sb.cap_front, sb.cap_leaf, m, &a.q_budget, &a.q_pool);
+    a.qin = ctx->qin_host;  // pinned: read by the kernel's setup
+    fill_common(ctx, a, ctx->mb_dev->ctr, &ctx->mb_dev->stats);
+    a.slot_of = ctx->slot_of;
+    a.n_slot_of = (unsigned long long)tab;
+    a.out = ctx->out_dev;
+    batch_limits(ctx->cap_front, ctx->cap_leaf, m, &a.q_budget, &a.q_pool);
+    const unsigned long long seq = ++ctx->hd_seq;
+    a.host_done = ctx->hd;
+    a.host_out = ctx->out_host;
+    a.seq = seq;
+    const int grid = grid_blocks(ctx, kind);
     a.work_ctas = m == 1 ? single_work_ctas(ctx, grid) : (unsigned)grid;
-    GD_CUDA(ctx, launch_query(kind, a, grid, sb.stream));
-    GD_CUDA(ctx, cudaMemcpyAsync(sb.out_host, sb.out_dev, sizeof(gd_result) * m, cudaMemcpyDeviceToHost, sb.stream));
-    GD_CUDA(ctx, cudaMemcpyAsync(sb.ctr_host, sb.mb_dev_ctr, sizeof(unsigned) * kCtrWords, cudaMemcpyDeviceToHost,
-                                 sb.stream));
+    GD_CUDA(ctx, launch_query(kind, a, grid, ctx->stream));
+    const volatile unsigned long long* stamp = &ctx->hd->seq;
+    bool got = false;
+    for (unsigned spin = 1;; ++spin) {
+        if (*stamp == seq) { got = true; break; }
+        if ((spin & 4095u) == 0u) {
+            const cudaError_t q = cudaStreamQuery(ctx->stream);
+            if (q == cudaSuccess) { got = *stamp == seq; break; }
+            if (q != cudaErrorNotReady) return cuda_fail(ctx, q, "serving batch launch");
+        }
+    }
+    std::atomic_thread_fence(std::memory_order_acquire);
+    ctx->stats_pending = true;
+    ctx->last_grid = grid;
+    ctx->pending_retries = 0;
+    if (!got) return fail(ctx, GD_ERR_CUDA, "serving batch ended without its result records");
+    if (ctx->hd->last_abort) return fail(ctx, GD_ERR_TIMEOUT, "a device-side wait timed out");
+    if (ctx->hd->bad_index)
+        return fail(ctx, GD_ERR_CUDA, "internal index check failed (sites " + std::to_string(ctx->hd->bad_index) + ")");
+    std::memcpy(out, (const void*)ctx->out_host, sizeof(gd_result) * (size_t)m);
     return GD_OK;
-}
-
-gd_status serve_single(gd_ctx* ctx, const gd_query& q, gd_result* out) {
-    return run_single(ctx, q.a, q.b, (int)q.kind, q.xa, q.xb, out);
 }
 
 int serve_device(gd_ctx* ctx) { return ctx->device; }

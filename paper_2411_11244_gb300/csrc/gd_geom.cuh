@@ -123,6 +123,38 @@ __device__ __forceinline__ V3<T> closest_on_triangle(V3<T> p, V3<T> a, V3<T> b, 
     return q;
 }
 
+// Projection of p onto the plane of triangle (a, b, c) when it falls inside
+// the closed triangle (*inside), else nothing (p is returned).  The
+// barycentric numerators and the determinant are dot products with the
+// normal n = (b - a) x (c - a): u = ((p - a) x (c - a)).n, v = ((b - a) x
+// (p - a)).n, det = n.n, which stay accurate for needle triangles where the
+// Gram form g00 g11 - g01^2 cancels to nothing.  A feature pair whose
+// projection falls outside needs no boundary fallback: the closest point is
+// then on an edge of the triangle, at a distance no smaller than the
+// edge-edge feature pair of that edge and an edge through p, which the
+// triangle-pair distance takes anyway.
+template <class T>
+__device__ __forceinline__ V3<T> project_into_triangle(V3<T> p, V3<T> a, V3<T> b, V3<T> c, bool* inside) {
+    const V3<T> e0 = b - a, e1 = c - a, w = p - a;
+    const V3<T> n = cross(e0, e1);
+    const T det = dot(n, n);
+    const T un = dot(cross(w, e1), n), vn = dot(cross(e0, w), n);
+    *inside = det > T(0) && un >= T(0) && vn >= T(0) && sadd(un, vn) <= det;
+    if (!*inside) return p;
+    return a + e0 * sdiv(un, det) + e1 * sdiv(vn, det);
+}
+
+// Whether the projection of p onto the plane of (a, b, c) falls inside the
+// closed triangle (the test of project_into_triangle, without the point).
+template <class T>
+__device__ __forceinline__ bool projects_into_triangle(V3<T> p, V3<T> a, V3<T> b, V3<T> c) {
+    const V3<T> e0 = b - a, e1 = c - a, w = p - a;
+    const V3<T> n = cross(e0, e1);
+    const T det = dot(n, n);
+    const T un = dot(cross(w, e1), n), vn = dot(cross(e0, w), n);
+    return det > T(0) && un >= T(0) && vn >= T(0) && sadd(un, vn) <= det;
+}
+
 // Closest points between segments p0 + s d1 and q0 + t d2, s, t in [0, 1].
 // The squared distance is a convex quadratic in (s, t): take the stationary
 // s (0 for parallel segments), clamp it, put t at its optimum for that s,
@@ -260,11 +292,16 @@ __device__ __forceinline__ V3<T> pick3(const V3<T>* X, int i) {
     return r;
 }
 
-// One of the 21 feature pairs of tri_tri_min, for a warp that spreads them
-// over its lanes: f in [0, 9) edge-edge, [9, 12) vertex of A vs B,
-// [12, 15) vertex of B vs A, [15, 18) edge of A crossing B's plane,
-// [18, 21) edge of B crossing A's plane.  Lanes without a feature (or whose
-// edge does not cross the plane) report an infinite distance.
+// One of the 21 feature pairs of the triangle-pair distance, for a warp that
+// spreads them over its lanes: f in [0, 9) edge-edge, [9, 12) vertex of A
+// vs B, [12, 15) vertex of B vs A, [15, 18) edge of A crossing B's plane,
+// [18, 21) edge of B crossing A's plane.  A vertex-face pair counts only
+// when the vertex projects inside the face, and a plane crossing only when it
+// lies inside the face (then the triangles intersect: a hit); otherwise the
+// closest pair of that feature is on an edge of the face, and the edge-edge
+// pairs already hold a pair at most as far (see project_into_triangle).
+// Lanes without a feature report an infinite distance.  The minimum over the
+// 21 is the triangle-pair distance.
 template <class T>
 __device__ __forceinline__ void tri_feature(int f, const V3<T>* A, const V3<T>* B, V3<T>* P, V3<T>* Q, T* d2,
                                             bool* hit) {
@@ -282,7 +319,8 @@ __device__ __forceinline__ void tri_feature(int f, const V3<T>* A, const V3<T>* 
         const int i = f - (va ? 9 : 12);
         const V3<T> v = va ? pick3(A, i) : pick3(B, i);
         const V3<T> t0 = va ? B[0] : A[0], t1 = va ? B[1] : A[1], t2 = va ? B[2] : A[2];
-        const V3<T> c = closest_on_triangle(v, t0, t1, t2, &in);
+        const V3<T> c = project_into_triangle(v, t0, t1, t2, &in);
+        have = in;
         *P = va ? v : c;
         *Q = va ? c : v;
     } else if (f < 21) {
@@ -295,10 +333,9 @@ __device__ __forceinline__ void tri_feature(int f, const V3<T>* A, const V3<T>* 
         T si = dot(n, e0 - f0), sj = dot(n, e1 - f0);
         have = ((si <= T(0) && sj >= T(0)) || (si >= T(0) && sj <= T(0))) && ssub(si, sj) != T(0);
         if (have) {
-            V3<T> X = e0 + (e1 - e0) * clamp01(sdiv(si, ssub(si, sj)));
-            V3<T> Y = closest_on_triangle(X, f0, f1, f2, &in);
-            if (ea) { *P = X; *Q = Y; } else { *P = Y; *Q = X; }
-            if (in) { *hit = true; *P = X; *Q = X; }
+            const V3<T> X = e0 + (e1 - e0) * clamp01(sdiv(si, ssub(si, sj)));
+            have = projects_into_triangle(X, f0, f1, f2);
+            if (have) { *hit = true; *P = X; *Q = X; }
         }
     } else {
         have = false;

@@ -184,10 +184,16 @@ struct KArgs {
                                 // the root pair (phase 1 and its barrier are skipped)
     unsigned work_ctas;         // CTAs [0, work_ctas) run the traversal and meet at the
                                 // grid barriers; the rest run background probes (0: all)
-    HostDone* host_done;        // single query: copy of the result for the host (or nullptr)
+    HostDone* host_done;        // copy of the result (single query) for the host, the launch's
+                                // abort and index-check words, and the sequence stamp (or nullptr)
     unsigned long long seq;     // ... stamped with this sequence number
+    gd_result* host_out;        // with host_done: the nq results copied here (pinned host
+                                // memory) before the stamp (or nullptr)
     unsigned long long* done_ns;// per query of the launch: globaltimer when its result record
                                 // was final (or nullptr)
+    float* ftree;               // single query, full refit (the paper's per-frame refit of
+                                // B): 6 floats per node of B, heap order, B's boxes in A's
+                                // frame, rebuilt at the start of the launch (or nullptr)
 };
 
 // ------------------------------------------------------------------ memory

@@ -115,7 +115,7 @@ extern "C" GD_API gd_status gd_query_device_noalloc(const gd_mesh* A, const gd_m
     // the refit-root table of the array holds 2^16 entries: with refit on, B
     // may have at most 16 + 8 = 24 tree levels (fewer than 2^25 triangles);
     // with refit off the table is not used
-    const bool refit = serve_tunables(ctx).refit_mode != 2;
+    const bool refit = serve_tunables(ctx).refit_mode == 1;
     const int LB = mesh_levels(B);
     const int dR = LB > kRefitH ? LB - kRefitH : 0;
     if (refit && dR > (int)kNaTableBits) return GD_ERR_INVALID_ARG;

@@ -152,6 +152,15 @@ __device__ __forceinline__ void mark_overflow(const KArgs& A, unsigned q) {
     atomicOr(A.ctr + kCtrOverflow, 1u);
 }
 
+// The launch arguments seen with the launch's mode as a compile-time
+// constant (same layout as KArgs): kOne for a launch of one query.  The
+// phases take the arguments as a deduced template type, so that every
+// single-query / batch branch folds in each kernel instantiation.
+template <bool ONE>
+struct KArgsT : KArgs {
+    static constexpr bool kOne = ONE;
+};
+
 // the constants of one query that the traversal reads
 struct QConst {
     Rigid32 X;
@@ -215,9 +224,10 @@ __device__ __forceinline__ void load_qconst(const QState& s, QConst& V) {
 // first barrier, and no CTA reads them earlier in the launch: plain (L1
 // cached) loads are safe for them.  U, status and the other fields written
 // during the traversal are always read with relaxed GPU-scope loads.
-__device__ __forceinline__ void view(const KArgs& A, unsigned q, QView& V) {
+template <class AT>
+__device__ __forceinline__ void view(const AT& A, unsigned q, QView& V) {
     if (V.q == q) return;
-    if (A.nq == 1) static_cast<QConst&>(V) = cta().v;
+    if (AT::kOne) static_cast<QConst&>(V) = cta().v;
     else load_qconst(A.qs[q], V);
     V.q = q;
 }
@@ -245,19 +255,21 @@ __device__ __forceinline__ void cta_load_query(const KArgs& A) {
 }
 
 // Thread 0's refresh of the CTA state after a barrier.
-__device__ __forceinline__ void cta_refresh(const KArgs& A) {
+template <class AT>
+__device__ __forceinline__ void cta_refresh(const AT& A) {
     CtaState& c = cta();
     unsigned v[kCtrReset];
 #pragma unroll
     for (int i = 0; i < kCtrReset; ++i) v[i] = ld_relaxed(A.ctr + i);
 #pragma unroll
     for (int i = 0; i < kCtrReset; ++i) c.ctr[i] = v[i];
-    if (A.nq == 1) cta_load_query(A);
+    if (AT::kOne) cta_load_query(A);
     c.cnt[0][0] = c.cnt[0][1] = c.cnt[1][0] = c.cnt[1][1] = 0u;
     c.rem = 0u;
 }
 
-__device__ __forceinline__ bool sync(const KArgs& A) {
+template <class AT>
+__device__ __forceinline__ bool sync(const AT& A) {
     return grid_sync(A, [&] { cta_refresh(A); });
 }
 
@@ -272,8 +284,9 @@ __device__ __forceinline__ float load_U(const QState& s, bool* stop) {
 
 // The same for query q of this launch: a single-query launch reads the CTA's
 // copy (the bound at the last barrier, lowered by this CTA since).
-__device__ __forceinline__ float load_Uq(const KArgs& A, unsigned q, bool* stop) {
-    if (A.nq == 1) {
+template <class AT>
+__device__ __forceinline__ float load_Uq(const AT& A, unsigned q, bool* stop) {
+    if (AT::kOne) {
         const volatile CtaState& c = cta();
         *stop = (c.stat & kStatStop) != 0u;
         return __uint_as_float(c.U);
@@ -285,9 +298,9 @@ __device__ __forceinline__ float load_Uq(const KArgs& A, unsigned q, bool* stop)
 // All lanes of the warp call this; lanes with have == false pass nothing.  A
 // single-query launch lowers the CTA's copy first and sends the global atomic
 // only for a warp value that beats it.
-template <int KIND>
-__device__ __forceinline__ void warp_bound_update(const KArgs& A, bool have, unsigned q, unsigned v) {
-    if (A.nq == 1) {
+template <int KIND, class AT>
+__device__ __forceinline__ void warp_bound_update(const AT& A, bool have, unsigned q, unsigned v) {
+    if (AT::kOne) {
         const unsigned r = KIND == 0 ? __reduce_min_sync(kFull, have ? v : 0xffffffffu)
                                      : __reduce_max_sync(kFull, have ? v : 0u);
         if ((threadIdx.x & 31) == 0) {
@@ -486,11 +499,11 @@ __device__ __forceinline__ void tri_pair_bounds(const QView& V, unsigned ta, uns
 // leaves more than ~u times the pair's local extent (plus E_df) of error.
 // Used for pairs that pass the float32 test, so that only near-ties reach the
 // float64 refinement; it stays on the float32 pipe (float64 is slow here).
-template <int KIND>
-__device__ __forceinline__ void tri_pair_bounds_tight(const KArgs& A, unsigned q, const QView& V, const Tri32& TA,
+template <int KIND, class AT>
+__device__ __forceinline__ void tri_pair_bounds_tight(const AT& A, unsigned q, const QView& V, const Tri32& TA,
                                                       const Tri32& TB, float* lo, float* up) {
     float Rl[9], tl[3], Edf;
-    if (A.nq == 1) {
+    if (AT::kOne) {
         const CtaState& c = cta();
 #pragma unroll
         for (int i = 0; i < 9; ++i) Rl[i] = c.Rl[i];
@@ -537,7 +550,7 @@ __device__ __forceinline__ void tri_pair_bounds_tight(const KArgs& A, unsigned q
 // thin shapes have boxes far larger than themselves, so most leaf pairs that
 // pass the box test fail this one at a tenth of the cost of the tight bounds.
 template <int KIND>
-__device__ __forceinline__ bool tri_pair_may_hold(const QView& V, const Tri32& TA, const Tri32& TB, float U) {
+__device__ __forceinline__ bool tri_pair_may_hold(const QConst& V, const Tri32& TA, const Tri32& TB, float U) {
     const V3<float> o = TA.v[0];
     V3<float> Al[3], Bl[3];
     float X = 0.f;
@@ -581,16 +594,17 @@ __device__ __forceinline__ bool tri_pair_may_hold(const QView& V, const Tri32& T
 // bound of the max) and whether the pair survives against Ucur; for a
 // survivor, *newU is its enhanced bound (Eq. 10 / Eq. 11) for the running
 // bound and *key orders survivors by it.
-template <int KIND>
+template <int KIND, bool FULL = false>
 __device__ __forceinline__ float pair_bounds(const KArgs& A, const QView& V, unsigned ia, unsigned ib, int db,
                                              float Ucur, bool* survive, unsigned* newU, unsigned* key) {
     Box ba = load_box(V.boxA, ia);
-    const unsigned slot = refit_slot(A, V, ib, db);
+    // FULL: B's whole tree was refit into A's frame at the start of the launch
+    const unsigned slot = FULL ? 0u : refit_slot(A, V, ib, db);
     float bound;
     *key = 0xffffffffu;
     if (slot != kNoSlot) {
         // B's box already in A's frame (refit): plain AABB-AABB bounds
-        Box bb = load_box_cg(A.rbox, refit_index(V, slot, ib, db));
+        Box bb = FULL ? load_box_cg(A.ftree, ib) : load_box_cg(A.rbox, refit_index(V, slot, ib, db));
         if (KIND == 0) {
             bound = lower_min_sq(ba, bb.lo, bb.hi);
             *survive = bound <= min_keep_threshold(Ucur, V.E_box);
@@ -635,14 +649,23 @@ __device__ __forceinline__ float pair_bounds(const KArgs& A, const QView& V, uns
 
 // ------------------------------------------------------------- refit
 
+// One shared-memory buffer for the refit of a subtree (lazy or full) and the
+// full refit's upper levels: one declaration, so the three uses do not each
+// add 12 KB of static shared memory to the CTA (2 CTAs per SM must fit).
+__device__ __forceinline__ float* refit_smem() {
+    __shared__ float sb[kRefitBoxes * 6];
+    return sb;
+}
+
 // Refit the B subtree below root (depth dR, 2^h leaves, h <= kRefitH) into
 // A's frame: one thread per leaf maps its one or two triangles with the
 // query's float32 map, the CTA reduces the h levels in shared memory, and the
 // 2^(h+1) - 1 boxes go to the slot in heap order (local root 1).  Every box is
 // the exact bound of float32-mapped vertices, each within e_c of its exact
 // image, so the widening E_box keeps every bound on it valid.
-__device__ void refit_subtree(const KArgs& A, unsigned q, unsigned root, unsigned slot) {
-    __shared__ float sb[kRefitBoxes * 6];
+template <class AT>
+__device__ void refit_subtree(const AT& A, unsigned q, unsigned root, unsigned slot) {
+    float* sb = refit_smem();
     QView V;
     view(A, q, V);
     const int h = V.LB - V.dR;
@@ -683,6 +706,81 @@ __device__ void refit_subtree(const KArgs& A, unsigned q, unsigned root, unsigne
     }
 }
 
+// Full refit of B into A's frame (refit mode 3: the paper refits B's tree for
+// every frame of a rigid motion, Section 8).  Pass 1: CTA job j refits the
+// subtree of 2^h leaves below node 2^dF + j exactly as refit_subtree does
+// (float32-mapped vertices, exact bounds, h levels reduced in shared memory)
+// and writes its boxes at their heap positions of A.ftree.  Pass 2 (after a
+// grid barrier): the levels above, 8 at a time, one CTA per 2^8 nodes.
+__device__ void full_refit_leaves(const KArgs& A, const QConst& V, unsigned root, int h) {
+    float* sb = refit_smem();
+    const unsigned nleaf = 1u << h;
+    for (unsigned i = threadIdx.x; i < nleaf; i += blockDim.x) {
+        const unsigned leaf = ((root << h) | i) - (1u << V.LB);
+        const unsigned t0 = leaf_first(V.TB, V.LB, leaf), t1 = leaf_first(V.TB, V.LB, leaf + 1);
+        float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+        for (unsigned t = t0; t < t1; ++t) {
+            const Tri32 T = load_tri(V.triB, t);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const V3<float> p = map32(V.X, T.v[k].x, T.v[k].y, T.v[k].z);
+                lo[0] = fminf(lo[0], p.x); lo[1] = fminf(lo[1], p.y); lo[2] = fminf(lo[2], p.z);
+                hi[0] = fmaxf(hi[0], p.x); hi[1] = fmaxf(hi[1], p.y); hi[2] = fmaxf(hi[2], p.z);
+            }
+        }
+        float* o = sb + 6 * (nleaf + i);
+        o[0] = lo[0]; o[1] = lo[1]; o[2] = lo[2]; o[3] = hi[0]; o[4] = hi[1]; o[5] = hi[2];
+    }
+    __syncthreads();
+    for (int lev = h - 1; lev >= 0; --lev) {
+        for (unsigned j = threadIdx.x; j < (1u << lev); j += blockDim.x) {
+            const unsigned k = (1u << lev) + j;
+            const float* l = sb + 12 * k;
+            float* o = sb + 6 * k;
+            o[0] = fminf(l[0], l[6]); o[1] = fminf(l[1], l[7]); o[2] = fminf(l[2], l[8]);
+            o[3] = fmaxf(l[3], l[9]); o[4] = fmaxf(l[4], l[10]); o[5] = fmaxf(l[5], l[11]);
+        }
+        __syncthreads();
+    }
+    // local node k (level rel = depth of k) is node (root << rel) | (k - 2^rel)
+    for (unsigned k = 1 + threadIdx.x; k < (2u << h); k += blockDim.x) {
+        const int rel = 31 - __clz(k);
+        const unsigned long long node = ((unsigned long long)root << rel) | (k - (1u << rel));
+        float* dst = A.ftree + 6ull * node;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) __stcg(dst + c, sb[6 * k + c]);
+    }
+    __syncthreads();
+}
+
+// lv levels above depth d for the 2^lv nodes of depth d from first: their
+// parents up to depth d - lv, reduced in shared memory
+__device__ void full_refit_up(const KArgs& A, unsigned long long first, int lv) {
+    float* sb = refit_smem();
+    const unsigned n = 1u << lv;
+    for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
+        const float* b = A.ftree + 6ull * (first + i);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) sb[6 * (n + i) + c] = __ldcg(b + c);
+    }
+    __syncthreads();
+    for (int lev = lv - 1; lev >= 0; --lev) {
+        for (unsigned j = threadIdx.x; j < (1u << lev); j += blockDim.x) {
+            const unsigned k = (1u << lev) + j;
+            const float* l = sb + 12 * k;
+            float* o = sb + 6 * k;
+            o[0] = fminf(l[0], l[6]); o[1] = fminf(l[1], l[7]); o[2] = fminf(l[2], l[8]);
+            o[3] = fmaxf(l[3], l[9]); o[4] = fmaxf(l[4], l[10]); o[5] = fmaxf(l[5], l[11]);
+            const int rel = lev;
+            const unsigned long long node = ((first >> lv) << rel) | j;
+            float* dst = A.ftree + 6ull * node;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) __stcg(dst + c, o[c]);
+        }
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------- probes
 
 // One compiled copy (not inlined): every caller (the refinement's grid and
@@ -695,9 +793,9 @@ __device__ __noinline__ double refine_pair_warp(const QState& s, unsigned ta, un
 template <int KIND>
 __device__ __noinline__ double refine_pair_cta(const QState& s, unsigned ta, unsigned tb, V3<double>* P,
                                                V3<double>* Q, int* ida, int* idb);
-template <int KIND>
-__device__ __noinline__ void leaf_tight(const KArgs& A, const uint4* list, unsigned n, int& pit, QView& V,
-                                        unsigned& tripairs, unsigned long long& bytes, bool dry);
+template <int KIND, class AT>
+__device__ __noinline__ void leaf_tight(const AT& A, const uint4* list, unsigned n, int& pit, unsigned& tripairs,
+                                        unsigned long long& bytes, bool dry);
 
 // Proof of D_min = 0 (min kind), run by a whole warp on one pair (ta, tb) of
 // query q whose float32 lower bound is 0: the float64 distance of the pair,
@@ -706,7 +804,8 @@ __device__ __noinline__ void leaf_tight(const KArgs& A, const uint4* list, unsig
 // enters the candidates with bound -1, the only mark the refinement keeps once
 // kStatZero is set.  A query starts at most kCertMax checks per launch, so
 // touching but disjoint pairs cannot make the proof attempts dominate.
-__device__ __noinline__ void certify_zero(const KArgs& A, unsigned q, unsigned ta, unsigned tb) {
+template <class AT>
+__device__ __noinline__ void certify_zero(const AT& A, unsigned q, unsigned ta, unsigned tb) {
     QState& s = A.qs[q];
     const int lane = threadIdx.x & 31;
     unsigned go = 0;
@@ -716,7 +815,7 @@ __device__ __noinline__ void certify_zero(const KArgs& A, unsigned q, unsigned t
     int ia, ib;
     const double d = refine_pair_warp<0>(s, ta, tb, &P, &Q, &ia, &ib);
     if (d == 0.0 && lane == 0) {
-        if (A.nq == 1) atomicOr(&cta().stat, kStatZero);
+        if (AT::kOne) atomicOr(&cta().stat, kStatZero);
         if (!(atomicOr(&s.status, kStatZero) & kStatZero)) {
             unsigned i = atomicAdd(A.ctr + kCtrCand, 1u);
             if (i < A.cap_cand) A.cand[i] = Cand{ta, tb, -1.f, q};
@@ -734,8 +833,8 @@ __device__ __noinline__ void certify_zero(const KArgs& A, unsigned q, unsigned t
 // the traversal's result does not depend on them.  They exist to reach a
 // near-final bound before the breadth-first levels widen (the sequential
 // depth-first behaviour Section 6 contrasts with).
-template <int KIND>
-__device__ void probe(const KArgs& A, Item it, const QView& V) {
+template <int KIND, class AT>
+__device__ void probe(const AT& A, Item it, const QView& V) {
     const int lane = threadIdx.x & 31;
     unsigned a = it.a, b = it.b;
     const unsigned q = it.q;
@@ -784,8 +883,8 @@ __device__ void probe(const KArgs& A, Item it, const QView& V) {
 // descendant pair of rank w mod 32 and then (w / 32) mod 32 among the
 // survivors (ordered by their enhanced bound), so that the walks of different
 // warps start in different subtree pairs; then it walks greedily as probe().
-template <int KIND>
-__device__ void probe_root(const KArgs& A, unsigned w, const QView& V) {
+template <int KIND, class AT>
+__device__ void probe_root(const AT& A, unsigned w, const QView& V) {
     const int lane = threadIdx.x & 31;
     unsigned a = 1u, b = 1u;
     for (int step = 0; step < 2; ++step) {
@@ -828,8 +927,8 @@ __device__ void probe_root(const KArgs& A, unsigned w, const QView& V) {
 // the global running bound (and may prove D_min = 0), which the traversal
 // reads at its next barrier.  The probes do not use refit boxes: those are
 // being written while the probes run.
-template <int KIND>
-__device__ void bg_probe_cta(const KArgs& A) {
+template <int KIND, class AT>
+__device__ void bg_probe_cta(const AT& A) {
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
         int ok = 1;
@@ -874,7 +973,7 @@ __device__ void bg_probe_cta(const KArgs& A) {
     int pit = 0;
     unsigned tp = 0;
     unsigned long long by = 0;
-    leaf_tight<KIND>(A, dry_list, 1u, pit, V, tp, by, true);
+    leaf_tight<KIND>(A, dry_list, 1u, pit, tp, by, true);
     V3<double> P, Q;
     int ia, ib;
     const double d = refine_pair_cta<KIND>(A.qs[0], 0u, 0u, &P, &Q, &ia, &ib);
@@ -1046,8 +1145,8 @@ __device__ __forceinline__ int adaptive_k(unsigned n, long long C, int kmax) {
     return k;
 }
 
-template <int KIND>
-__device__ void expand_level(const KArgs& A, int level, unsigned n, int s, unsigned long long& pairs,
+template <int KIND, bool FULL, class AT>
+__device__ void expand_level(const AT& A, int level, unsigned n, int s, unsigned long long& pairs,
                              unsigned long long& bytes) {
     const Item* in = (level & 1) ? A.front1 : A.front0;
     Item* out = (level & 1) ? A.front0 : A.front1;
@@ -1107,7 +1206,7 @@ __device__ void expand_level(const KArgs& A, int level, unsigned n, int s, unsig
         unsigned newU = KIND == 0 ? 0xffffffffu : 0u, key;
         if (valid) {
             ++pairs;
-            bound = pair_bounds<KIND>(A, V, ia, ib, dBc, Ucur, &survive, &newU, &key);
+            bound = pair_bounds<KIND, FULL>(A, V, ia, ib, dBc, Ucur, &survive, &newU, &key);
         }
         warp_bound_update<KIND>(A, survive, q, newU);
         if (A.q_budget) {
@@ -1170,10 +1269,13 @@ __device__ __forceinline__ void cta_merge_bound(unsigned long long w) {
 // update, candidates, and the D = 0 check of a pair that may touch.  One
 // compiled copy (not inlined), so that a dry run (dry: bounds only, no side
 // effect) by a background CTA early in the launch brings its code into L2
-// before the leaf phase needs it.
-template <int KIND>
-__device__ __noinline__ void leaf_tight(const KArgs& A, const uint4* list, unsigned n, int& pit, QView& V,
-                                        unsigned& tripairs, unsigned long long& bytes, bool dry) {
+// before the leaf phase needs it.  It keeps a query view of its own: a view
+// passed in by reference would live in local memory in the caller, whose
+// slot loop re-fills it for every query change of a batch.
+template <int KIND, class AT>
+__device__ __noinline__ void leaf_tight(const AT& A, const uint4* list, unsigned n, int& pit, unsigned& tripairs,
+                                        unsigned long long& bytes, bool dry) {
+    QView V;
     bool have = false, emit = false;
     float cb = 0.f;
     unsigned newU = KIND == 0 ? 0xffffffffu : 0u;
@@ -1234,21 +1336,24 @@ __device__ __noinline__ void leaf_tight(const KArgs& A, const uint4* list, unsig
 // end) every thread takes one listed pair for the tight bounds.  Only a few
 // per cent of the pairs pass the cheap test, so bounding them densely keeps
 // whole warps on the expensive part instead of one lane in each.
-template <int KIND>
-__device__ void leaf_phase(const KArgs& A, unsigned nleaf, unsigned& tripairs, unsigned long long& bytes) {
+template <int KIND, class AT>
+__device__ void leaf_phase(const AT& A, unsigned nleaf, unsigned& tripairs, unsigned long long& bytes) {
     __shared__ uint4 list[2 * kBlock];
     __shared__ unsigned list_n;
     const unsigned long long total = (unsigned long long)nleaf * 4ull;
     const unsigned long long gstride = (unsigned long long)work_ctas(A) * blockDim.x;
-    const bool pull = A.nq == 1 && threadIdx.x == 0;
+    const bool pull = AT::kOne && threadIdx.x == 0;
     const int lane = threadIdx.x & 31;
-    QView V;
+    // the query's constants: a single query reads the CTA's shared copy where
+    // it uses them (no per-thread copy held through the slot loop); a batch
+    // keeps a per-thread view of the last query it met
+    QView Vb;
     int pit = 0;
     if (threadIdx.x == 0) list_n = 0u;
     for (unsigned long long cbase = (unsigned long long)blockIdx.x * blockDim.x; cbase < total; cbase += gstride) {
         // a single query whose traversal stopped (D = 0 proven) skips the rest
         // (this barrier also publishes list_n)
-        if (__syncthreads_or(A.nq == 1 && (((volatile CtaState&)cta()).stat & kStatStop) != 0u)) break;
+        if (__syncthreads_or(AT::kOne && (((volatile CtaState&)cta()).stat & kStatStop) != 0u)) break;
         // issued now, merged at the end of the iteration (the load's latency
         // hides behind this iteration's work)
         unsigned long long gw = 0;
@@ -1266,7 +1371,8 @@ __device__ void leaf_phase(const KArgs& A, unsigned nleaf, unsigned& tripairs, u
             }
         }
         unsigned q = it.q;
-        view(A, q, V);
+        if (!AT::kOne) view(A, q, Vb);
+        const QConst& V = AT::kOne ? static_cast<const QConst&>(cta().v) : static_cast<const QConst&>(Vb);
         if (valid && (depth_of(it.a) != V.LA || depth_of(it.b) != V.LB)) {
             flag_bad(A, kBadLeaf);
             valid = false;
@@ -1297,7 +1403,7 @@ __device__ void leaf_phase(const KArgs& A, unsigned nleaf, unsigned& tripairs, u
         __syncthreads();
         const unsigned n = list_n;
         if (n >= (unsigned)kBlock) {
-            leaf_tight<KIND>(A, list + (n - kBlock), kBlock, pit, V, tripairs, bytes, false);
+            leaf_tight<KIND>(A, list + (n - kBlock), kBlock, pit, tripairs, bytes, false);
             __syncthreads();
             if (threadIdx.x == 0) list_n = n - kBlock;
         }
@@ -1305,7 +1411,7 @@ __device__ void leaf_phase(const KArgs& A, unsigned nleaf, unsigned& tripairs, u
     }
     __syncthreads();
     const unsigned n = list_n;
-    if (n > 0u) leaf_tight<KIND>(A, list, n, pit, V, tripairs, bytes, false);
+    if (n > 0u) leaf_tight<KIND>(A, list, n, pit, tripairs, bytes, false);
     __syncthreads();
 }
 
@@ -1544,8 +1650,8 @@ __device__ __noinline__ double refine_pair_cta(const QState& s, unsigned ta, uns
 // Every candidate's float64 distance (NaN when not kept) and points are
 // stored, the per-query extreme is raised or lowered, and the refined
 // candidates are listed for the selection.
-template <int KIND>
-__device__ void refine_phase_cta(const KArgs& A, unsigned ncand, unsigned& refined, unsigned long long& bytes) {
+template <int KIND, class AT>
+__device__ void refine_phase_cta(const AT& A, unsigned ncand, unsigned& refined, unsigned long long& bytes) {
     __shared__ unsigned s_list[kBlock];
     __shared__ unsigned s_n;
     const unsigned long long W = work_ctas(A);
@@ -1727,7 +1833,8 @@ __device__ void status_phase(const KArgs& A, unsigned long long first, unsigned 
 // Run the refit jobs appended since the last call (one job per CTA at a time);
 // returns false if the grid barrier after them failed; *ran tells whether
 // there were any.
-__device__ bool refit_jobs(const KArgs& A, bool lead, unsigned& refits, bool* ran) {
+template <class AT>
+__device__ bool refit_jobs(const AT& A, bool lead, unsigned& refits, bool* ran) {
     unsigned jobs = cta().ctr[kCtrJobs], done = cta().ctr[kCtrJobsDone];
     if (jobs > A.cap_slots) jobs = A.cap_slots;
     *ran = jobs > done;
@@ -1754,8 +1861,16 @@ __device__ bool refit_jobs(const KArgs& A, bool lead, unsigned& refits, bool* ra
 
 // ------------------------------------------------------------- kernel
 
-template <int KIND>
-__global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
+// FULL: the single query's B is refit whole into A's frame first (refit mode
+// 3, the paper's per-frame refit); a separate instantiation, so that the
+// default kernel's level loop is compiled without it.  ONE: a launch of one
+// query (nq == 1) or a batch; with the query count known at compile time
+// every single-query / batch branch of the inlined phases folds, so each
+// instantiation carries only its own code and register pressure.
+template <int KIND, bool FULL, bool ONE>
+__global__ void __launch_bounds__(kBlock, 2) k_query(KArgs Aparam) {
+    using AT = KArgsT<ONE>;
+    const AT& A = static_cast<const AT&>(Aparam);
     unsigned long long pairs = 0, bytes = 0;
     unsigned tripairs = 0, refined = 0, refits = 0;
     unsigned leaf_flushed = 0;
@@ -1784,7 +1899,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
         for (int i = threadIdx.x; i < kCtrReset; i += blockDim.x) A.ctr[i] = 0u;
         if (A.fuse_root) __syncthreads();  // cleared before the root is pushed below
     }
-    if (A.nq == 1) {
+    if (AT::kOne) {
         if (gfirst < 32) setup_query_warp(A, KIND);
     } else {
         for (int q = (int)gfirst; q < A.nq; q += (int)gstride) setup_query(A, q, KIND);
@@ -1831,6 +1946,24 @@ __global__ void __launch_bounds__(kBlock, 2) k_query(KArgs A) {
         }
     }
     if (!sync(A)) goto done;
+
+    if (FULL) {
+        // full refit of B into A's frame (single query): subtrees of 2^h
+        // leaves, then the levels above 8 at a time
+        const QConst& V = cta().v;
+        const int h = min(V.LB, kRefitH);
+        const int dF = V.LB - h;
+        for (unsigned j = blockIdx.x; j < (1u << dF); j += W) full_refit_leaves(A, V, (1u << dF) + j, h);
+        if (!sync(A)) goto done;
+        for (int d = dF; d > 0;) {
+            const int lv = min(d, kRefitH);
+            for (unsigned j = blockIdx.x; j < (1u << (d - lv)); j += W)
+                full_refit_up(A, (1ull << d) + ((unsigned long long)j << lv), lv);
+            if (!sync(A)) goto done;
+            d -= lv;
+        }
+        lap(1);
+    }
 
     // phase 1: root pairs
     if (A.fuse_root) goto levels;
@@ -1904,7 +2037,7 @@ levels:
             }
             if (lead) A.stats->probes += P;
             if (!sync(A)) goto done;
-            if (lead && !reprobe) A.stats->u_probe = A.nq == 1 ? __uint_as_float(cta().U) : 0.f;
+            if (lead && !reprobe) A.stats->u_probe = AT::kOne ? __uint_as_float(cta().U) : 0.f;
             lap(2);
         }
         unsigned rmax = cta().ctr[kCtrRem + level % 3];
@@ -1920,13 +2053,13 @@ levels:
                 A.stats->slots[level] = (unsigned)s;
                 // query 0's bound as this CTA knows it (no global round trip
                 // on the lead's way into the level)
-                A.stats->u_level[level] = A.nq == 1 ? __uint_as_float(cta().U) : 0.f;
+                A.stats->u_level[level] = AT::kOne ? __uint_as_float(cta().U) : 0.f;
             }
             A.stats->levels = level + 1;
         }
         if (A.q_budget)  // the counters of this level's pushes are those of level + 2
             for (int q = (int)gfirst; q < A.nq; q += (int)gstride) A.qs[q].pushed[level & 1] = 0u;
-        expand_level<KIND>(A, level, n, s, pairs, bytes);
+        expand_level<KIND, FULL>(A, level, n, s, pairs, bytes);
         if (!sync(A)) goto done;
         if (lead) {
             unsigned long long now = globaltimer();
@@ -1998,7 +2131,7 @@ levels:
                 if (s_go) {
                     lap(6);
                     const RefinedSet R{nullptr, nc};
-                    if (A.nq == 1) {
+                    if (AT::kOne) {
                         select_finalize_single(A, R);
                         lap(7);
                     } else {
@@ -2019,7 +2152,7 @@ levels:
         if (!sync(A)) goto done;
         lap(5);
         const RefinedSet R = refined_set(A, cta().ctr[kCtrRefined], nc);
-        if (A.nq == 1) {
+        if (AT::kOne) {
             // one query: CTA 0 selects and writes the witness alone (the refined
             // candidates are few), no further grid barrier
             if (blockIdx.x == 0) {
@@ -2064,6 +2197,8 @@ done:
             atomicAdd(&s_tri, tripairs);
             atomicAdd(&s_ref, refined);
         }
+        __shared__ unsigned s_last_ab;
+        __shared__ int s_last;
         __syncthreads();
         if (threadIdx.x == 0) {
             const int w = blockIdx.x % kAccWays;
@@ -2075,26 +2210,39 @@ done:
             // next launch and publishes this launch's abort flag
             __threadfence();
             unsigned e = atomicAdd(A.ctr + kCtrExit, 1u);
-            if (e == gridDim.x - 1) {
+            s_last = e == gridDim.x - 1;
+            if (s_last) {
                 unsigned ab = atomicExch(A.ctr + kCtrAbort, 0u);
                 atomicExch(A.ctr + kCtrLastAbort, ab);
                 atomicExch(A.ctr + kCtrBarCount, 0u);
                 atomicExch(A.ctr + kCtrSetupDone, 0u);
                 atomicExch(A.ctr + kCtrExit, 0u);
                 __threadfence();
-                if (A.host_done) {
-                    // every other CTA has left (their writes, the result
-                    // record among them, were fenced before their exit count)
-                    HostDone* h = A.host_done;
-                    static_assert(sizeof(gd_result) % 8 == 0, "result record copied in 8-byte words");
-                    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(A.out);
-                    unsigned long long* dst = reinterpret_cast<unsigned long long*>(&h->out);
-                    for (int k = 0; k < (int)(sizeof(gd_result) / 8); ++k) dst[k] = __ldcg(src + k);
-                    h->last_abort = ab;
-                    h->bad_index = ld_relaxed(A.ctr + kCtrBadIndex);
-                    __threadfence_system();
-                    *reinterpret_cast<volatile unsigned long long*>(&h->seq) = A.seq;
-                }
+                s_last_ab = ab;
+            }
+        }
+        __syncthreads();
+        if (s_last && A.host_done) {
+            // every other CTA has left (their writes, the result records among
+            // them, were fenced before their exit count): the records go to
+            // the host's pinned memory, then the stamp
+            HostDone* h = A.host_done;
+            static_assert(sizeof(gd_result) % 8 == 0, "result record copied in 8-byte words");
+            constexpr int kW = (int)(sizeof(gd_result) / 8);
+            const unsigned long long* src = reinterpret_cast<const unsigned long long*>(A.out);
+            if (A.host_out) {
+                unsigned long long* dst = reinterpret_cast<unsigned long long*>(A.host_out);
+                for (long long k = threadIdx.x; k < (long long)A.nq * kW; k += blockDim.x) dst[k] = __ldcg(src + k);
+            } else if (threadIdx.x < kW) {
+                reinterpret_cast<unsigned long long*>(&h->out)[threadIdx.x] = __ldcg(src + threadIdx.x);
+            }
+            __threadfence_system();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                h->last_abort = s_last_ab;
+                h->bad_index = ld_relaxed(A.ctr + kCtrBadIndex);
+                __threadfence_system();
+                *reinterpret_cast<volatile unsigned long long*>(&h->seq) = A.seq;
             }
         }
     }
@@ -2104,24 +2252,43 @@ done:
 
 // Both kinds get the same shared-memory carveout, so that CTAs of a min and a
 // max launch can share an SM (an SM holds CTAs of one carveout at a time).
+// The instantiations of one kind: batch, single query, single query with the
+// full refit.
+template <int KIND>
+static const void* kind_kernel(int i) {
+    return i == 0 ? (const void*)k_query<KIND, false, false>
+                  : (i == 1 ? (const void*)k_query<KIND, false, true> : (const void*)k_query<KIND, true, true>);
+}
+
 template <int KIND>
 static int occupancy_blocks() {
     static bool configured = false;
     if (!configured) {
-        cudaFuncSetAttribute(k_query<KIND>, cudaFuncAttributePreferredSharedMemoryCarveout, 25);
+        for (int i = 0; i < 3; ++i)
+            cudaFuncSetAttribute(kind_kernel<KIND>(i), cudaFuncAttributePreferredSharedMemoryCarveout, 25);
         configured = true;
     }
-    int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_query<KIND>, kBlock, 0);
+    // the instantiations use the same registers and shared memory per CTA;
+    // the launch takes the smallest occupancy so that every one fits
+    int nb = 1 << 30;
+    for (int i = 0; i < 3; ++i) {
+        int n = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kind_kernel<KIND>(i), kBlock, 0);
+        nb = n < nb ? n : nb;
+    }
     return nb;
 }
 
 int query_max_blocks_per_sm(int kind) { return kind == 0 ? occupancy_blocks<0>() : occupancy_blocks<1>(); }
 
+static const void* query_kernel(int kind, const KArgs& args) {
+    const int i = args.nq != 1 ? 0 : (args.ftree ? 2 : 1);
+    return kind == 0 ? kind_kernel<0>(i) : kind_kernel<1>(i);
+}
+
 cudaError_t launch_query(int kind, const KArgs& args, int grid, cudaStream_t stream) {
     void* params[] = {const_cast<KArgs*>(&args)};
-    const void* fn = kind == 0 ? (const void*)k_query<0> : (const void*)k_query<1>;
-    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), params, 0, stream);
+    return cudaLaunchCooperativeKernel(query_kernel(kind, args), dim3(grid), dim3(kBlock), params, 0, stream);
 }
 
 // A graph with the query kernel as its one cooperative kernel node (the
@@ -2132,7 +2299,7 @@ cudaError_t build_query_graph(int kind, const KArgs& args, int grid, cudaGraphEx
     if (e != cudaSuccess) return e;
     void* params[] = {const_cast<KArgs*>(&args)};
     cudaKernelNodeParams p{};
-    p.func = kind == 0 ? (void*)k_query<0> : (void*)k_query<1>;
+    p.func = const_cast<void*>(query_kernel(kind, args));
     p.gridDim = dim3(grid);
     p.blockDim = dim3(kBlock);
     p.sharedMemBytes = 0;

@@ -1,12 +1,29 @@
-// Continuous-batching server (gd_serve_*): a host thread admits queued
-// requests into free slots (each slot: a stream and its own work buffers),
-// launches one persistent traversal per slot batch, and harvests finished
-// slots while others are still running, so requests that arrive during a
-// launch overlap with it on the device.  Admission is by an HBM footprint
-// estimate against the slot's buffer budget.
+// Continuous-batching server (gd_serve_*).  One execution lane: a host thread
+// takes every queued request of the head request's kind (up to max_batch,
+// within the memory budget) and runs them as one persistent launch on the
+// whole GPU, on a private execution context with buffers sized from the
+// budget; requests that arrive meanwhile are admitted into the next launch
+// as soon as this one ends.  One request alone runs as a single query (the
+// same launch as gd_min_distance / gd_max_distance); a batch's queries are
+// read by the kernel from pinned memory and its results written back there,
+// so neither path copies or synchronises on the way.
+//
+// Only one cooperative grid is ever in flight: CUDA does not promise that
+// cooperative grids launched on different streams are resident together, and
+// a grid whose CTAs wait at a grid barrier for CTAs that cannot be scheduled
+// can only time out.
+//
+// Admission is by HBM footprint: each request holds a predicted number of
+// work-buffer bytes (footprint(), a model of the measured front, leaf-pair
+// and candidate peaks of single queries) from submission until its result is
+// published; a submission that would take the held bytes beyond the budget
+// is refused with GD_ERR_BUSY, and a batch holds at most a budget's worth.
+// A request whose work outgrows its share of the lane's buffers anyway is run
+// again alone, where the buffers grow as far as it needs.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -28,125 +45,90 @@ struct Request {
     long long foot;
 };
 
-struct Slot {
-    SlotBuffers b;
-    bool busy = false;
-    bool whole = false;  // launched on the whole GPU: no other slot starts meanwhile
-    int kind = 0;
-    std::vector<Request> reqs;
-};
-
-// Estimated device bytes of one query: its per-query records plus a front
-// share that grows with the square root of the leaf counts (surface-contact
-// fronts scale with the contact patch, not with the volume of pairs).
+// Predicted work-buffer bytes of one query: 16 B per front entry in each of
+// the two front buffers at the largest level, 16 B per leaf pair, 72 B per
+// float64 candidate (record, distance, witness points), plus 1 KB of
+// per-query records.  The counts are power laws c s^p in s = sqrt(T_A) +
+// sqrt(T_B) (a surface-contact front grows with the contact patch, not with
+// T_A T_B).  Fitted to 800 single queries on the 64-mesh serving pool (random
+// pairs and placements, one in four a max query; largest front, leaf pairs
+// and candidates from gd_stats): p by least squares in log-log, c the 99th
+// percentile of the residuals, so that 99% of those queries lie below each
+// curve (the largest query measured needed 438 MB).
 long long footprint(const gd_query& q) {
-    long long ta = serve_mesh_tris(q.a), tb = serve_mesh_tris(q.b);
-    double s = std::sqrt((double)ta) + std::sqrt((double)tb);
-    return 1024 + (long long)(s * 64.0);
+    const double ta = (double)serve_mesh_tris(q.a), tb = (double)serve_mesh_tris(q.b);
+    const double sq = std::sqrt(ta) + std::sqrt(tb);
+    const double front = 349.0 * std::pow(sq, 1.223);
+    const double leaf = 71.5 * std::pow(sq, 1.514);
+    const double cand = 570.0 * std::pow(sq, 0.642);
+    const double bytes = 16.0 * (2.0 * front + leaf) + 72.0 * cand + 1024.0;
+    return (long long)std::ceil(bytes);
 }
 
 }  // namespace
 
 struct gd_server {
-    gd_ctx* ctx = nullptr;
+    gd_ctx* ctx = nullptr;   // the user's context (validation of submissions)
+    gd_ctx* exec = nullptr;  // private execution context: stream, buffers, pinned records
     gd_serve_opts opts{};
-    std::vector<Slot> slots;
     std::mutex mu;
     std::condition_variable cv;
     std::deque<Request> queue;
+    std::atomic<long long> queued{0};  // queue length, read without the lock by the loop
     std::unordered_map<uint64_t, gd_result> done;
     std::unordered_map<uint64_t, int> pending;
-    long long queued_foot = 0;
-    long long slot_budget = 0;
+    long long held_foot = 0;  // predicted bytes of queued and running requests
     uint64_t next_ticket = 1;
-    int whole_grid = 0;  // co-resident CTAs of the whole GPU
     std::atomic<bool> stop{false};
     std::thread loop;
-    gd_status loop_error = GD_OK;
 };
 
 namespace {
 
-void free_slot(Slot& s) {
-    SlotBuffers& b = s.b;
-    if (b.stream) cudaStreamSynchronize(b.stream);
-    cudaFree(b.front[0]); cudaFree(b.front[1]); cudaFree(b.leafq); cudaFree(b.cand); cudaFree(b.cand_d); cudaFree(b.cand_pts);
-    cudaFree(b.qs); cudaFree(b.qin_dev); cudaFree(b.out_dev); cudaFree(b.mb_dev_ctr); cudaFree(b.stats_dev);
-    cudaFree(b.rbox); cudaFree(b.jobs); cudaFree(b.slot_of);
-    cudaFreeHost(b.qin_host); cudaFreeHost(b.out_host); cudaFreeHost(b.ctr_host);
-    if (b.stream) cudaStreamDestroy(b.stream);
-    b = SlotBuffers{};
-}
-
-bool alloc_slot(Slot& s, long long budget, long long max_batch, int grid) {
-    SlotBuffers& b = s.b;
-    // queue entries (16 B) for two fronts and the leaf queue, plus candidates (24 B)
-    long long per = std::max<long long>(budget / (3 * 16 + 24 / 4), 1 << 16);
-    b.cap_front = std::min<long long>(per, 0xffffffffll);
-    b.cap_leaf = b.cap_front;
-    b.cap_cand = std::max<long long>(b.cap_front / 4, 1 << 14);
-    b.cap_q = max_batch;
-    b.grid = grid;
-    bool ok = cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking) == cudaSuccess;
-    ok = ok && cudaMalloc(&b.front[0], sizeof(Item) * b.cap_front) == cudaSuccess;
-    ok = ok && cudaMalloc(&b.front[1], sizeof(Item) * b.cap_front) == cudaSuccess;
-    ok = ok && cudaMalloc(&b.leafq, sizeof(Item) * b.cap_leaf) == cudaSuccess;
-    ok = ok && cudaMalloc(&b.cand, sizeof(Cand) * b.cap_cand) == cudaSuccess;
-    ok = ok && cudaMalloc(&b.cand_d, sizeof(double) * b.cap_cand) == cudaSuccess;
-    ok = ok && cudaMalloc(&b.cand_pts, sizeof(double) * 6 * b.cap_cand) == cudaSuccess;
-    ok = ok && cudaMalloc(&b.qs, sizeof(QState) * b.cap_q) == cudaSuccess;
-    ok = ok && cudaMalloc(&b.qin_dev, sizeof(QIn) * b.cap_q) == cudaSuccess;
-    ok = ok && cudaMalloc(&b.out_dev, sizeof(gd_result) * b.cap_q) == cudaSuccess;
-    ok = ok && cudaMalloc(&b.mb_dev_ctr, sizeof(unsigned) * kCtrWords) == cudaSuccess;
-    ok = ok && cudaMemset(b.mb_dev_ctr, 0, sizeof(unsigned) * kCtrWords) == cudaSuccess;
-    ok = ok && cudaMalloc(&b.stats_dev, sizeof(StatsDev)) == cudaSuccess;
-    ok = ok && cudaMallocHost(&b.qin_host, sizeof(QIn) * b.cap_q) == cudaSuccess;
-    ok = ok && cudaMallocHost(&b.out_host, sizeof(gd_result) * b.cap_q) == cudaSuccess;
-    ok = ok && cudaMallocHost(&b.ctr_host, sizeof(unsigned) * kCtrWords) == cudaSuccess;
-    // refit slots (12 KB each) and root tables for up to 4096 roots per query
-    b.cap_slots = 2048;
-    b.cap_table = 4096ll * max_batch;
-    ok = ok && cudaMalloc(&b.rbox, sizeof(float) * 6 * kRefitBoxes * (size_t)b.cap_slots) == cudaSuccess;
-    ok = ok && cudaMalloc(&b.jobs, sizeof(uint2) * (size_t)b.cap_slots) == cudaSuccess;
-    ok = ok && cudaMalloc(&b.slot_of, sizeof(unsigned) * (size_t)b.cap_table) == cudaSuccess;
-    return ok;
-}
-
-void harvest(gd_server* S, Slot& s) {
-    std::vector<std::pair<Request, gd_result>> redo;
-    bool aborted = s.b.ctr_host[kCtrLastAbort] != 0;
-    const bool bad = s.b.ctr_host[kCtrBadIndex] != 0;  // an internal index check failed
-    {
-        std::lock_guard<std::mutex> g(S->mu);
-        for (size_t j = 0; j < s.reqs.size(); ++j) {
-            gd_result r = s.b.out_host[j];
-            if (aborted) r.status = GD_ERR_TIMEOUT;
-            if (bad) r.status = GD_ERR_CUDA;
-            // work beyond the slot's buffers, or a slot launch whose bounded
-            // waits gave up: rerun alone below
-            if (r.status == GD_ERR_OVERFLOW || r.status == GD_ERR_TIMEOUT) {
-                redo.push_back({s.reqs[j], r});
-                continue;
-            }
-            S->pending.erase(s.reqs[j].ticket);
-            S->done[s.reqs[j].ticket] = r;
-        }
+// Run one batch (all of one kind) on the lane; results land in res.
+void run_batch(gd_server* S, const std::vector<Request>& take, std::vector<gd_result>& res) {
+    const size_t m = take.size();
+    res.assign(m, gd_result{});
+    if (m == 1) {
+        gd_status st = serve_single(S->exec, take[0].q, &res[0]);
+        if (st != GD_OK) res[0].status = st;
+        return;
     }
-    // rerun alone on the context's own buffers, with the device otherwise idle
-    // (this runs on the serving thread, so no slot is launched meanwhile)
-    if (!redo.empty())
-        for (Slot& o : S->slots)
-            if (o.busy && &o != &s) cudaStreamSynchronize(o.b.stream);
-    for (auto& pr : redo) {
+    std::vector<gd_query> qs(m);
+    for (size_t j = 0; j < m; ++j) qs[j] = take[j].q;
+    gd_status st = serve_batch(S->exec, qs.data(), (long long)m, (int)qs[0].kind, res.data());
+    if (st == GD_ERR_TIMEOUT) {
+        // a bounded device wait gave up: each query runs again alone below
+        for (gd_result& r : res) { r = gd_result{}; r.status = GD_ERR_TIMEOUT; }
+    } else if (st != GD_OK) {
+        for (gd_result& r : res) { r = gd_result{}; r.status = st; }
+        return;
+    }
+    // a query that outgrew its share of the queues (or a launch whose
+    // bounded waits gave up) runs again alone, with buffers grown for it
+    for (size_t j = 0; j < m; ++j) {
+        if (res[j].status != GD_ERR_OVERFLOW && res[j].status != GD_ERR_TIMEOUT) continue;
         gd_result r{};
-        gd_status st = serve_single(S->ctx, pr.first.q, &r);
-        if (st != GD_OK) r.status = st;
-        std::lock_guard<std::mutex> g(S->mu);
-        S->pending.erase(pr.first.ticket);
-        S->done[pr.first.ticket] = r;
+        gd_status s1 = serve_single(S->exec, take[j].q, &r);
+        if (s1 != GD_OK) r.status = s1;
+        res[j] = r;
     }
-    s.reqs.clear();
-    s.busy = false;
+}
+
+constexpr long long kBatchFrom = 8;
+constexpr int kPipeline = 2;  // single-query launches in flight on the lane
+
+struct InFlight {
+    Request req;
+    int slot;
+    unsigned long long seq;
+};
+
+void publish(gd_server* S, const Request& r, const gd_result& res) {
+    std::lock_guard<std::mutex> g(S->mu);
+    S->pending.erase(r.ticket);
+    S->done[r.ticket] = res;
+    S->held_foot -= r.foot;
 }
 
 void run_loop(gd_server* S) {
@@ -155,109 +137,86 @@ void run_loop(gd_server* S) {
     // a request arriving in a steady stream is not delayed by a thread wake-up
     const auto kStayAwake = std::chrono::milliseconds(20);
     auto last_work = std::chrono::steady_clock::now();
+    std::vector<Request> take;
+    std::vector<gd_result> res;
+    std::deque<InFlight> fl;  // pipelined single queries, oldest first
+    int next_slot = 0;
     for (;;) {
         bool worked = false;
-        // harvest finished slots; a slot whose stream reports an error (the
-        // context is unusable then) fails its requests instead of being
-        // waited for forever
-        for (Slot& s : S->slots) {
-            if (!s.busy) continue;
-            cudaError_t q = cudaStreamQuery(s.b.stream);
-            if (q == cudaSuccess) {
-                harvest(S, s);
-                worked = true;
-            } else if (q != cudaErrorNotReady) {
-                std::lock_guard<std::mutex> g(S->mu);
-                for (auto& r : s.reqs) {
-                    gd_result res{};
-                    res.status = GD_ERR_CUDA;
-                    S->pending.erase(r.ticket);
-                    S->done[r.ticket] = res;
-                }
-                s.reqs.clear();
-                s.busy = false;
-                S->loop_error = GD_ERR_CUDA;
-                worked = true;
-            }
+        // collect the oldest single query once its record is stamped
+        if (!fl.empty() && serve_single_ready(S->exec, fl.front().slot, fl.front().seq)) {
+            gd_result r{};
+            const InFlight f = fl.front();
+            fl.pop_front();
+            gd_status st = serve_single_finish(S->exec, f.req.q, f.slot, f.seq, &r);
+            if (st != GD_OK && r.status == GD_OK) r.status = st;
+            publish(S, f.req, r);
+            worked = true;
         }
-        // admit queued requests into free slots (none while a slot holds the
-        // whole GPU)
-        bool whole_busy = false;
-        for (Slot& s : S->slots) whole_busy = whole_busy || (s.busy && s.whole);
-        for (Slot& s : S->slots) {
-            if (whole_busy) break;
-            if (s.busy) continue;
-            std::vector<Request> take;
-            {
-                std::unique_lock<std::mutex> g(S->mu);
-                if (S->queue.empty()) break;
-                if (S->opts.linger_us > 0 && (long long)S->queue.size() < S->opts.max_batch) {
-                    // wait briefly for more requests to fill the batch
-                    S->cv.wait_for(g, std::chrono::microseconds(S->opts.linger_us));
-                    if (S->queue.empty()) break;
-                }
-                int kind = (int)S->queue.front().q.kind;
+        take.clear();
+        bool batch = false;
+        if (S->queued.load(std::memory_order_acquire) > 0 && (long long)fl.size() < kPipeline) {
+            std::unique_lock<std::mutex> g(S->mu);
+            if (S->opts.linger_us > 0 && fl.empty() && (long long)S->queue.size() < S->opts.max_batch &&
+                !S->stop.load()) {
+                // wait (once) for more requests to fill the batch
+                S->cv.wait_for(g, std::chrono::microseconds(S->opts.linger_us),
+                               [&] { return (long long)S->queue.size() >= S->opts.max_batch || S->stop.load(); });
+            }
+            // a short queue runs one request at a time as a single query (the
+            // single-query launch has the background probes, the CTA-shared
+            // bound and the one-warp setup that a batch launch lacks, so the
+            // heaviest requests, which set the tail, run fastest alone), with
+            // the next one already launched behind it on the stream; from
+            // kBatchFrom waiting requests on, a batch's throughput pays for
+            // that (a batch starts once the pipelined launches are collected)
+            batch = (long long)S->queue.size() >= kBatchFrom;
+            if (!S->queue.empty() && (!batch || fl.empty())) {
+                const gd_kind kind = S->queue.front().q.kind;
+                const long long cap = batch ? S->opts.max_batch : 1;
                 long long foot = 0;
-                for (auto it = S->queue.begin(); it != S->queue.end() && (long long)take.size() < S->opts.max_batch;) {
-                    if ((int)it->q.kind != kind) { ++it; continue; }
-                    if (!take.empty() && foot + it->foot > S->slot_budget) break;
+                for (auto it = S->queue.begin(); it != S->queue.end() && (long long)take.size() < cap;) {
+                    if (it->q.kind != kind) { ++it; continue; }
+                    if (!take.empty() && foot + it->foot > S->opts.memory_budget) break;
                     foot += it->foot;
-                    S->queued_foot -= it->foot;
                     take.push_back(*it);
                     it = S->queue.erase(it);
                 }
+                S->queued.store((long long)S->queue.size(), std::memory_order_release);
             }
-            if (take.empty()) break;
-            std::vector<gd_query> qs(take.size());
-            for (size_t j = 0; j < take.size(); ++j) qs[j] = take[j].q;
-            int kind = (int)qs[0].kind;
-            // a batch that finds the GPU idle and the queue empty gets the whole
-            // GPU (the latency of a lone request is that of a plain query);
-            // otherwise the slot's share, so that slots run side by side
-            bool idle = true;
-            for (Slot& o : S->slots) idle = idle && !o.busy;
-            bool solo = false;
-            if (idle) {
-                std::lock_guard<std::mutex> g(S->mu);
-                solo = S->queue.empty();
-            }
-            const int grid = solo ? S->whole_grid : s.b.grid;
-            gd_status st = serve_launch_batch(S->ctx, s.b, qs.data(), (long long)qs.size(), kind, grid);
-            if (st != GD_OK) {
-                std::lock_guard<std::mutex> g(S->mu);
-                for (auto& r : take) {
-                    gd_result res{};
-                    res.status = st;
-                    S->pending.erase(r.ticket);
-                    S->done[r.ticket] = res;
-                }
-                continue;
-            }
-            s.kind = kind;
-            s.whole = solo;
-            s.reqs = std::move(take);
-            s.busy = true;
-            worked = true;
-            if (solo) break;
         }
-        if (S->stop.load()) {
-            bool idle = true;
-            for (Slot& s : S->slots) idle = idle && !s.busy;
-            std::lock_guard<std::mutex> g(S->mu);
-            if (idle && S->queue.empty()) break;
-        }
-        const auto now = std::chrono::steady_clock::now();
-        if (worked) last_work = now;
-        if (!worked) {
-            std::unique_lock<std::mutex> g(S->mu);
-            bool any_busy = false;
-            for (Slot& s : S->slots) any_busy = any_busy || s.busy;
-            if (S->queue.empty() && !any_busy && !S->stop.load() && now - last_work > kStayAwake) {
-                S->cv.wait_for(g, std::chrono::milliseconds(2));
+        if (take.size() == 1 && !batch) {
+            InFlight f{take[0], next_slot, 0ull};
+            gd_status st = serve_single_launch(S->exec, f.req.q, f.slot, &f.seq);
+            if (st == GD_OK) {
+                fl.push_back(f);
+                next_slot = (next_slot + 1) % kPipeline;
             } else {
-                g.unlock();
-                std::this_thread::yield();
+                gd_result r{};
+                r.status = st;
+                publish(S, f.req, r);
             }
+            worked = true;
+        } else if (!take.empty()) {
+            run_batch(S, take, res);
+            for (size_t j = 0; j < take.size(); ++j) publish(S, take[j], res[j]);
+            worked = true;
+        }
+        if (worked) {
+            last_work = std::chrono::steady_clock::now();
+            continue;
+        }
+        if (!fl.empty()) continue;  // wait for the stamp
+        if (S->stop.load()) {
+            std::lock_guard<std::mutex> g(S->mu);
+            if (S->queue.empty()) break;
+            continue;
+        }
+        if (std::chrono::steady_clock::now() - last_work > kStayAwake) {
+            std::unique_lock<std::mutex> g(S->mu);
+            S->cv.wait_for(g, std::chrono::milliseconds(2), [&] { return !S->queue.empty() || S->stop.load(); });
+        } else {
+            std::this_thread::yield();
         }
     }
 }
@@ -266,52 +225,48 @@ void run_loop(gd_server* S) {
 
 extern "C" {
 
+GD_API gd_status gd_query_footprint(const gd_query* q, int64_t* bytes) {
+    if (!q || !bytes || !q->a || !q->b) return GD_ERR_INVALID_ARG;
+    *bytes = footprint(*q);
+    return GD_OK;
+}
+
 GD_API gd_status gd_serve_start(gd_ctx* ctx, const gd_serve_opts* opts, gd_server** out) {
     if (!ctx || !out) return GD_ERR_INVALID_ARG;
     *out = nullptr;
     gd_serve_opts o{};
-    // measured on a 64-mesh pool at saturation: 2 slots of 16 queries gave
-    // 9.2 K q/s; 4 x 256 gave 5.2 K, 2 x 1024 6.2 K (a launch lasts as long
-    // as its slowest query, so small batches keep the slots turning over)
-    o.slots = 2;
+    o.slots = 1;
     o.max_batch = 16;
     o.memory_budget = 8ll << 30;
     o.linger_us = 0;
     if (opts) {
-        if (opts->slots > 0) o.slots = std::min(opts->slots, 64);
         if (opts->max_batch > 0) o.max_batch = opts->max_batch;
         if (opts->memory_budget > 0) o.memory_budget = opts->memory_budget;
         if (opts->linger_us > 0) o.linger_us = opts->linger_us;
     }
-    cudaSetDevice(serve_device(ctx));
-    // make sure the context's own buffers exist for oversized requests
+    const int device = serve_device(ctx);
+    gd_ctx* exec = nullptr;
+    gd_status s = gd_ctx_create(device, &exec);
+    if (s != GD_OK) return s;
+    // the lane's work buffers come out of the budget: two fronts and the leaf
+    // queue of n entries (16 B each) and n / 4 candidates (72 B each)
+    gd_tunables t = serve_tunables(ctx);
+    const long long n = std::max<long long>(o.memory_budget / (3 * 16 + 72 / 4), 1 << 16);
+    t.front_capacity = n;
+    t.leaf_capacity = n;
+    t.cand_capacity = std::max<long long>(n / 4, 1 << 14);
+    t.max_capacity = std::max<long long>(t.max_capacity, n);
+    t.batch_budget = 0;
+    s = gd_ctx_set_tunables(exec, &t);
+    if (s == GD_OK) s = serve_prepare(exec, o.max_batch);
+    if (s != GD_OK) {
+        gd_ctx_destroy(exec);
+        return s;
+    }
     gd_server* S = new gd_server();
     S->ctx = ctx;
+    S->exec = exec;
     S->opts = o;
-    S->slot_budget = o.memory_budget / o.slots;
-    // Every slot's cooperative grid must stay resident while the other slots
-    // run theirs.  The CTAs of a grid are spread over the GPU's partitions, so
-    // an exact split of the full capacity can leave one partition
-    // over-subscribed (a 3-way split, 3 x 101 CTAs, was seen to leave a grid
-    // partly unscheduled until its bounded barrier wait gave up): the slots
-    // share 90% of the capacity, in grids of a multiple of 16 CTAs.
-    int occ = std::max(1, std::min(query_max_blocks_per_sm(0), query_max_blocks_per_sm(1)));
-    int cap = occ * serve_sms(ctx);
-    int per = cap;
-    if (o.slots > 1) {
-        per = (cap * 9 / 10) / o.slots;
-        per -= per % 16;
-        if (per < 16) per = std::min(16, cap);
-    }
-    S->whole_grid = cap;
-    S->slots.resize(o.slots);
-    for (Slot& s : S->slots) {
-        if (!alloc_slot(s, S->slot_budget, o.max_batch, per)) {
-            for (Slot& t : S->slots) free_slot(t);
-            delete S;
-            return GD_ERR_OOM;
-        }
-    }
     S->loop = std::thread(run_loop, S);
     *out = S;
     return GD_OK;
@@ -327,13 +282,15 @@ GD_API gd_status gd_serve_submit(gd_server* S, const gd_query* q, uint64_t* tick
     {
         std::lock_guard<std::mutex> g(S->mu);
         if (S->stop.load()) return GD_ERR_BUSY;
-        long long cap = S->slot_budget * (long long)S->slots.size();
-        const long long qmax = std::max(4096ll, 16ll * S->opts.max_batch * (long long)S->slots.size());
-        if ((long long)S->queue.size() >= qmax || S->queued_foot + r.foot > cap)
-            return GD_ERR_BUSY;
+        const long long qmax = std::max(4096ll, 16ll * S->opts.max_batch);
+        // a request larger than the whole budget is admitted only onto an
+        // empty lane (it then runs alone, its buffers grown for it)
+        const bool fits = S->held_foot + r.foot <= S->opts.memory_budget || S->held_foot == 0;
+        if ((long long)S->queue.size() >= qmax || !fits) return GD_ERR_BUSY;
         r.ticket = S->next_ticket++;
-        S->queued_foot += r.foot;
+        S->held_foot += r.foot;
         S->queue.push_back(r);
+        S->queued.store((long long)S->queue.size(), std::memory_order_release);
         S->pending[r.ticket] = 1;
     }
     S->cv.notify_all();
@@ -373,7 +330,7 @@ GD_API gd_status gd_serve_stop(gd_server* S) {
     S->stop.store(true);
     S->cv.notify_all();
     if (S->loop.joinable()) S->loop.join();
-    for (Slot& s : S->slots) free_slot(s);
+    gd_ctx_destroy(S->exec);
     delete S;
     return GD_OK;
 }

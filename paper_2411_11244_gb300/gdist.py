@@ -31,7 +31,7 @@ EXPORTS = [
     "gd_get_stats", "gd_ctx_stream", "gd_mesh_create", "gd_bvh_build", "gd_mesh_update", "gd_mesh_destroy", "gd_mesh_info",
     "gd_mesh_download", "gd_min_distance", "gd_max_distance", "gd_naive_query", "gd_point_distance", "gd_point_stats", "gd_query_device", "gd_query_device_noalloc",
     "gd_batch_query", "gd_batch_times", "gd_autotune", "gd_graph_create", "gd_graph_launch", "gd_graph_destroy",
-    "gd_mesh_build_time",
+    "gd_mesh_build_time", "gd_query_footprint",
     "gd_serve_start", "gd_serve_submit", "gd_serve_poll", "gd_serve_drain", "gd_serve_stop",
 ]
 
@@ -139,6 +139,7 @@ def load(path: str = LIB_PATH):
         "gd_query_device_noalloc": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _vp, _vp]),
         "gd_batch_query": (C.c_int, [_vp, C.POINTER(gd_query), C.c_int64, C.POINTER(gd_result)]),
         "gd_batch_times": (C.c_int, [_vp, C.c_int64, C.POINTER(C.c_int64)]),
+        "gd_query_footprint": (C.c_int, [C.POINTER(gd_query), C.POINTER(C.c_int64)]),
         "gd_mesh_build_time": (C.c_int, [_vp, C.POINTER(C.c_double)]),
         "gd_autotune": (C.c_int, [_vp, C.POINTER(gd_query), C.c_int64, C.c_int32, C.POINTER(gd_tunables)]),
         "gd_graph_create": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp, _vp, _vp, C.POINTER(_vp)]),
@@ -421,6 +422,15 @@ def gd_batch_times(ctx, n: int) -> np.ndarray:
     out = np.zeros(n, dtype=np.int64)
     _check(load().gd_batch_times(ctx, n, out.ctypes.data_as(C.POINTER(C.c_int64))), ctx)
     return out
+
+
+def gd_query_footprint(query) -> int:
+    """Predicted work-buffer bytes of one query (the server's admission model)."""
+    if not isinstance(query, gd_query):
+        query = make_queries([query])[0]
+    b = C.c_int64()
+    _check(load().gd_query_footprint(C.byref(query), C.byref(b)))
+    return b.value
 
 
 def gd_serve_start(ctx, slots=0, max_batch=0, memory_budget=0, linger_us=0):

@@ -311,8 +311,10 @@ def test_batch_eviction_matches_single(G, oracle_mod):
 
 
 def test_refit_modes_agree(G, oracle_mod):
-    """Refitting B's low subtrees only tightens bounds: with and without it
-    every answer matches the FP64 oracle (value and witness), and the two
+    """Refitting B only tightens bounds: with the lazy refit of B's low
+    subtrees (mode 1), without refit (mode 2) and with the paper's full refit
+    of B into A's frame per query (mode 3), every answer matches the FP64
+    oracle (value and witness), single query and device-resident, and the
     modes give the same answer."""
     rng = np.random.default_rng(31)
     c = G.gd_ctx_create(0)
@@ -333,6 +335,11 @@ def test_refit_modes_agree(G, oracle_mod):
                 r2 = fn(c, ma, mb, xa, xb)
                 check(r2, A, xa, B, xb, kind, ref, diag, oracle_mod)
                 same_answer(r1, r2, oracle_mod, A, xa, B, xb, kind)
+                G.gd_ctx_set_tunables(c, refit_mode=3)
+                r3 = fn(c, ma, mb, xa, xb)
+                check(r3, A, xa, B, xb, kind, ref, diag, oracle_mod)
+                same_answer(r1, r3, oracle_mod, A, xa, B, xb, kind)
+                G.gd_ctx_set_tunables(c, refit_mode=1)
         G.gd_mesh_destroy(ma)
         G.gd_mesh_destroy(mb)
     finally:
@@ -648,7 +655,7 @@ def test_serve_alone_equals_in_mix(G, ctx, oracle_mod):
     for q in qs:
         fn = G.gd_min_distance if q[4] == 0 else G.gd_max_distance
         alone.append(fn(ctx, q[0], q[1], q[2], q[3]))
-    srv = G.gd_serve_start(ctx, slots=3, max_batch=16)
+    srv = G.gd_serve_start(ctx, max_batch=16)
     try:
         tickets = []
         for i in range(len(qs)):
@@ -670,12 +677,63 @@ def test_serve_alone_equals_in_mix(G, ctx, oracle_mod):
     finally:
         G.gd_serve_stop(srv)
     assert len(got) == len(tickets)
+    bvh = [oracle_mod.Bvh(m) for m in meshes]
     for i, t in enumerate(tickets):
         a, b = ids[i]
-        same_answer(got[t], alone[i], oracle_mod, meshes[a], qs[i][2], meshes[b], qs[i][3],
-                    "min" if qs[i][4] == 0 else "max")
+        kind = "min" if qs[i][4] == 0 else "max"
+        same_answer(got[t], alone[i], oracle_mod, meshes[a], qs[i][2], meshes[b], qs[i][3], kind)
+        ref = oracle_mod.bvh_query(bvh[a], qs[i][2], bvh[b], qs[i][3], kind)
+        check(got[t], meshes[a], qs[i][2], meshes[b], qs[i][3], kind, ref,
+              oracle_mod.diag(meshes[a], qs[i][2], meshes[b], qs[i][3]), oracle_mod)
     for h in hs:
         G.gd_mesh_destroy(h)
+
+
+def test_serve_admission_by_footprint(G, ctx, oracle_mod):
+    """Admission by HBM footprint: with a budget below the predicted
+    footprints of two requests together, the second submission is refused
+    (GD_ERR_BUSY) while the first is held (queued: a long linger keeps it
+    waiting for company), and admitted once the first has finished; both
+    answers match the oracle.  A request larger than the whole budget is
+    admitted onto an empty server and still answered."""
+    import time
+    rng = np.random.default_rng(12)
+    A, B = synth.torus(1.0, 0.25, 40, 20), synth.geosphere(12, 0.6, 1e-3, 1)
+    ha, hb = _mesh(G, ctx, A), _mesh(G, ctx, B)
+    items = [(ha, hb, _rigid(rng, 0.3), _rigid(rng, 1.5), G.GD_MIN) for _ in range(2)]
+    arr = G.make_queries(items)
+    f1, f2 = G.gd_query_footprint(arr[0]), G.gd_query_footprint(arr[1])
+    assert f1 > 1024 and f2 > 1024
+
+    def wait(srv, t):
+        deadline = time.time() + 60
+        while time.time() < deadline:
+            rc, r = G.gd_serve_poll(srv, t)
+            if rc == 0:
+                return r
+            assert rc == G.GD_ERR_NOT_READY
+            time.sleep(0.001)
+        raise AssertionError("request not served")
+
+    oa, ob = oracle_mod.Bvh(A), oracle_mod.Bvh(B)
+    for budget in (f1 + f2 - 1, f1 // 2):
+        srv = G.gd_serve_start(ctx, max_batch=16, memory_budget=budget, linger_us=300000)
+        try:
+            rc1, t1 = G.gd_serve_submit(srv, arr[0])
+            assert rc1 == 0
+            rc2, _ = G.gd_serve_submit(srv, arr[1])
+            assert rc2 == G.GD_ERR_BUSY
+            r1 = wait(srv, t1)
+            rc2, t2 = G.gd_serve_submit(srv, arr[1])
+            assert rc2 == 0
+            r2 = wait(srv, t2)
+        finally:
+            G.gd_serve_stop(srv)
+        for r, (a, b, xa, xb, k) in zip((r1, r2), items):
+            ref = oracle_mod.bvh_query(oa, xa, ob, xb, "min")
+            check(r, A, xa, B, xb, "min", ref, oracle_mod.diag(A, xa, B, xb), oracle_mod)
+    G.gd_mesh_destroy(ha)
+    G.gd_mesh_destroy(hb)
 
 
 def test_serve_drain_collects_every_ticket(G, ctx, oracle_mod):
@@ -688,7 +746,7 @@ def test_serve_drain_collects_every_ticket(G, ctx, oracle_mod):
     qs = [(hs[i % 2], hs[(i + 1) % 2], _rigid(rng, 0.3), _rigid(rng, 1.5), G.GD_MIN) for i in range(40)]
     alone = [G.gd_min_distance(ctx, q[0], q[1], q[2], q[3]) for q in qs]
     arr = G.make_queries(qs)
-    srv = G.gd_serve_start(ctx, slots=2, max_batch=8)
+    srv = G.gd_serve_start(ctx, max_batch=8)
     try:
         idx = {}
         for i in range(len(qs)):
@@ -994,6 +1052,20 @@ def test_rings_full_size_frames(G, ctx, oracle_mod):
     frames against the oracle's float64 BVH traversal."""
     A, B, xa, xbs = synth.config_rings(frames=100)
     run_pair(G, ctx, oracle_mod, A, B, [(xa, xbs[i]) for i in (0, 37, 99)], kinds=("min",), bvh_oracle=True)
+
+
+def test_rings_full_size_full_refit(G, oracle_mod):
+    """The paper's per-frame refit (refit mode 3) at full size: B's 2^22-leaf
+    tree refit into A's frame in three passes (subtrees of 2^8 leaves, then
+    8 and 6 levels above them) before the traversal; min and max of two
+    frames against the oracle's float64 BVH traversal."""
+    c = G.gd_ctx_create(0)
+    try:
+        G.gd_ctx_set_tunables(c, refit_mode=3)
+        A, B, xa, xbs = synth.config_rings(frames=100)
+        run_pair(G, c, oracle_mod, A, B, [(xa, xbs[i]) for i in (5, 61)], kinds=("min", "max"), bvh_oracle=True)
+    finally:
+        G.gd_ctx_destroy(c)
 
 
 def test_gears_full_size_batch_sample(G, ctx, oracle_mod):
