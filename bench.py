@@ -335,16 +335,85 @@ def build_roofline(G, meshes, peak, peak_kind):
     written), 8 radix passes of 8 bits over the 63-bit codes (8 B/T histogram
     read, 12 B/T read and 12 B/T written by the scatter: 256 B/T), the sorted
     order copied (8 B/T), leaves (4 B/T order + 12 B/T indices + 12 B/V read,
-    48 B/T triangle records written) and 24 B per node box written."""
+    48 B/T triangle records and 12 B/T vertex indices in leaf order, for the
+    refits, written) and 24 B per node box written."""
     out = []
     for h, T, V in meshes:
         L, _ = G.gd_mesh_info(h)
         ms = G.gd_mesh_build_time(h)
-        alg = 364 * T + 36 * V + 24 * ((2 << L) - 1)
+        alg = 376 * T + 36 * V + 24 * ((2 << L) - 1)
         gbs = alg / (ms * 1e-3) / 1e9
         out.append({"triangles": T, "device_ms": ms, "alg_bytes": alg, "achieved": gbs, "peak": peak,
                     "unit": "GB/s", "frac": gbs / peak, "peak_source": peak_kind})
     return out
+
+
+def bench_tori(G, ctx, steps, warmup, cpu=True):
+    """Config 1: two tori (R = 1, r = 0.3, 32 x 32 quads = 2,048 triangles
+    each), B under the stored seeded rotation at +2.5 along x (the first seed
+    whose draw does not intersect, tests/golden/tori_seed.json).  Per kind:
+    device time per query (CUDA events, transforms resident, L2 flushed),
+    the synchronous call (e2e), and the brute-force FP64 oracle (all
+    4,194,304 triangle pairs) on one thread and on all cores, with the
+    engine's answer against it."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_2411_11244_gb300 import synth
+    seed = json.load(open(os.path.join(ROOT, "tests", "golden", "tori_seed.json")))["seed"]
+    A, B, xa, xb = synth.config_tori(seed)
+    ma, mb = G.gd_mesh_create(ctx, *A), G.gd_mesh_create(ctx, *B)
+    G.gd_bvh_build(ma, ctx=ctx)
+    G.gd_bvh_build(mb, ctx=ctx)
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    dev = stream.device
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    d_xa = torch.tensor(np.asarray(xa), dtype=torch.float64, device=dev)
+    d_xb = torch.tensor(np.asarray(xb), dtype=torch.float64, device=dev)
+    d_out = torch.zeros(10, dtype=torch.float64, device=dev)
+    diag = oracle.diag(A, xa, B, xb)
+    res = {"workload": f"two tori: 2 x {len(A[1])} tris, seed {seed}"}
+    for kind, k, fn in (("min", G.GD_MIN, G.gd_min_distance), ("max", G.GD_MAX, G.gd_max_distance)):
+        r = fn(ctx, ma, mb, xa, xb)
+        ms = []
+        for j in range(warmup + steps):
+            flush.fill_(float(j))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            G.gd_query_device(ctx, ma, mb, k, d_xa.data_ptr(), d_xb.data_ptr(), d_out.data_ptr(), sptr)
+            e1.record(stream)
+            e1.synchronize()
+            if j >= warmup:
+                ms.append(e0.elapsed_time(e1))
+        e2e = []
+        for j in range(steps):
+            flush.fill_(float(j))
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            fn(ctx, ma, mb, xa, xb)
+            e2e.append(1000.0 * (time.perf_counter() - t1))
+        leg = {"ms_per_query": statistics.mean(ms), "p50_ms": sorted(ms)[len(ms) // 2],
+               "e2e": {"value": statistics.mean(e2e), "unit": "ms/query"}}
+        if cpu:
+            threads = os.cpu_count() or 1
+            t0 = time.perf_counter()
+            ref = oracle.brute(A, xa, B, xb, kind, threads=1)
+            one = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            oracle.brute(A, xa, B, xb, kind, threads=threads)
+            allc = time.perf_counter() - t0
+            dw = oracle.witness_distance(A, xa, B, xb, r.tri_a, r.tri_b, kind)[0]
+            leg["cpu_baseline"] = {"value": 1000.0 * allc, "unit": "ms/query", "cores": threads, "kind": "oracle",
+                                   "one_core_ms": 1000.0 * one,
+                                   "sample": "one query, brute force over all 4,194,304 triangle pairs (FP64)"}
+            leg["parity"] = {"abs_err_over_diag": abs(r.d - ref.d) / diag,
+                             "witness_ok": abs(dw - ref.d) <= 1e-12 * abs(ref.d) + 1e-15 * diag}
+        res[kind] = leg
+    G.gd_mesh_destroy(ma)
+    G.gd_mesh_destroy(mb)
+    del flush
+    return res
 
 
 def bench_icospheres(G, ctx, steps, warmup, cpu_frames=64, cpu=True):
@@ -507,10 +576,10 @@ def bench_deformable(G, ctx, ma, frames=8):
     u_host, q_host, d_host = run([h.numpy() for h in host])
     # device time of the update from device memory (events on the engine's
     # stream around the synchronous call) against the HBM roofline, with the
-    # bytes the update must move: per triangle 4 B order + 12 B indices read
-    # and a 48 B record stored, 12 B per distinct vertex gathered (repeated
-    # gathers of a vertex are cache hits), 24 B per tree node stored, and the
-    # vertex copy (12 B per vertex each way)
+    # bytes the update must move: per triangle 4 B order + 12 B vertex indices
+    # (both in leaf order) read and a 48 B record stored, 12 B per distinct
+    # vertex gathered (repeated gathers of a vertex are cache hits), 24 B per
+    # tree node stored, and the vertex copy (12 B per vertex each way)
     es = torch.cuda.ExternalStream(G.gd_ctx_stream(ctx))
     dt = []
     for i in range(frames):
@@ -742,6 +811,7 @@ def main():
     ap.add_argument("--no-naive", action="store_true")
     ap.add_argument("--no-points", action="store_true")
     ap.add_argument("--no-icospheres", action="store_true")
+    ap.add_argument("--no-tori", action="store_true")
     ap.add_argument("--batched-queries", type=int, default=4096)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -886,6 +956,8 @@ def main():
         line["served"] = bench_served(G, ctx)
     if one and not args.no_icospheres:
         line["icospheres"] = bench_icospheres(G, ctx, args.steps, args.warmup, cpu=not args.no_cpu_baseline)
+    if one and not args.no_tori:
+        line["tori"] = bench_tori(G, ctx, args.steps, args.warmup, cpu=not args.no_cpu_baseline)
     print(json.dumps(line), flush=True)
     G.gd_ctx_destroy(ctx)
     if world > 1:

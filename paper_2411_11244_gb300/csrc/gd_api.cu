@@ -39,6 +39,7 @@ struct gd_mesh {
     float* d_box = nullptr;
     float4* d_tri = nullptr;
     unsigned* d_order = nullptr;  // original index of each sorted triangle (leaf order)
+    int32_t* d_stris = nullptr;   // vertex indices of each sorted triangle (leaf order), for refits
     MeshDev* d_desc = nullptr;
     MeshDev h_desc{};
     unsigned* d_flags = nullptr;  // validation flags of gd_mesh_update
@@ -736,8 +737,8 @@ GD_API gd_status gd_bvh_build(gd_mesh* m, const gd_build_opts* opts) {
     }
     int L = 0;
     while ((2ll << L) <= m->nt) ++L;
-    cudaFree(m->d_box); cudaFree(m->d_tri); cudaFree(m->d_order);
-    m->d_box = nullptr; m->d_tri = nullptr; m->d_order = nullptr;
+    cudaFree(m->d_box); cudaFree(m->d_tri); cudaFree(m->d_order); cudaFree(m->d_stris);
+    m->d_box = nullptr; m->d_tri = nullptr; m->d_order = nullptr; m->d_stris = nullptr;
     m->built = false;
     m->tree = false;
     BuildBuffers b{};
@@ -760,10 +761,12 @@ GD_API gd_status gd_bvh_build(gd_mesh* m, const gd_build_opts* opts) {
     cudaError_t e = cudaMalloc(&m->d_box, sizeof(float) * 6 * (2ull << L));
     if (e == cudaSuccess) e = cudaMalloc(&m->d_tri, sizeof(float4) * 3 * m->nt);
     if (e == cudaSuccess) e = cudaMalloc(&m->d_order, sizeof(unsigned) * m->nt);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_stris, sizeof(int32_t) * 3 * m->nt);
     if (e != cudaSuccess) { cleanup(); return cuda_fail(ctx, e, "gd_bvh_build alloc"); }
     b.box = m->d_box;
     b.tri = m->d_tri;
     b.order = m->d_order;
+    b.stris = m->d_stris;
     unsigned flags[8] = {0};
     // device time of the build's kernels: events around the validation and
     // around the tree build (not the allocations and the flag read-back)
@@ -822,7 +825,7 @@ GD_API gd_status gd_mesh_update(gd_mesh* m, const float* verts, int64_t nv) {
     GD_CUDA(ctx, cudaMemcpyAsync(m->d_verts, verts, sizeof(float) * 3 * nv, cudaMemcpyDefault, ctx->stream));
     BuildBuffers b{};
     b.verts = m->d_verts; b.tris = m->d_tris; b.nv = m->nv; b.nt = m->nt; b.L = m->L;
-    b.box = m->d_box; b.tri = m->d_tri; b.order = m->d_order; b.flags = m->d_flags;
+    b.box = m->d_box; b.tri = m->d_tri; b.order = m->d_order; b.stris = m->d_stris; b.flags = m->d_flags;
     // the refit writes max |coordinate| straight into the device descriptor
     float* P_dev = reinterpret_cast<float*>(reinterpret_cast<char*>(m->d_desc) + offsetof(MeshDev, P));
     GD_CUDA(ctx, build_refit(b, P_dev, ctx->stream));
@@ -848,7 +851,7 @@ GD_API void gd_mesh_destroy(gd_mesh* m) {
         cudaStreamSynchronize(m->ctx->stream);
     }
     cudaFree(m->d_verts); cudaFree(m->d_tris); cudaFree(m->d_box); cudaFree(m->d_tri); cudaFree(m->d_desc);
-    cudaFree(m->d_order); cudaFree(m->d_flags);
+    cudaFree(m->d_order); cudaFree(m->d_stris); cudaFree(m->d_flags);
     delete m;
 }
 

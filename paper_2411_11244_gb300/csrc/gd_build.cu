@@ -231,6 +231,14 @@ __global__ void k_rs_scatter(const unsigned long long* kin, const unsigned* vin,
 
 constexpr int kTreeLevels = 8;  // tree levels one CTA reduces (2^8 = 256 nodes in, one out)
 
+// A node box (lo xyz, hi xyz, 24 bytes, 8-byte aligned) as three float2 stores.
+__device__ __forceinline__ void store_box(float* o, const float lo[3], const float hi[3]) {
+    float2* p = reinterpret_cast<float2*>(o);
+    p[0] = make_float2(lo[0], lo[1]);
+    p[1] = make_float2(lo[2], hi[0]);
+    p[2] = make_float2(hi[1], hi[2]);
+}
+
 // Subtree union shared by the two tree kernels: on entry thread i holds node
 // box (lo, hi) of the CTA's 2^levels consecutive nodes of depth d (heap ids
 // from first = 2^d + CTA offset); each step makes node k of the level above
@@ -253,11 +261,7 @@ __device__ __forceinline__ void reduce_subtree(float* box, long long first, int 
             hi[0] = fmaxf(l[3], r[3]); hi[1] = fmaxf(l[4], r[4]); hi[2] = fmaxf(l[5], r[5]);
         }
         __syncthreads();
-        if (i < n) {
-            float* o = box + 6 * ((first >> s) + i);
-            o[0] = lo[0]; o[1] = lo[1]; o[2] = lo[2];
-            o[3] = hi[0]; o[4] = hi[1]; o[5] = hi[2];
-        }
+        if (i < n) store_box(box + 6 * ((first >> s) + i), lo, hi);
     }
     if ((first >> levels) == 1 && i == 0) {
         if (root_out)
@@ -273,11 +277,16 @@ __device__ __forceinline__ void reduce_subtree(float* box, long long first, int 
 // leaves: leaf l owns sorted triangles [floor(l T / 2^L), floor((l+1) T / 2^L)).
 // One thread per leaf, 2^levels leaves per CTA: gather the leaf's triangles in
 // sorted order (order[j] = original index of sorted triangle j), store them
-// and the exact leaf box, then the CTA's subtree above its leaves.
+// and the exact leaf box, then the CTA's subtree above its leaves.  The build
+// (stris_in == nullptr) reads each triangle's vertex indices through order
+// and stores them in leaf order (stris_out); the refit of a deformed mesh
+// reads them from there, contiguously, so its vertex gathers wait on one
+// load instead of two dependent ones.
 // bad != nullptr: a non-finite coordinate sets *bad (the refit's check; the
 // build validated the vertices before sorting).
 __global__ void k_leaves(const float* verts, const int32_t* tris, long long nt, int L, const unsigned* order,
-                         float4* tri, float* box, int levels, unsigned* bad, float* root_out, float* P_out) {
+                         const int32_t* stris_in, int32_t* stris_out, float4* tri, float* box, int levels,
+                         unsigned* bad, float* root_out, float* P_out) {
     const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // grid x block = 2^L exactly
     const long long s = (long long)(((unsigned long long)l * (unsigned long long)nt) >> L);
     const long long e = (long long)(((unsigned long long)(l + 1) * (unsigned long long)nt) >> L);
@@ -285,10 +294,17 @@ __global__ void k_leaves(const float* verts, const int32_t* tris, long long nt, 
     bool finite = true;
     for (long long j = s; j < e; ++j) {
         const unsigned id = order[j];
+        int vi[3];
+        if (stris_in) {
+            vi[0] = stris_in[3 * j]; vi[1] = stris_in[3 * j + 1]; vi[2] = stris_in[3 * j + 2];
+        } else {
+            vi[0] = tris[3ll * id]; vi[1] = tris[3ll * id + 1]; vi[2] = tris[3ll * id + 2];
+            if (stris_out) { stris_out[3 * j] = vi[0]; stris_out[3 * j + 1] = vi[1]; stris_out[3 * j + 2] = vi[2]; }
+        }
         float v[9];
         for (int k = 0; k < 3; ++k)
             for (int c = 0; c < 3; ++c) {
-                const float x = verts[3ll * tris[3ll * id + k] + c];
+                const float x = verts[3ll * vi[k] + c];
                 finite = finite && isfinite(x);
                 v[3 * k + c] = x;
                 lo[c] = fminf(lo[c], x);
@@ -299,9 +315,7 @@ __global__ void k_leaves(const float* verts, const int32_t* tris, long long nt, 
         tri[3 * j + 2] = make_float4(v[8], __int_as_float((int)id), 0.f, 0.f);
     }
     if (bad && __syncthreads_or(!finite) && threadIdx.x == 0) atomicOr(bad, 1u);
-    float* b = box + 6 * ((1ll << L) + l);
-    b[0] = lo[0]; b[1] = lo[1]; b[2] = lo[2];
-    b[3] = hi[0]; b[4] = hi[1]; b[5] = hi[2];
+    store_box(box + 6 * ((1ll << L) + l), lo, hi);
     reduce_subtree(box, (1ll << L) + (long long)blockIdx.x * blockDim.x, levels, lo, hi, root_out, P_out);
 }
 
@@ -316,11 +330,12 @@ __global__ void k_reduce_up(float* box, int d, int levels, float* root_out, floa
 
 // all boxes from the sorted order: leaves plus the lowest levels, then one
 // launch per further kTreeLevels levels (three launches for 2^22 leaves)
-void tree_boxes(const float* verts, const int32_t* tris, long long nt, int L, const unsigned* order, float4* tri,
-                float* box, unsigned* bad, float* root_out, float* P_out, cudaStream_t st) {
+void tree_boxes(const float* verts, const int32_t* tris, long long nt, int L, const unsigned* order,
+                const int32_t* stris_in, int32_t* stris_out, float4* tri, float* box, unsigned* bad, float* root_out,
+                float* P_out, cudaStream_t st) {
     int lv = L < kTreeLevels ? L : kTreeLevels;
-    k_leaves<<<(unsigned)(1ll << (L - lv)), 1u << lv, 0, st>>>(verts, tris, nt, L, order, tri, box, lv, bad,
-                                                                 root_out, P_out);
+    k_leaves<<<(unsigned)(1ll << (L - lv)), 1u << lv, 0, st>>>(verts, tris, nt, L, order, stris_in, stris_out, tri, box,
+                                                                 lv, bad, root_out, P_out);
     for (int d = L - lv; d > 0; d -= lv) {
         lv = d < kTreeLevels ? d : kTreeLevels;
         k_reduce_up<<<(unsigned)(1ll << (d - lv)), 1u << lv, 0, st>>>(box, d, lv, root_out, P_out);
@@ -373,14 +388,14 @@ cudaError_t build_tree(const BuildBuffers& b, cudaStream_t st) {
     const int cur = radix_sort_pairs(b.keys, b.vals, b.nt, 3 * b.morton_bits, b.hist, st);
     cudaError_t e = cudaMemcpyAsync(b.order, b.vals[cur], sizeof(unsigned) * b.nt, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return e;
-    tree_boxes(b.verts, b.tris, b.nt, b.L, b.order, b.tri, b.box, nullptr, nullptr, nullptr, st);
+    tree_boxes(b.verts, b.tris, b.nt, b.L, b.order, nullptr, b.stris, b.tri, b.box, nullptr, nullptr, nullptr, st);
     return cudaGetLastError();
 }
 
 cudaError_t build_refit(const BuildBuffers& b, float* P_out, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(b.flags, 0, 16 * sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
-    tree_boxes(b.verts, b.tris, b.nt, b.L, b.order, b.tri, b.box, b.flags + 1,
+    tree_boxes(b.verts, b.tris, b.nt, b.L, b.order, b.stris, nullptr, b.tri, b.box, b.flags + 1,
                reinterpret_cast<float*>(b.flags + 8), P_out, st);
     return cudaGetLastError();
 }

@@ -18,6 +18,8 @@ struct BuildBuffers {
     float* box;           // 6 * 2^(L+1) floats, device
     float4* tri;          // 3 * nt float4, device
     unsigned* order;      // nt, device: original index of each sorted triangle (kept for refits)
+    int32_t* stris;       // nt x 3, device: the sorted triangles' vertex indices (written by the
+                          // build, read by refits; may be nullptr for a build that keeps none)
     unsigned* flags;      // device: [0] bad index, [1] non-finite vertex, [2..8] bounds scratch
     unsigned long long* keys[2];  // nt each, device
     unsigned* vals[2];            // nt each, device
