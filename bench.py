@@ -323,7 +323,7 @@ def bench_batched(G, ctx, n=4096, reps=3, tune_sample=512):
         "speedup_qps": (n / wall) / (n / plain_wall),
         "mix": {"intersecting": zero, "errors": bad, "separate": n - zero - bad},
         "batch_kernel": {"levels": st["levels"], "leaf_pairs": st["leaf_pairs"], "candidates": st["candidates"],
-                         "retries": st["retries"]},
+                         "retries": st["retries"], "phase_us_summed_over_launches": st["phase_us"]},
     }
 
 

@@ -176,7 +176,9 @@ typedef struct {
                                     all levels, leaf narrow phase, float64
                                     refinement, wait for the refinement of the
                                     other CTAs, witness selection, result
-                                    records, total, (2 unused) */
+                                    records, total, (2 unused); CTA 0's view;
+                                    after gd_batch_query, summed over its
+                                    launches */
     uint32_t probes;             /* greedy descents run to seed the bound */
     float u_level[32];           /* running bound entering each level (query 0) */
     float u_probe;               /* running bound after the probes (query 0) */

@@ -294,8 +294,8 @@ unsigned single_work_ctas(const gd_ctx* c, int grid) {
     return (unsigned)(grid - bg);
 }
 
-int grid_blocks(gd_ctx* c, int kind) {
-    int occ = query_max_blocks_per_sm(kind);
+int grid_blocks(gd_ctx* c, int kind, bool batch = false) {
+    int occ = query_max_blocks_per_sm(kind, batch);
     int b = c->tun.blocks_per_sm > 0 ? std::min(c->tun.blocks_per_sm, occ) : occ;
     if (b < 1) b = 1;
     return b * c->sms;
@@ -486,7 +486,7 @@ gd_status batch_pass(gd_ctx* ctx, const gd_query* q, const std::vector<int64_t>&
     a.out = ctx->out_dev;
     a.done_ns = ctx->done_dev;
     batch_limits(ctx->cap_front, ctx->cap_leaf, m, &a.q_budget, &a.q_pool);
-    int grid = grid_blocks(ctx, kind);
+    int grid = grid_blocks(ctx, kind, m > 1);
     GD_CUDA(ctx, launch_query(kind, a, grid, ctx->stream));
     GD_CUDA(ctx, cudaMemcpyAsync(ctx->out_host, ctx->out_dev, sizeof(gd_result) * m, cudaMemcpyDeviceToHost, ctx->stream));
     GD_CUDA(ctx, cudaMemcpyAsync(ctx->done_host, ctx->done_dev, sizeof(unsigned long long) * m,
@@ -508,6 +508,8 @@ gd_status batch_pass(gd_ctx* ctx, const gd_query* q, const std::vector<int64_t>&
         agg->front[i] += st.front[i];
         agg->slots[i] = std::max(agg->slots[i], st.slots[i]);
     }
+    // phase times of CTA 0, summed over the batch's launches
+    for (int i = 0; i < 12; ++i) agg->phase_ns[i] += st.phase_ns[i];
     if (ctx->mb_host->ctr[kCtrLastAbort]) return fail(ctx, GD_ERR_TIMEOUT, "a device-side wait timed out");
     if (ctx->mb_host->ctr[kCtrBadIndex])
         return fail(ctx, GD_ERR_CUDA,
@@ -1351,7 +1353,7 @@ gd_status serve_batch(gd_ctx* ctx, const gd_query* qs, long long m, int kind, gd
     a.host_done = ctx->hd;
     a.host_out = ctx->out_host;
     a.seq = seq;
-    const int grid = grid_blocks(ctx, kind);
+    const int grid = grid_blocks(ctx, kind, m > 1);
     a.work_ctas = m == 1 ? single_work_ctas(ctx, grid) : (unsigned)grid;
     GD_CUDA(ctx, launch_query(kind, a, grid, ctx->stream));
     const volatile unsigned long long* stamp = &ctx->hd->seq;

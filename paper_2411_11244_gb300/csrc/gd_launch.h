@@ -103,7 +103,8 @@ int sort_points(const PointArgs& g, unsigned long long* const keys[2], unsigned*
 cudaError_t launch_point(const PointArgs& g, cudaStream_t stream);
 
 // ---- query (gd_query.cu)
-int query_max_blocks_per_sm(int kind);
+// co-resident CTAs per SM of the query kernel's single-query or batch launch
+int query_max_blocks_per_sm(int kind, bool batch = false);
 cudaError_t launch_query(int kind, const KArgs& args, int grid, cudaStream_t stream);
 cudaError_t build_query_graph(int kind, const KArgs& args, int grid, cudaGraphExec_t* exec);
 

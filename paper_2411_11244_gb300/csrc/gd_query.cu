@@ -1338,7 +1338,10 @@ __device__ __noinline__ void leaf_tight(const AT& A, const uint4* list, unsigned
 // whole warps on the expensive part instead of one lane in each.
 template <int KIND, class AT>
 __device__ void leaf_phase(const AT& A, unsigned nleaf, unsigned& tripairs, unsigned long long& bytes) {
-    __shared__ uint4 list[2 * kBlock];
+    // slots per thread and iteration (two, measured for single queries: the
+    // leaf phase took 17.2 -> 18.3 us on the rings; one kept)
+    constexpr int U = 1;
+    __shared__ uint4 list[(1 + U) * kBlock];
     __shared__ unsigned list_n;
     const unsigned long long total = (unsigned long long)nleaf * 4ull;
     const unsigned long long gstride = (unsigned long long)work_ctas(A) * blockDim.x;
@@ -1350,7 +1353,7 @@ __device__ void leaf_phase(const AT& A, unsigned nleaf, unsigned& tripairs, unsi
     QView Vb;
     int pit = 0;
     if (threadIdx.x == 0) list_n = 0u;
-    for (unsigned long long cbase = (unsigned long long)blockIdx.x * blockDim.x; cbase < total; cbase += gstride) {
+    for (unsigned long long cbase = (unsigned long long)blockIdx.x * blockDim.x; cbase < total; cbase += U * gstride) {
         // a single query whose traversal stopped (D = 0 proven) skips the rest
         // (this barrier also publishes list_n)
         if (__syncthreads_or(AT::kOne && (((volatile CtaState&)cta()).stat & kStatStop) != 0u)) break;
@@ -1358,54 +1361,71 @@ __device__ void leaf_phase(const AT& A, unsigned nleaf, unsigned& tripairs, unsi
         // hides behind this iteration's work)
         unsigned long long gw = 0;
         if (pull) gw = ld_relaxed64(reinterpret_cast<const unsigned long long*>(&A.qs[0].U));
-        unsigned long long vt = cbase + threadIdx.x;
-        bool valid = vt < total;
-        Item it = {1u, 1u, 0.f, 0u};
-        if (valid) {
-            float4 raw = __ldcg(reinterpret_cast<const float4*>(A.leafq + (vt >> 2)));
-            it = *reinterpret_cast<Item*>(&raw);
-            if (!item_ok(A, it)) {
-                flag_bad(A, kBadLeaf);
-                it = Item{1u, 1u, 0.f, 0u};
-                valid = false;
+        // the slots' queue entries first (independent loads), then their tests
+        Item it[U];
+        bool valid[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const unsigned long long vt = cbase + (unsigned long long)u * gstride + threadIdx.x;
+            valid[u] = vt < total;
+            it[u] = Item{1u, 1u, 0.f, 0u};
+            if (valid[u]) {
+                float4 raw = __ldcg(reinterpret_cast<const float4*>(A.leafq + (vt >> 2)));
+                it[u] = *reinterpret_cast<Item*>(&raw);
             }
         }
-        unsigned q = it.q;
-        if (!AT::kOne) view(A, q, Vb);
-        const QConst& V = AT::kOne ? static_cast<const QConst&>(cta().v) : static_cast<const QConst&>(Vb);
-        if (valid && (depth_of(it.a) != V.LA || depth_of(it.b) != V.LB)) {
-            flag_bad(A, kBadLeaf);
-            valid = false;
+        unsigned ta[U], tb[U], q[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const unsigned long long vt = cbase + (unsigned long long)u * gstride + threadIdx.x;
+            if (valid[u] && !item_ok(A, it[u])) {
+                flag_bad(A, kBadLeaf);
+                it[u] = Item{1u, 1u, 0.f, 0u};
+                valid[u] = false;
+            }
+            q[u] = it[u].q;
+            if (!AT::kOne) view(A, q[u], Vb);
+            const QConst& V = AT::kOne ? static_cast<const QConst&>(cta().v) : static_cast<const QConst&>(Vb);
+            if (valid[u] && (depth_of(it[u].a) != V.LA || depth_of(it[u].b) != V.LB)) {
+                flag_bad(A, kBadLeaf);
+                valid[u] = false;
+            }
+            const unsigned sub = (unsigned)(vt & 3);
+            const unsigned la = it[u].a - (1u << V.LA), lb = it[u].b - (1u << V.LB);
+            const unsigned a0 = leaf_first(V.TA, V.LA, la), a1 = leaf_first(V.TA, V.LA, la + 1);
+            const unsigned b0 = leaf_first(V.TB, V.LB, lb), b1 = leaf_first(V.TB, V.LB, lb + 1);
+            ta[u] = a0 + (sub >> 1);
+            tb[u] = b0 + (sub & 1);
+            valid[u] = valid[u] && ta[u] < a1 && tb[u] < b1;
+            bool stop;
+            const float Ucur = load_Uq(A, q[u], &stop);
+            valid[u] = valid[u] && !stop;
+            if (KIND == 0) valid[u] = valid[u] && it[u].bound <= min_keep_threshold(Ucur, V.E_box);
+            else valid[u] = valid[u] && it[u].bound >= max_keep_threshold(Ucur, V.E_box);
+            if (valid[u] && sub == 0) bytes += 16ull + 36ull * ((a1 - a0) + (b1 - b0));
+            if (valid[u]) {
+                const Tri32 TA = load_tri(V.triA, ta[u]), TB = load_tri(V.triB, tb[u]);
+                valid[u] = tri_pair_may_hold<KIND>(V, TA, TB, Ucur);
+            }
         }
-        unsigned sub = (unsigned)(vt & 3);
-        unsigned la = it.a - (1u << V.LA), lb = it.b - (1u << V.LB);
-        unsigned a0 = leaf_first(V.TA, V.LA, la), a1 = leaf_first(V.TA, V.LA, la + 1);
-        unsigned b0 = leaf_first(V.TB, V.LB, lb), b1 = leaf_first(V.TB, V.LB, lb + 1);
-        unsigned ta = a0 + (sub >> 1), tb = b0 + (sub & 1);
-        valid = valid && ta < a1 && tb < b1;
-        bool stop;
-        float Ucur = load_Uq(A, q, &stop);
-        valid = valid && !stop;
-        if (KIND == 0) valid = valid && it.bound <= min_keep_threshold(Ucur, V.E_box);
-        else valid = valid && it.bound >= max_keep_threshold(Ucur, V.E_box);
-        if (valid && sub == 0) bytes += 16ull + 36ull * ((a1 - a0) + (b1 - b0));
-        if (valid) {
-            const Tri32 TA = load_tri(V.triA, ta), TB = load_tri(V.triB, tb);
-            valid = tri_pair_may_hold<KIND>(V, TA, TB, Ucur);
+        // queue the pairs that passed (one shared atomic per warp and slot);
+        // the list holds < kBlock entries between iterations, so it never
+        // overflows
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const unsigned m = __ballot_sync(kFull, valid[u]);
+            unsigned base = 0u;
+            if (lane == 0 && m) base = atomicAdd(&list_n, (unsigned)__popc(m));
+            base = __shfl_sync(kFull, base, 0);
+            if (valid[u]) list[base + __popc(m & lanemask_lt())] = make_uint4(ta[u], tb[u], q[u], 0u);
         }
-        // queue the pairs that passed (one shared atomic per warp); the list
-        // holds < kBlock entries between iterations, so it never overflows
-        const unsigned m = __ballot_sync(kFull, valid);
-        unsigned base = 0u;
-        if (lane == 0 && m) base = atomicAdd(&list_n, (unsigned)__popc(m));
-        base = __shfl_sync(kFull, base, 0);
-        if (valid) list[base + __popc(m & lanemask_lt())] = make_uint4(ta, tb, q, 0u);
         __syncthreads();
-        const unsigned n = list_n;
-        if (n >= (unsigned)kBlock) {
+        unsigned n = list_n;
+        while (n >= (unsigned)kBlock) {
             leaf_tight<KIND>(A, list + (n - kBlock), kBlock, pit, tripairs, bytes, false);
             __syncthreads();
-            if (threadIdx.x == 0) list_n = n - kBlock;
+            n -= kBlock;
+            if (threadIdx.x == 0) list_n = n;
         }
         if (pull) cta_merge_bound<KIND>(gw);
     }
@@ -1867,8 +1887,11 @@ __device__ bool refit_jobs(const AT& A, bool lead, unsigned& refits, bool* ran) 
 // query (nq == 1) or a batch; with the query count known at compile time
 // every single-query / batch branch of the inlined phases folds, so each
 // instantiation carries only its own code and register pressure.
+#ifndef GD_BATCH_CTAS
+#define GD_BATCH_CTAS 4
+#endif
 template <int KIND, bool FULL, bool ONE>
-__global__ void __launch_bounds__(kBlock, 2) k_query(KArgs Aparam) {
+__global__ void __launch_bounds__(kBlock, ONE ? 2 : GD_BATCH_CTAS) k_query(KArgs Aparam) {
     using AT = KArgsT<ONE>;
     const AT& A = static_cast<const AT&>(Aparam);
     unsigned long long pairs = 0, bytes = 0;
@@ -2261,17 +2284,20 @@ static const void* kind_kernel(int i) {
 }
 
 template <int KIND>
-static int occupancy_blocks() {
+static int occupancy_blocks(bool batch) {
     static bool configured = false;
     if (!configured) {
+        // a single query's CTAs need 2 x 22 KB of shared memory per SM; a
+        // batch's may take more CTAs per SM
         for (int i = 0; i < 3; ++i)
-            cudaFuncSetAttribute(kind_kernel<KIND>(i), cudaFuncAttributePreferredSharedMemoryCarveout, 25);
+            cudaFuncSetAttribute(kind_kernel<KIND>(i), cudaFuncAttributePreferredSharedMemoryCarveout, i == 0 ? 50 : 25);
         configured = true;
     }
-    // the instantiations use the same registers and shared memory per CTA;
-    // the launch takes the smallest occupancy so that every one fits
+    // a batch launch runs instantiation 0; a single query 1 or 2, which use
+    // the same registers and shared memory per CTA (the smaller occupancy of
+    // the two so that either fits)
     int nb = 1 << 30;
-    for (int i = 0; i < 3; ++i) {
+    for (int i = batch ? 0 : 1; i < (batch ? 1 : 3); ++i) {
         int n = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kind_kernel<KIND>(i), kBlock, 0);
         nb = n < nb ? n : nb;
@@ -2279,7 +2305,9 @@ static int occupancy_blocks() {
     return nb;
 }
 
-int query_max_blocks_per_sm(int kind) { return kind == 0 ? occupancy_blocks<0>() : occupancy_blocks<1>(); }
+int query_max_blocks_per_sm(int kind, bool batch) {
+    return kind == 0 ? occupancy_blocks<0>(batch) : occupancy_blocks<1>(batch);
+}
 
 static const void* query_kernel(int kind, const KArgs& args) {
     const int i = args.nq != 1 ? 0 : (args.ftree ? 2 : 1);
