@@ -29,6 +29,7 @@
 #include "gd_internal.cuh"
 #include "gd_launch.h"
 
+
 namespace gd {
 
 constexpr float kU = 5.9604645e-08f;    // 2^-24, unit roundoff of float32
@@ -549,18 +550,19 @@ __device__ __forceinline__ void tri_pair_bounds_tight(const AT& A, unsigned q, c
 // distance, widened upward, is below the running bound.  Triangles with long
 // thin shapes have boxes far larger than themselves, so most leaf pairs that
 // pass the box test fail this one at a tenth of the cost of the tight bounds.
+// Bw: B's three vertices already mapped into A's frame.
 template <int KIND>
-__device__ __forceinline__ bool tri_pair_may_hold(const QConst& V, const Tri32& TA, const Tri32& TB, float U) {
+__device__ __forceinline__ bool tri_pair_may_hold_mapped(float E_box, const Tri32& TA, const V3<float>* Bw, float U) {
     const V3<float> o = TA.v[0];
     V3<float> Al[3], Bl[3];
     float X = 0.f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         Al[k] = TA.v[k] - o;
-        Bl[k] = map32(V.X, TB.v[k].x, TB.v[k].y, TB.v[k].z) - o;
+        Bl[k] = Bw[k] - o;
         X = fmaxf(X, fmaxf(max_abs3(Al[k]), max_abs3(Bl[k])));
     }
-    const float E = __fadd_ru(V.E_box, __fmul_ru(256.0f * kU * 1.001f, X));
+    const float E = __fadd_ru(E_box, __fmul_ru(256.0f * kU * 1.001f, X));
     if (KIND == 0) {
         const V3<float> n = (Al[0] + Al[1] + Al[2]) - (Bl[0] + Bl[1] + Bl[2]);
         const float nn = dot(n, n);
@@ -585,6 +587,15 @@ __device__ __forceinline__ bool tri_pair_may_hold(const QConst& V, const Tri32& 
             }
         return upper_from_sq(m2, E) >= U;
     }
+}
+
+// The same test with B's triangle as stored (mapped into A's frame here).
+template <int KIND>
+__device__ __forceinline__ bool tri_pair_may_hold(const QConst& V, const Tri32& TA, const Tri32& TB, float U) {
+    V3<float> Bw[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Bw[k] = map32(V.X, TB.v[k].x, TB.v[k].y, TB.v[k].z);
+    return tri_pair_may_hold_mapped<KIND>(V.E_box, TA, Bw, U);
 }
 
 // ------------------------------------------------------------- pair bounds
@@ -1329,6 +1340,18 @@ __device__ __noinline__ void leaf_tight(const AT& A, const uint4* list, unsigned
     }
 }
 
+// The CTA's list of triangle pairs waiting for their tight bounds (both
+// forms of the leaf phase use it; it holds 3 kBlock entries).
+__device__ __forceinline__ uint4* leaf_list() {
+    __shared__ uint4 l[3 * kBlock];
+    return l;
+}
+
+__device__ __forceinline__ unsigned& leaf_list_n() {
+    __shared__ unsigned n;
+    return n;
+}
+
 // The leaf pairs' triangle pairs, 4 slots per leaf pair (<= 2 x 2 triangles),
 // in two stages per CTA: every thread takes one slot, loads its two
 // triangles and runs the cheap float32 test; the pairs that pass go to a
@@ -1337,12 +1360,12 @@ __device__ __noinline__ void leaf_tight(const AT& A, const uint4* list, unsigned
 // per cent of the pairs pass the cheap test, so bounding them densely keeps
 // whole warps on the expensive part instead of one lane in each.
 template <int KIND, class AT>
-__device__ void leaf_phase(const AT& A, unsigned nleaf, unsigned& tripairs, unsigned long long& bytes) {
+__device__ void leaf_phase_slots(const AT& A, unsigned nleaf, unsigned& tripairs, unsigned long long& bytes) {
     // slots per thread and iteration (two, measured for single queries: the
     // leaf phase took 17.2 -> 18.3 us on the rings; one kept)
     constexpr int U = 1;
-    __shared__ uint4 list[(1 + U) * kBlock];
-    __shared__ unsigned list_n;
+    uint4* list = leaf_list();
+    unsigned& list_n = leaf_list_n();
     const unsigned long long total = (unsigned long long)nleaf * 4ull;
     const unsigned long long gstride = (unsigned long long)work_ctas(A) * blockDim.x;
     const bool pull = AT::kOne && threadIdx.x == 0;
@@ -1433,6 +1456,120 @@ __device__ void leaf_phase(const AT& A, unsigned nleaf, unsigned& tripairs, unsi
     const unsigned n = list_n;
     if (n > 0u) leaf_tight<KIND>(A, list, n, pit, tripairs, bytes, false);
     __syncthreads();
+}
+
+// The same two stages with one thread per leaf pair: it loads the pair's
+// (up to) 2 + 2 triangles, maps each of B's into A's frame once, and runs the
+// cheap test on its (up to) four triangle pairs.  The passing pairs reach the
+// list in two pushes of two between CTA barriers, so that it holds fewer
+// than kBlock + 2 kBlock entries before a drain.
+template <int KIND, class AT>
+__device__ void leaf_phase_pairs(const AT& A, unsigned nleaf, unsigned& tripairs, unsigned long long& bytes) {
+    uint4* list = leaf_list();
+    unsigned& list_n = leaf_list_n();
+    const unsigned long long gstride = (unsigned long long)work_ctas(A) * blockDim.x;
+    const bool pull = AT::kOne && threadIdx.x == 0;
+    const int lane = threadIdx.x & 31;
+    QView Vb;
+    int pit = 0;
+    if (threadIdx.x == 0) list_n = 0u;
+    for (unsigned long long cbase = (unsigned long long)blockIdx.x * blockDim.x; cbase < nleaf; cbase += gstride) {
+        if (__syncthreads_or(AT::kOne && (((volatile CtaState&)cta()).stat & kStatStop) != 0u)) break;
+        unsigned long long gw = 0;
+        if (pull) gw = ld_relaxed64(reinterpret_cast<const unsigned long long*>(&A.qs[0].U));
+        const unsigned long long vt = cbase + threadIdx.x;
+        bool valid = vt < nleaf;
+        Item it = Item{1u, 1u, 0.f, 0u};
+        if (valid) {
+            float4 raw = __ldcg(reinterpret_cast<const float4*>(A.leafq + vt));
+            it = *reinterpret_cast<Item*>(&raw);
+            if (!item_ok(A, it)) {
+                flag_bad(A, kBadLeaf);
+                it = Item{1u, 1u, 0.f, 0u};
+                valid = false;
+            }
+        }
+        const unsigned q = it.q;
+        if (!AT::kOne) view(A, q, Vb);
+        const QConst& V = AT::kOne ? static_cast<const QConst&>(cta().v) : static_cast<const QConst&>(Vb);
+        if (valid && (depth_of(it.a) != V.LA || depth_of(it.b) != V.LB)) {
+            flag_bad(A, kBadLeaf);
+            valid = false;
+        }
+        const unsigned la = it.a - (1u << V.LA), lb = it.b - (1u << V.LB);
+        const unsigned a0 = leaf_first(V.TA, V.LA, la), a1 = leaf_first(V.TA, V.LA, la + 1);
+        const unsigned b0 = leaf_first(V.TB, V.LB, lb), b1 = leaf_first(V.TB, V.LB, lb + 1);
+        valid = valid && a0 < a1 && b0 < b1;
+        bool stop;
+        const float Ucur = load_Uq(A, q, &stop);
+        valid = valid && !stop;
+        if (KIND == 0) valid = valid && it.bound <= min_keep_threshold(Ucur, V.E_box);
+        else valid = valid && it.bound >= max_keep_threshold(Ucur, V.E_box);
+        // bit 2i + j: triangle pair (a0 + i, b0 + j) passed the cheap test
+        unsigned m = 0u;
+        if (valid) {
+            bytes += 16ull + 36ull * ((a1 - a0) + (b1 - b0));
+            const bool a2 = a1 - a0 >= 2u, b2 = b1 - b0 >= 2u;
+            const Tri32 TA0 = load_tri(V.triA, a0), TA1 = load_tri(V.triA, a2 ? a0 + 1u : a0);
+            const Tri32 TB0 = load_tri(V.triB, b0), TB1 = load_tri(V.triB, b2 ? b0 + 1u : b0);
+            // B's triangles mapped once each, one at a time
+            V3<float> Bw[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) Bw[k] = map32(V.X, TB0.v[k].x, TB0.v[k].y, TB0.v[k].z);
+            if (tri_pair_may_hold_mapped<KIND>(V.E_box, TA0, Bw, Ucur)) m |= 1u;
+            if (a2 && tri_pair_may_hold_mapped<KIND>(V.E_box, TA1, Bw, Ucur)) m |= 4u;
+            if (b2) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) Bw[k] = map32(V.X, TB1.v[k].x, TB1.v[k].y, TB1.v[k].z);
+                if (tri_pair_may_hold_mapped<KIND>(V.E_box, TA0, Bw, Ucur)) m |= 2u;
+                if (a2 && tri_pair_may_hold_mapped<KIND>(V.E_box, TA1, Bw, Ucur)) m |= 8u;
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+            for (int r = 2 * h; r < 2 * h + 2; ++r) {
+                const bool p = (m >> r) & 1u;
+                const unsigned mb = __ballot_sync(kFull, p);
+                unsigned base = 0u;
+                if (lane == 0 && mb) base = atomicAdd(&list_n, (unsigned)__popc(mb));
+                base = __shfl_sync(kFull, base, 0);
+                if (p) list[base + __popc(mb & lanemask_lt())] = make_uint4(a0 + (r >> 1), b0 + (r & 1), q, 0u);
+            }
+            __syncthreads();
+            unsigned n = list_n;
+            if (n >= (unsigned)kBlock) {
+                while (n >= (unsigned)kBlock) {
+                    leaf_tight<KIND>(A, list + (n - kBlock), kBlock, pit, tripairs, bytes, false);
+                    __syncthreads();
+                    n -= kBlock;
+                }
+                if (threadIdx.x == 0) list_n = n;
+            }
+            // every thread has read list_n before the next push changes it
+            __syncthreads();
+        }
+        if (pull) cta_merge_bound<KIND>(gw);
+    }
+    __syncthreads();
+    const unsigned n = list_n;
+    if (n > 0u) leaf_tight<KIND>(A, list, n, pit, tripairs, bytes, false);
+    __syncthreads();
+}
+
+// The leaf phase.  A batch whose queue needs more than one pass of slots (4
+// slots per leaf pair, one per thread) runs the form with a thread per leaf
+// pair, which loads each triangle and maps each of B's once instead of twice
+// (gear batch of 512 queries: 94 -> 75 ms).  A single query keeps the slot
+// form, the shortest chain per thread: the per-pair form in its kernel, even
+// out of line and taken only for long queues, cost the rings and icosphere
+// queries 2-4 % (registers of the rest of the kernel) for 3 % on the gears'
+// plain calls.
+template <int KIND, class AT>
+__device__ void leaf_phase(const AT& A, unsigned nleaf, unsigned& tripairs, unsigned long long& bytes) {
+    const unsigned long long threads = (unsigned long long)work_ctas(A) * blockDim.x;
+    if (!AT::kOne && 4ull * nleaf > threads) leaf_phase_pairs<KIND>(A, nleaf, tripairs, bytes);
+    else leaf_phase_slots<KIND>(A, nleaf, tripairs, bytes);
 }
 
 // ------------------------------------------------------------- phases 4-6
