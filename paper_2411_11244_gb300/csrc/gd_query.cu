@@ -339,6 +339,24 @@ __device__ __forceinline__ void warp_bound_update(const AT& A, bool have, unsign
     }
 }
 
+// The CTA's ranges in two queues for the counts its warps added to the
+// shared counters of parity p (every thread calls; threads 0 and 32 take one
+// global atomic each and clear the other parity for the next iteration).
+__device__ __forceinline__ void cta_reserve(int p, unsigned* cnt0, unsigned* cnt1) {
+    CtaState& c = cta();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned n = c.cnt[p][0];
+        c.base[0] = n ? atomicAdd(cnt0, n) : 0u;
+        c.cnt[p ^ 1][0] = 0u;
+    } else if (threadIdx.x == 32) {
+        const unsigned n = c.cnt[p][1];
+        c.base[1] = n ? atomicAdd(cnt1, n) : 0u;
+        c.cnt[p ^ 1][1] = 0u;
+    }
+    __syncthreads();
+}
+
 // Append the entries of one CTA-wide iteration to two queues (want0 -> buf0,
 // want1 -> buf1) with one global atomic per queue and CTA: the warps count
 // into shared memory, threads 0 and 32 reserve the CTA's ranges.  Every
@@ -358,17 +376,7 @@ __device__ __forceinline__ bool cta_push2(int it, const E& v, bool want0, E* buf
     }
     o0 = __shfl_sync(kFull, o0, 0);
     o1 = __shfl_sync(kFull, o1, 0);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned n = c.cnt[p][0];
-        c.base[0] = n ? atomicAdd(cnt0, n) : 0u;
-        c.cnt[p ^ 1][0] = 0u;
-    } else if (threadIdx.x == 32) {
-        const unsigned n = c.cnt[p][1];
-        c.base[1] = n ? atomicAdd(cnt1, n) : 0u;
-        c.cnt[p ^ 1][1] = 0u;
-    }
-    __syncthreads();
+    cta_reserve(p, cnt0, cnt1);
     const unsigned lt = lanemask_lt();
     bool ok = true;
     if (want0) {
@@ -380,6 +388,49 @@ __device__ __forceinline__ bool cta_push2(int it, const E& v, bool want0, E* buf
         const unsigned idx = c.base[1] + o1 + __popc(m1 & lt);
         if (idx < cap1) __stcg(reinterpret_cast<float4*>(buf1 + idx), *reinterpret_cast<const float4*>(&v));
         else ok = false;
+    }
+    return ok;
+}
+
+// The same for up to four entries per thread: v[j] for the bits j of m, all
+// to buf1 if to1, else all to buf0, in the order of j.  The warp's offsets
+// come from the bits of the per-thread counts (three ballots per queue).
+template <class E>
+__device__ __forceinline__ bool cta_push4(int it, const E* v, unsigned m, bool to1, E* buf0, unsigned* cnt0,
+                                          unsigned cap0, E* buf1, unsigned* cnt1, unsigned cap1) {
+    CtaState& c = cta();
+    const int lane = threadIdx.x & 31, p = it & 1;
+    const unsigned k = (unsigned)__popc(m);
+    const unsigned k0 = to1 ? 0u : k, k1 = to1 ? k : 0u;
+    const unsigned lt = lanemask_lt();
+    unsigned pre0 = 0u, tot0 = 0u, pre1 = 0u, tot1 = 0u;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        const unsigned b0 = __ballot_sync(kFull, (k0 >> b) & 1u), b1 = __ballot_sync(kFull, (k1 >> b) & 1u);
+        pre0 += (unsigned)__popc(b0 & lt) << b;
+        tot0 += (unsigned)__popc(b0) << b;
+        pre1 += (unsigned)__popc(b1 & lt) << b;
+        tot1 += (unsigned)__popc(b1) << b;
+    }
+    unsigned o0 = 0u, o1 = 0u;
+    if (lane == 0) {
+        if (tot0) o0 = atomicAdd(&c.cnt[p][0], tot0);
+        if (tot1) o1 = atomicAdd(&c.cnt[p][1], tot1);
+    }
+    o0 = __shfl_sync(kFull, o0, 0);
+    o1 = __shfl_sync(kFull, o1, 0);
+    cta_reserve(p, cnt0, cnt1);
+    E* buf = to1 ? buf1 : buf0;
+    const unsigned cap = to1 ? cap1 : cap0;
+    unsigned idx = to1 ? c.base[1] + o1 + pre1 : c.base[0] + o0 + pre0;
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if ((m >> j) & 1u) {
+            if (idx < cap) __stcg(reinterpret_cast<float4*>(buf + idx), *reinterpret_cast<const float4*>(&v[j]));
+            else ok = false;
+            ++idx;
+        }
     }
     return ok;
 }
@@ -1250,6 +1301,133 @@ __device__ void expand_level(const AT& A, int level, unsigned n, int s, unsigned
         if (survive && !leafpair && dBc == V.dR) claim_root(A, V, q, ib);
         // remaining depth of the entries pushed to the next front
         unsigned rem = (survive && !leafpair) ? (unsigned)(remA - kA + remB - kB) : 0u;
+        rem = __reduce_max_sync(kFull, rem);
+        if (lane == 0 && rem > 0) atomicMax(&cta().rem, rem);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned r = cta().rem;
+        if (r > 0) atomicMax(out_rem, r);
+    }
+}
+
+// A batch level of one tree level each (s = 2) whose front outgrows the
+// grid: one thread per front entry and its (up to) four child pairs, so that
+// the entry's load, its query's view and running bound, and the warp's
+// collective steps (bound update, queue shares, CTA append) run once per
+// entry instead of once per child pair.  Same bounds, survivors and queue
+// contents (up to order) as expand_level.
+template <int KIND, class AT>
+__device__ void expand_level_entries(const AT& A, int level, unsigned n, unsigned long long& pairs,
+                                     unsigned long long& bytes) {
+    constexpr int s = 2;
+    const Item* in = (level & 1) ? A.front1 : A.front0;
+    Item* out = (level & 1) ? A.front0 : A.front1;
+    unsigned* out_cnt = A.ctr + kCtrCnt + (level + 1) % 3;
+    unsigned* out_rem = A.ctr + kCtrRem + (level + 1) % 3;
+    unsigned* leaf_cnt = A.ctr + kCtrLeaf;
+    const unsigned long long gstride = (unsigned long long)work_ctas(A) * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    QView V;
+    int iter = 0;
+    for (unsigned long long cbase = (unsigned long long)blockIdx.x * blockDim.x; cbase < n;
+         cbase += gstride, ++iter) {
+        const unsigned long long vt = cbase + threadIdx.x;
+        bool valid = vt < n;
+        Item it = {1u, 1u, 0.f, 0u};
+        if (valid) {
+            float4 raw = __ldcg(reinterpret_cast<const float4*>(in + vt));
+            it = *reinterpret_cast<Item*>(&raw);
+            if (!item_ok(A, it)) {
+                flag_bad(A, kBadFront);
+                it = Item{1u, 1u, 0.f, 0u};
+                valid = false;
+            }
+        }
+        const unsigned q = it.q;
+        view(A, q, V);
+        const int dA = depth_of(it.a), dB = depth_of(it.b);
+        int remA = V.LA - dA, remB = V.LB - dB;
+        if (remA < 0 || remB < 0) {
+            if (valid) flag_bad(A, kBadFront);
+            valid = false;
+            remA = max(remA, 0);
+            remB = max(remB, 0);
+        }
+        int kA = min((s + 1) >> 1, remA);
+        int kB = min(s - kA, remB);
+        if (V.dR >= 0 && dB < V.dR) kB = min(kB, V.dR - dB);  // stop on the refit roots
+        kA = min(s - kB, remA);
+        bool stop;
+        const float Ucur = load_Uq(A, q, &stop);
+        valid = valid && !stop;
+        if (KIND == 0) valid = valid && it.bound <= min_keep_threshold(Ucur, V.E_box);
+        else valid = valid && it.bound >= max_keep_threshold(Ucur, V.E_box);
+        if (valid) bytes += 16ull + 24ull * ((1ull << kA) + (1ull << kB));
+        const int dBc = dB + kB;
+        const bool leafpair = (kA == remA) && (kB == remB);
+        const unsigned nchild = valid ? 1u << (kA + kB) : 0u;
+        // the children (child c: A's child c >> kB, B's child c & (2^kB - 1)),
+        // their survivors (bit c of sm) and the best enhanced bound among them
+        Item o[4];
+        unsigned sm = 0u;
+        unsigned best = KIND == 0 ? 0xffffffffu : 0u;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const unsigned ia = (it.a << kA) | ((unsigned)c >> kB);
+            const unsigned ib = (it.b << kB) | ((unsigned)c & ((1u << kB) - 1u));
+            o[c] = Item{ia, ib, 0.f, q};
+            if ((unsigned)c < nchild) {
+                ++pairs;
+                bool survive = false;
+                unsigned newU = KIND == 0 ? 0xffffffffu : 0u, key;
+                o[c].bound = pair_bounds<KIND, false>(A, V, ia, ib, dBc, Ucur, &survive, &newU, &key);
+                if (survive) {
+                    sm |= 1u << c;
+                    best = KIND == 0 ? min(best, newU) : max(best, newU);
+                }
+            }
+        }
+        warp_bound_update<KIND>(A, sm != 0u, q, best);
+        if (A.q_budget) {
+            // the queue shares (as in expand_level), one atomic per query
+            // among the warp's lanes with survivors
+            bool pend = sm != 0u;
+            for (;;) {
+                const unsigned pm = __ballot_sync(kFull, pend);
+                if (!pm) break;
+                const int leader = __ffs(pm) - 1;
+                const unsigned lq = __shfl_sync(kFull, q, leader);
+                const bool mine = pend && q == lq;
+                const unsigned tot = __reduce_add_sync(kFull, mine ? (unsigned)__popc(sm) : 0u);
+                unsigned over = 0u;
+                if (lane == leader) {
+                    const unsigned old = atomicAdd(&A.qs[lq].pushed[(level + 1) & 1], tot);
+                    if (old + tot > A.q_budget) {
+                        const unsigned pold = atomicAdd(A.ctr + (((level + 1) & 1) ? kCtrPool1 : kCtrPool0), tot);
+                        if (pold + tot > A.q_pool) {
+                            over = 1u;
+                            atomicOr(&A.qs[lq].status, kStatEvict);
+                        }
+                    }
+                }
+                over = __shfl_sync(kFull, over, leader);
+                if (mine) {
+                    pend = false;
+                    if (over) sm = 0u;
+                }
+            }
+        }
+        if (!cta_push4(iter, o, sm, leafpair, out, out_cnt, A.cap_front, A.leafq, leaf_cnt, A.cap_leaf))
+            mark_overflow(A, q);
+        bytes += 16ull * (unsigned)__popc(sm);
+        if (!leafpair && dBc == V.dR) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if ((sm >> c) & 1u) claim_root(A, V, q, o[c].b);
+        }
+        // remaining depth of the entries pushed to the next front
+        unsigned rem = (sm != 0u && !leafpair) ? (unsigned)(remA - kA + remB - kB) : 0u;
         rem = __reduce_max_sync(kFull, rem);
         if (lane == 0 && rem > 0) atomicMax(&cta().rem, rem);
     }
@@ -2219,7 +2397,12 @@ levels:
         }
         if (A.q_budget)  // the counters of this level's pushes are those of level + 2
             for (int q = (int)gfirst; q < A.nq; q += (int)gstride) A.qs[q].pushed[level & 1] = 0u;
-        expand_level<KIND, FULL>(A, level, n, s, pairs, bytes);
+        // a batch front of more than twice the grid's threads at one tree
+        // level each: a thread per entry
+        if (!AT::kOne && s == 2 && (unsigned long long)n > 2ull * gstride)
+            expand_level_entries<KIND>(A, level, n, pairs, bytes);
+        else
+            expand_level<KIND, FULL>(A, level, n, s, pairs, bytes);
         if (!sync(A)) goto done;
         if (lead) {
             unsigned long long now = globaltimer();
