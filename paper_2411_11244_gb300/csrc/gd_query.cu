@@ -593,17 +593,39 @@ __device__ __forceinline__ void tri_pair_bounds_tight(const AT& A, unsigned q, c
     tri_bounds_core<KIND>(Al, Bl, __fadd_ru(Edf, __fmul_ru(256.0f * kU * 1.001f, X)), lo, up);
 }
 
+// Whether the plane of triangle P separates it from triangle Q by more than
+// the running bound U: the separation of the two along P's normal (any axis
+// gives a lower bound of their distance), widened as in tri_bounds_core.
+__device__ __forceinline__ bool plane_apart(const V3<float>* P, const V3<float>* Q, float E, float U) {
+    const V3<float> n = cross(P[1] - P[0], P[2] - P[0]);
+    const float nn = dot(n, n);
+    if (!(nn > 0.f)) return false;
+    float pmin = FLT_MAX, pmax = -FLT_MAX, qmin = FLT_MAX, qmax = -FLT_MAX;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float p = dot(n, P[k]), q = dot(n, Q[k]);
+        pmin = fminf(pmin, p);
+        pmax = fmaxf(pmax, p);
+        qmin = fminf(qmin, q);
+        qmax = fmaxf(qmax, q);
+    }
+    const float sep = fmaxf(qmin - pmax, pmin - qmax);
+    return sep > 0.f && lower_from_dist(sep / sqrtf(nn), E) > U;
+}
+
 // Cheap float32 test run before the tight bounds of a leaf's triangle pair:
-// false only if the pair cannot hold the extreme.  Min kind: the separation of
-// the two triangles along the line between their centroids (a valid lower
-// bound of their distance for any direction, widened as in tri_bounds_core)
-// exceeds the running bound U.  Max kind: the largest float32 vertex-pair
-// distance, widened upward, is below the running bound.  Triangles with long
-// thin shapes have boxes far larger than themselves, so most leaf pairs that
-// pass the box test fail this one at a tenth of the cost of the tight bounds.
+// false only if the pair cannot hold the extreme.  Min kind: the separation
+// of the two triangles along the line between their centroids, or (planes)
+// along the normal of either one's plane (along any direction a valid lower
+// bound of their distance, widened as in tri_bounds_core), exceeds the
+// running bound U.  Max kind: the largest float32 vertex-pair distance, widened upward, is
+// below the running bound.  Triangles with long thin shapes have boxes far
+// larger than themselves, so most leaf pairs that pass the box test fail
+// this one at a tenth of the cost of the tight bounds.
 // Bw: B's three vertices already mapped into A's frame.
 template <int KIND>
-__device__ __forceinline__ bool tri_pair_may_hold_mapped(float E_box, const Tri32& TA, const V3<float>* Bw, float U) {
+__device__ __forceinline__ bool tri_pair_may_hold_mapped(float E_box, const Tri32& TA, const V3<float>* Bw, float U,
+                                                         bool planes) {
     const V3<float> o = TA.v[0];
     V3<float> Al[3], Bl[3];
     float X = 0.f;
@@ -625,8 +647,9 @@ __device__ __forceinline__ bool tri_pair_may_hold_mapped(float E_box, const Tri3
             bmax = fmaxf(bmax, dot(n, Bl[k]));
         }
         const float sep = amin - bmax;
-        if (!(sep > 0.f)) return true;
-        return lower_from_dist(sep / sqrtf(nn), E) <= U;
+        if (sep > 0.f && lower_from_dist(sep / sqrtf(nn), E) > U) return false;
+        // the pairs left: the planes of A and of B as the separating axes
+        return !(planes && (plane_apart(Al, Bl, E, U) || plane_apart(Bl, Al, E, U)));
     } else {
         float m2 = 0.f;
 #pragma unroll
@@ -642,11 +665,12 @@ __device__ __forceinline__ bool tri_pair_may_hold_mapped(float E_box, const Tri3
 
 // The same test with B's triangle as stored (mapped into A's frame here).
 template <int KIND>
-__device__ __forceinline__ bool tri_pair_may_hold(const QConst& V, const Tri32& TA, const Tri32& TB, float U) {
+__device__ __forceinline__ bool tri_pair_may_hold(const QConst& V, const Tri32& TA, const Tri32& TB, float U,
+                                                  bool planes) {
     V3<float> Bw[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) Bw[k] = map32(V.X, TB.v[k].x, TB.v[k].y, TB.v[k].z);
-    return tri_pair_may_hold_mapped<KIND>(V.E_box, TA, Bw, U);
+    return tri_pair_may_hold_mapped<KIND>(V.E_box, TA, Bw, U, planes);
 }
 
 // ------------------------------------------------------------- pair bounds
@@ -1478,7 +1502,7 @@ __device__ __noinline__ void leaf_tight(const AT& A, const uint4* list, unsigned
         if (!stop) {
             const Tri32 TA = load_tri(V.triA, ta), TB = load_tri(V.triB, tb);
             // the bound may have moved since the pair was queued: test again
-            if (dry || tri_pair_may_hold<KIND>(V, TA, TB, Ucur)) {
+            if (dry || tri_pair_may_hold<KIND>(V, TA, TB, Ucur, !AT::kOne)) {
                 ++tripairs;
                 float lo, up;
                 tri_pair_bounds_tight<KIND>(A, q, V, TA, TB, &lo, &up);
@@ -1548,6 +1572,9 @@ __device__ void leaf_phase_slots(const AT& A, unsigned nleaf, unsigned& tripairs
     const unsigned long long gstride = (unsigned long long)work_ctas(A) * blockDim.x;
     const bool pull = AT::kOne && threadIdx.x == 0;
     const int lane = threadIdx.x & 31;
+    // the plane axes of the cheap test pay off on queues longer than one pass
+    // (a rings query, one pass, lost 1.8 us of leaf phase with them)
+    const bool planes = total > gstride;
     // the query's constants: a single query reads the CTA's shared copy where
     // it uses them (no per-thread copy held through the slot loop); a batch
     // keeps a per-thread view of the last query it met
@@ -1606,7 +1633,7 @@ __device__ void leaf_phase_slots(const AT& A, unsigned nleaf, unsigned& tripairs
             if (valid[u] && sub == 0) bytes += 16ull + 36ull * ((a1 - a0) + (b1 - b0));
             if (valid[u]) {
                 const Tri32 TA = load_tri(V.triA, ta[u]), TB = load_tri(V.triB, tb[u]);
-                valid[u] = tri_pair_may_hold<KIND>(V, TA, TB, Ucur);
+                valid[u] = tri_pair_may_hold<KIND>(V, TA, TB, Ucur, planes);
             }
         }
         // queue the pairs that passed (one shared atomic per warp and slot);
@@ -1694,13 +1721,13 @@ __device__ void leaf_phase_pairs(const AT& A, unsigned nleaf, unsigned& tripairs
             V3<float> Bw[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) Bw[k] = map32(V.X, TB0.v[k].x, TB0.v[k].y, TB0.v[k].z);
-            if (tri_pair_may_hold_mapped<KIND>(V.E_box, TA0, Bw, Ucur)) m |= 1u;
-            if (a2 && tri_pair_may_hold_mapped<KIND>(V.E_box, TA1, Bw, Ucur)) m |= 4u;
+            if (tri_pair_may_hold_mapped<KIND>(V.E_box, TA0, Bw, Ucur, true)) m |= 1u;
+            if (a2 && tri_pair_may_hold_mapped<KIND>(V.E_box, TA1, Bw, Ucur, true)) m |= 4u;
             if (b2) {
 #pragma unroll
                 for (int k = 0; k < 3; ++k) Bw[k] = map32(V.X, TB1.v[k].x, TB1.v[k].y, TB1.v[k].z);
-                if (tri_pair_may_hold_mapped<KIND>(V.E_box, TA0, Bw, Ucur)) m |= 2u;
-                if (a2 && tri_pair_may_hold_mapped<KIND>(V.E_box, TA1, Bw, Ucur)) m |= 8u;
+                if (tri_pair_may_hold_mapped<KIND>(V.E_box, TA0, Bw, Ucur, true)) m |= 2u;
+                if (a2 && tri_pair_may_hold_mapped<KIND>(V.E_box, TA1, Bw, Ucur, true)) m |= 8u;
             }
         }
 #pragma unroll
