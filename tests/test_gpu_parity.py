@@ -1086,6 +1086,35 @@ def test_gears_full_size_batch_sample(G, ctx, oracle_mod):
         G.gd_mesh_destroy(mb)
 
 
+def test_gears_batch_forms_and_plain_calls(G, ctx, oracle_mod):
+    """64 gear transforms (min) in one batch launch: its widest levels hold
+    more than twice the grid's threads at one tree level each, so they run a
+    thread per front entry, and its leaf queue more than a quarter of them,
+    so the leaf phase runs a thread per leaf pair.  8 of the answers against
+    the oracle, and the same 8 transforms as plain single-query calls (min and
+    max), whose long leaf queues take the plane axes of the cheap test."""
+    A, B, xa, xbs = synth.config_gears(64)
+    idx = list(range(3, 64, 8))
+    ma, mb = _mesh(G, ctx, A), _mesh(G, ctx, B)
+    try:
+        out = G.gd_batch_query(ctx, [(ma, mb, xa, xb, G.GD_MIN) for xb in xbs])
+        st = G.gd_get_stats(ctx)
+        threads = st["blocks"] * 256
+        assert any(f > 2 * threads and sl == 2 for f, sl in zip(st["front"], st["slots"])), st["front"]
+        assert 4 * st["leaf_pairs"] > threads, st["leaf_pairs"]
+        bA, bB = oracle_mod.Bvh(A), oracle_mod.Bvh(B)
+        for kind, fn in (("min", G.gd_min_distance), ("max", G.gd_max_distance)):
+            refs = oracle_mod.bvh_query_batch(bA, xa, bB, [xbs[i] for i in idx], kind)
+            for k, i in enumerate(idx):
+                diag = oracle_mod.diag(A, xa, B, xbs[i])
+                if kind == "min":
+                    check(out[i], A, xa, B, xbs[i], kind, refs[k], diag, oracle_mod)
+                check(fn(ctx, ma, mb, xa, xbs[i]), A, xa, B, xbs[i], kind, refs[k], diag, oracle_mod)
+    finally:
+        G.gd_mesh_destroy(ma)
+        G.gd_mesh_destroy(mb)
+
+
 def test_icospheres_full_size_min_max(G, ctx, oracle_mod):
     """Two 1.31 M-triangle noisy spheres at a gap of 1e-5 x diag, min and max."""
     A, B, xa, xb = synth.config_icospheres(level=8)
