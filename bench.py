@@ -682,7 +682,7 @@ def bench_points(G, ctx, ma, n=1 << 20, reps=3):
     }
 
 
-def bench_served(G, ctx, rates=(1000, 3000, 10000, 30000, 100000), n_req=1500, seed=0):
+def bench_served(G, ctx, rates=(1000, 3000, 10000, 30000, 100000), n_req=3000, seed=0):
     """A pool of 64 meshes (tori, geodesic spheres, gears; 1e3..4e6 triangles,
     BVHs resident) and a stream of random mesh pairs and transforms arriving
     as a Poisson process of rate lambda.  Served: gd_serve_submit/drain with
