@@ -877,8 +877,8 @@ template <int KIND>
 __device__ __noinline__ double refine_pair_warp(const QState& s, unsigned ta, unsigned tb, V3<double>* P,
                                                 V3<double>* Q, int* ida, int* idb);
 template <int KIND>
-__device__ __noinline__ double refine_pair_cta(const QState& s, unsigned ta, unsigned tb, V3<double>* P,
-                                               V3<double>* Q, int* ida, int* idb);
+__device__ __noinline__ double refine_pair_cta(const QState& s, const float4* triA, const float4* triB, unsigned ta,
+                                               unsigned tb, V3<double>* P, V3<double>* Q, int* ida, int* idb);
 template <int KIND, class AT>
 __device__ __noinline__ void leaf_tight(const AT& A, const uint4* list, unsigned n, int& pit, unsigned& tripairs,
                                         unsigned long long& bytes, bool dry);
@@ -1062,7 +1062,7 @@ __device__ void bg_probe_cta(const AT& A) {
     leaf_tight<KIND>(A, dry_list, 1u, pit, tp, by, true);
     V3<double> P, Q;
     int ia, ib;
-    const double d = refine_pair_cta<KIND>(A.qs[0], 0u, 0u, &P, &Q, &ia, &ib);
+    const double d = refine_pair_cta<KIND>(A.qs[0], A.qs[0].A->tri, A.qs[0].B->tri, 0u, 0u, &P, &Q, &ia, &ib);
     if (by == 7ull && d == -1.0) atomicAdd(&A.stats->probes, 0u);  // keeps the dry runs live
 }
 
@@ -1908,13 +1908,13 @@ __device__ __noinline__ double refine_pair_warp(const QState& s, unsigned ta, un
 // thread of the CTA calls it; the result (return value, P, Q) is valid in
 // warp 0, *ida and *idb on every thread.
 template <int KIND>
-__device__ __noinline__ double refine_pair_cta(const QState& s, unsigned ta, unsigned tb, V3<double>* P,
-                                               V3<double>* Q, int* ida, int* idb) {
+__device__ __noinline__ double refine_pair_cta(const QState& s, const float4* triA, const float4* triB, unsigned ta,
+                                               unsigned tb, V3<double>* P, V3<double>* Q, int* ida, int* idb) {
     __shared__ double s_d2[3];
     __shared__ int s_f[3];
     __shared__ double s_pq[3][6];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    Tri32 TA = load_tri(s.A->tri, ta), TB = load_tri(s.B->tri, tb);
+    Tri32 TA = load_tri(triA, ta), TB = load_tri(triB, tb);
     *ida = TA.id;
     *idb = TB.id;
     __syncthreads();  // the shared results of a previous pair have been read
@@ -2025,13 +2025,20 @@ __device__ void refine_phase_cta(const AT& A, unsigned ncand, unsigned& refined,
             float4 raw = __ldcg(reinterpret_cast<const float4*>(A.cand + i));
             const Cand c = *reinterpret_cast<Cand*>(&raw);
             bool keep = false;
-            if (c.q >= (unsigned)A.nq || c.ta >= (unsigned)A.qs[c.q < (unsigned)A.nq ? c.q : 0].A->T ||
-                c.tb >= (unsigned)A.qs[c.q < (unsigned)A.nq ? c.q : 0].B->T) {
+            // a single query checks against the CTA's copies of its constants
+            // and status (refreshed at the barrier before this phase), not
+            // through dependent global loads
+            const bool bad = AT::kOne ? (c.q != 0u || c.ta >= (unsigned long long)cta().v.TA ||
+                                         c.tb >= (unsigned long long)cta().v.TB)
+                                      : (c.q >= (unsigned)A.nq ||
+                                         c.ta >= (unsigned)A.qs[c.q < (unsigned)A.nq ? c.q : 0].A->T ||
+                                         c.tb >= (unsigned)A.qs[c.q < (unsigned)A.nq ? c.q : 0].B->T);
+            if (bad) {
                 flag_bad(A, kBadCand);
             } else {
                 bool stop;
                 const float U = load_Uq(A, c.q, &stop);
-                const unsigned st = ld_relaxed(&A.qs[c.q].status);
+                const unsigned st = AT::kOne ? ((volatile CtaState&)cta()).stat : ld_relaxed(&A.qs[c.q].status);
                 // once D_min = 0 is proven only the proving pair (bound -1) is
                 // refined; an evicted query is answered by its own launch later
                 keep = KIND == 0 ? (stop ? (st & kStatZero) && c.bound < 0.f : c.bound <= U)
@@ -2049,7 +2056,11 @@ __device__ void refine_phase_cta(const AT& A, unsigned ncand, unsigned& refined,
             QState& s = A.qs[c.q];
             V3<double> P, Q;
             int ia, ib;
-            const double d = refine_pair_cta<KIND>(s, c.ta, c.tb, &P, &Q, &ia, &ib);
+            // (a single query's triangle arrays from the CTA's copy: two
+            // dependent loads fewer before the triangles)
+            const float4* tA = AT::kOne ? cta().v.triA : s.A->tri;
+            const float4* tB = AT::kOne ? cta().v.triB : s.B->tri;
+            const double d = refine_pair_cta<KIND>(s, tA, tB, c.ta, c.tb, &P, &Q, &ia, &ib);
             if (threadIdx.x == 0) {
                 double* w = A.cand_pts + 6ull * ci;
                 w[0] = P.x; w[1] = P.y; w[2] = P.z; w[3] = Q.x; w[4] = Q.y; w[5] = Q.z;
